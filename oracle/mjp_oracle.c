@@ -1,0 +1,467 @@
+/*
+ * mjp_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, obviously-correct CPU reference for the R-MJP transient
+ * distribution of Pessoa, Schweiger & Presse, "Avoiding matrix exponentials
+ * for large transition rate matrices" (arXiv 2312.05647).  Only the test
+ * suite, the smoke check and the benchmark's CPU-baseline leg may load it.
+ * It shares no source, header, table or helper with the CUDA library; the two
+ * meet only in the seeded input generators.
+ *
+ * Arithmetic is IEEE FP64 throughout, except the Poisson weights, which are
+ * formed in long double log space (80-bit on x86-64, 128-bit on AArch64)
+ * because exp(-x) underflows FP64 for x > 708 (the paper's Algorithm 2 starts
+ * its recurrence at exp(-Omega t) and would silently return zeros there).
+ * Build with -ffp-contract=off: no multiply-add may be fused, so that the
+ * truncation index K is computed with exactly two roundings (Algorithm 2).
+ *
+ * Parity status: every routine below is pinned by the CPU test suite against
+ * closed forms, an independent library routine or brute force; see
+ * tests/test_oracle_pins.py.
+ */
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_ALLOC (-3)
+
+/* Model kinds (the same numbers the public header uses, restated here). */
+#define ORC_BD1D 1        /* birth-death, Eq. BD_def (Sec. 3.1.1)            */
+#define ORC_TWOSTATE 2    /* two-state birth-death, Eq. Gene_def (Sec. 3.1.2)*/
+#define ORC_MRNA_PROT2D 3 /* mRNA/protein birth-death, built from Eq.       */
+                          /* STS_chem's R->R+P reaction without switching    */
+
+/* ------------------------------------------------------------------------ */
+/* Rate matrices Lambda as CSR, rows = source state n, off-diagonal lambda_nm */
+/* (Sec. 2.1: lambda_nn = 0).  Columns of each row are ascending.            */
+/* ------------------------------------------------------------------------ */
+
+static int64_t push(int64_t* row_ptr, int32_t* col, double* val, int64_t nnz,
+                    int64_t cap, int64_t m, double rate) {
+  (void)row_ptr;
+  if (col != NULL) {
+    if (nnz >= cap) return -1;
+    col[nnz] = (int32_t)m;
+    val[nnz] = rate;
+  }
+  return nnz + 1;
+}
+
+/*
+ * Fill (row_ptr, col, val) for model `kind`; return nnz, or a negative error.
+ * With col == NULL only nnz is counted.
+ *
+ * BD1D (dims = {N}, theta = {beta, gamma}), Eq. BD_def:
+ *   lambda_{n,n+1} = beta, lambda_{n,n-1} = gamma*n.  The state space is cut
+ *   at N (Sec. 3.1.1); a birth out of n = N-1 is dropped (reflecting top), so
+ *   rows of A still sum to zero.
+ * TWOSTATE (dims = {N_R}, theta = {beta, gamma, lambda_act, lambda_ina}),
+ *   Eq. Gene_def with index n = n_R + sigma*N_R, sigma = 0 active, 1 inactive
+ *   (Sec. 3.1.2): active states produce at beta (dropped at n_R = N_R-1),
+ *   every state degrades at gamma*n_R, active->inactive at lambda_ina and
+ *   inactive->active at lambda_act (the reaction scheme Eq. 2S_chem and the
+ *   text of Sec. 3.1.2; the case labels of Eq. Gene_def are read accordingly).
+ * MRNA_PROT2D (dims = {M, P}, theta = {k_m, gamma_m, k_p, gamma_p}), index
+ *   n = m + M*p as in Sec. 3.1.3: m->m+1 at k_m, m->m-1 at gamma_m*m,
+ *   p->p+1 at k_p*m, p->p-1 at gamma_p*p; births out of the box are dropped.
+ */
+int64_t orc_build_model(int kind, const int64_t* dims, int ndims,
+                        const double* theta, int ntheta, int64_t* row_ptr,
+                        int32_t* col, double* val, int64_t cap) {
+  int64_t nnz = 0;
+  if (kind == ORC_BD1D) {
+    if (ndims != 1 || ntheta != 2 || dims[0] < 1) return ORC_ERR_ARG;
+    int64_t N = dims[0];
+    double beta = theta[0], gamma = theta[1];
+    for (int64_t n = 0; n < N; ++n) {
+      if (row_ptr) row_ptr[n] = nnz;
+      if (n >= 1) nnz = push(row_ptr, col, val, nnz, cap, n - 1, gamma * (double)n);
+      if (n + 1 < N) nnz = push(row_ptr, col, val, nnz, cap, n + 1, beta);
+      if (nnz < 0) return ORC_ERR_ARG;
+    }
+    if (row_ptr) row_ptr[N] = nnz;
+    return nnz;
+  }
+  if (kind == ORC_TWOSTATE) {
+    if (ndims != 1 || ntheta != 4 || dims[0] < 2) return ORC_ERR_ARG;
+    int64_t NR = dims[0];
+    double beta = theta[0], gamma = theta[1], lact = theta[2], lina = theta[3];
+    for (int64_t sg = 0; sg < 2; ++sg) {
+      for (int64_t nr = 0; nr < NR; ++nr) {
+        int64_t n = nr + sg * NR;
+        if (row_ptr) row_ptr[n] = nnz;
+        if (sg == 0) {
+          if (nr >= 1) nnz = push(row_ptr, col, val, nnz, cap, n - 1, gamma * (double)nr);
+          if (nr + 1 < NR) nnz = push(row_ptr, col, val, nnz, cap, n + 1, beta);
+          nnz = push(row_ptr, col, val, nnz, cap, n + NR, lina);
+        } else {
+          nnz = push(row_ptr, col, val, nnz, cap, n - NR, lact);
+          if (nr >= 1) nnz = push(row_ptr, col, val, nnz, cap, n - 1, gamma * (double)nr);
+        }
+        if (nnz < 0) return ORC_ERR_ARG;
+      }
+    }
+    if (row_ptr) row_ptr[2 * NR] = nnz;
+    return nnz;
+  }
+  if (kind == ORC_MRNA_PROT2D) {
+    if (ndims != 2 || ntheta != 4 || dims[0] < 2 || dims[1] < 1) return ORC_ERR_ARG;
+    int64_t M = dims[0], P = dims[1];
+    double km = theta[0], gm = theta[1], kp = theta[2], gp = theta[3];
+    for (int64_t p = 0; p < P; ++p) {
+      for (int64_t m = 0; m < M; ++m) {
+        int64_t n = m + M * p;
+        if (row_ptr) row_ptr[n] = nnz;
+        if (p >= 1) nnz = push(row_ptr, col, val, nnz, cap, n - M, gp * (double)p);
+        if (m >= 1) nnz = push(row_ptr, col, val, nnz, cap, n - 1, gm * (double)m);
+        if (m + 1 < M) nnz = push(row_ptr, col, val, nnz, cap, n + 1, km);
+        if (p + 1 < P && m >= 1) nnz = push(row_ptr, col, val, nnz, cap, n + M, kp * (double)m);
+        if (nnz < 0) return ORC_ERR_ARG;
+      }
+    }
+    if (row_ptr) row_ptr[M * P] = nnz;
+    return nnz;
+  }
+  return ORC_ERR_ARG;
+}
+
+/* Largest exit rate max_n sum_m lambda_nm = max_n |a_nn| (Eq. A_def), each
+ * row summed in stored (ascending column) order. */
+double orc_max_exit(int64_t n, const int64_t* row_ptr, const double* val) {
+  double best = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double e = 0.0;
+    for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) e = e + val[j];
+    if (e > best) best = e;
+  }
+  return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Truncation index and Poisson weights (Sec. 2.2.3, Algorithm 2).          */
+/* ------------------------------------------------------------------------ */
+
+/* Algorithm 2 loops while k <= x + 6 sqrt(x), incrementing k first, so the
+ * last jump index reached is K = floor(x + 6 sqrt(x)) + 1, x = Omega t. */
+int64_t orc_K_paper(double x) {
+  double s = sqrt(x);
+  double six_s = 6.0 * s;
+  double y = x + six_s;
+  return (int64_t)floor(y) + 1;
+}
+
+static long double log_pois(long double x, int64_t k) {
+  /* log Poisson(k | x), Eq. ME_uniform, in long double. */
+  return -x + (long double)k * logl(x) - lgammal((long double)k + 1.0L);
+}
+
+/*
+ * P[k] = Poisson(k | x) for k = 0..K (Eq. ME_uniform), and *eps = 1 - sum P
+ * = epsilon_{k*} of Eq. R-MJP_expansion.  The sum uses Kahan compensation in
+ * long double.  x = 0 gives the point mass at k = 0.
+ */
+int orc_poisson_weights(double x, int64_t K, double* P, double* eps) {
+  if (!(x >= 0.0) || K < 0) return ORC_ERR_ARG;
+  long double s = 0.0L, c = 0.0L;
+  for (int64_t k = 0; k <= K; ++k) {
+    long double p;
+    if (x == 0.0) p = (k == 0) ? 1.0L : 0.0L;
+    else p = expl(log_pois((long double)x, k));
+    P[k] = (double)p;
+    long double y = p - c;
+    long double t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  *eps = (double)(1.0L - s);
+  return ORC_OK;
+}
+
+/* Smallest K with 1 - sum_{k<=K} Poisson(k|x) <= tol (the "tolerance"
+ * truncation used by tight closed-form tests; not the paper's rule). */
+int64_t orc_K_tol(double x, double tol) {
+  if (!(x >= 0.0) || !(tol > 0.0)) return -1;
+  if (x == 0.0) return 0;
+  long double s = 0.0L, c = 0.0L;
+  for (int64_t k = 0;; ++k) {
+    long double p = expl(log_pois((long double)x, k));
+    long double y = p - c;
+    long double t = s + y;
+    c = (t - s) - y;
+    s = t;
+    if (1.0L - s <= (long double)tol) return k;
+    if (k > (int64_t)1e9) return -1;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* R-MJP series (Eq. R-MJP_expansion, Algorithm 2) at several times.        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * out[i*n + s] = rho*(t_i)_s for i < ntimes, where
+ *   rho*(t) = sum_{k=0}^{K} rho0 B^k P_k + (1 - sum_{k=0}^{K} P_k) rho0 B^K,
+ *   B = I + A/Omega (Eq. B_def), Omega = omega_factor * max_n |a_nn|
+ *   (the paper takes omega_factor = 1.1), P_k = Poisson(k | Omega t),
+ *   K = orc_K_paper(Omega t) (mode 0) or orc_K_tol(Omega t, tol) (mode 1).
+ * One chain rho0 B^k serves all times; each time gets exactly Algorithm 2
+ * with its own K_i and tail.  rho B is formed row by row (scatter form).
+ * If every rate is zero, A = 0 and rho(t) = rho0.
+ * omega_out/K_out/eps_out (nullable) receive Omega, K_i and epsilon_i.
+ */
+int orc_expv(int64_t n, const int64_t* row_ptr, const int32_t* col,
+             const double* val, const double* rho0, const double* times,
+             int ntimes, int mode, double tol, double omega_factor,
+             double* out, double* omega_out, int64_t* K_out, double* eps_out) {
+  if (n < 1 || ntimes < 0 || !(omega_factor > 1.0)) return ORC_ERR_ARG;
+  for (int i = 0; i < ntimes; ++i)
+    if (!(times[i] >= 0.0) || isinf(times[i])) return ORC_ERR_ARG;
+  double maxe = orc_max_exit(n, row_ptr, val);
+  if (maxe == 0.0) {
+    for (int i = 0; i < ntimes; ++i) {
+      memcpy(out + (size_t)i * n, rho0, sizeof(double) * (size_t)n);
+      if (K_out) K_out[i] = 0;
+      if (eps_out) eps_out[i] = 0.0;
+    }
+    if (omega_out) *omega_out = 0.0;
+    return ORC_OK;
+  }
+  double omega = omega_factor * maxe;
+  if (omega_out) *omega_out = omega;
+
+  int64_t* K = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ntimes > 0 ? ntimes : 1));
+  double** P = (double**)calloc((size_t)(ntimes > 0 ? ntimes : 1), sizeof(double*));
+  double* tail = (double*)malloc(sizeof(double) * (size_t)(ntimes > 0 ? ntimes : 1));
+  double* bdiag = (double*)malloc(sizeof(double) * (size_t)n);
+  double* boff = (double*)malloc(sizeof(double) * (size_t)(row_ptr[n] > 0 ? row_ptr[n] : 1));
+  double* rho = (double*)malloc(sizeof(double) * (size_t)n);
+  double* nxt = (double*)malloc(sizeof(double) * (size_t)n);
+  int rc = ORC_OK;
+  if (!K || !P || !tail || !bdiag || !boff || !rho || !nxt) { rc = ORC_ERR_ALLOC; goto done; }
+
+  /* B = I + A/Omega: b_nn = 1 - e_n/Omega, b_nm = lambda_nm/Omega. */
+  for (int64_t s = 0; s < n; ++s) {
+    double e = 0.0;
+    for (int64_t j = row_ptr[s]; j < row_ptr[s + 1]; ++j) {
+      e = e + val[j];
+      boff[j] = val[j] / omega;
+    }
+    bdiag[s] = 1.0 - e / omega;
+  }
+
+  int64_t Kmax = 0;
+  for (int i = 0; i < ntimes; ++i) {
+    double x = omega * times[i];
+    K[i] = (mode == 0) ? orc_K_paper(x) : orc_K_tol(x, tol);
+    if (K[i] < 0) { rc = ORC_ERR_ARG; goto done; }
+    P[i] = (double*)malloc(sizeof(double) * (size_t)(K[i] + 1));
+    if (!P[i]) { rc = ORC_ERR_ALLOC; goto done; }
+    orc_poisson_weights(x, K[i], P[i], &tail[i]);
+    if (K_out) K_out[i] = K[i];
+    if (eps_out) eps_out[i] = tail[i];
+    if (K[i] > Kmax) Kmax = K[i];
+  }
+
+  memcpy(rho, rho0, sizeof(double) * (size_t)n);
+  for (int i = 0; i < ntimes; ++i)
+    for (int64_t s = 0; s < n; ++s) out[(size_t)i * n + s] = P[i][0] * rho[s];
+
+  for (int64_t k = 1; k <= Kmax; ++k) {
+    /* rho <- rho B (Algorithm 2, loop body). */
+    for (int64_t s = 0; s < n; ++s) nxt[s] = 0.0;
+    for (int64_t s = 0; s < n; ++s) {
+      double r = rho[s];
+      nxt[s] += r * bdiag[s];
+      for (int64_t j = row_ptr[s]; j < row_ptr[s + 1]; ++j) nxt[col[j]] += r * boff[j];
+    }
+    double* tmp = rho; rho = nxt; nxt = tmp;
+    /* rho* += P_k rho for every time whose loop is still running. */
+    for (int i = 0; i < ntimes; ++i) {
+      if (k > K[i]) continue;
+      double w = P[i][k];
+      double* o = out + (size_t)i * n;
+      if (w != 0.0)
+        for (int64_t s = 0; s < n; ++s) o[s] += w * rho[s];
+      if (k == K[i]) /* rho* += (1 - P_cumulative) rho, after the loop. */
+        for (int64_t s = 0; s < n; ++s) o[s] += tail[i] * rho[s];
+    }
+  }
+  /* A time with K_i = 0 (tolerance mode, t = 0) still needs its tail. */
+  for (int i = 0; i < ntimes; ++i) {
+    if (K[i] != 0) continue;
+    double* o = out + (size_t)i * n;
+    for (int64_t s = 0; s < n; ++s) o[s] += tail[i] * rho0[s];
+  }
+
+done:
+  if (P) for (int i = 0; i < ntimes; ++i) free(P[i]);
+  free(P); free(K); free(tail); free(bdiag); free(boff); free(rho); free(nxt);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense matrix exponential: scaling and squaring with the degree-13 Pade   */
+/* approximant (N. J. Higham, SIAM J. Matrix Anal. Appl. 26 (2005) 1179).   */
+/* The paper's "conventional" baseline (Sec. 1, Sec. 3.2); used on tiny N.  */
+/* ------------------------------------------------------------------------ */
+
+static void matmul(int n, const double* A, const double* B, double* C) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < n; ++l) s += A[i * n + l] * B[l * n + j];
+      C[i * n + j] = s;
+    }
+}
+
+/* E = exp(A) for a dense row-major n x n matrix. */
+int orc_expm_pade13(int n, const double* A, double* E) {
+  if (n < 1) return ORC_ERR_ARG;
+  const int m = 13;
+  /* Pade [13/13] numerator coefficients b_j = (2m-j)! m! / ((2m)! j! (m-j)!). */
+  double b[14];
+  for (int j = 0; j <= m; ++j) {
+    long double v = lgammal(2.0L * m - j + 1) + lgammal((long double)m + 1) -
+                    lgammal(2.0L * m + 1) - lgammal((long double)j + 1) -
+                    lgammal((long double)(m - j) + 1);
+    b[j] = (double)expl(v);
+  }
+  const double theta13 = 5.371920351148152; /* Higham 2005, Table 2.3 */
+  size_t nn = (size_t)n * n;
+  double* W = (double*)calloc(nn * 12, sizeof(double));
+  int* piv = (int*)malloc(sizeof(int) * (size_t)n);
+  if (!W || !piv) { free(W); free(piv); return ORC_ERR_ALLOC; }
+  double *As = W, *A2 = W + nn, *A4 = W + 2 * nn, *A6 = W + 3 * nn, *U = W + 4 * nn,
+         *V = W + 5 * nn, *T1 = W + 6 * nn, *T2 = W + 7 * nn, *Pm = W + 8 * nn,
+         *Qm = W + 9 * nn, *R = W + 10 * nn, *T3 = W + 11 * nn;
+  double norm1 = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += fabs(A[i * n + j]);
+    if (s > norm1) norm1 = s;
+  }
+  int sc = 0;
+  if (norm1 > theta13) sc = (int)ceil(log2(norm1 / theta13));
+  double f = ldexp(1.0, -sc);
+  for (size_t i = 0; i < nn; ++i) As[i] = A[i] * f;
+  matmul(n, As, As, A2);
+  matmul(n, A2, A2, A4);
+  matmul(n, A4, A2, A6);
+  /* U = A [A6 (b13 A6 + b11 A4 + b9 A2) + b7 A6 + b5 A4 + b3 A2 + b1 I] */
+  for (size_t i = 0; i < nn; ++i) T1[i] = b[13] * A6[i] + b[11] * A4[i] + b[9] * A2[i];
+  matmul(n, A6, T1, T2);
+  for (size_t i = 0; i < nn; ++i) T2[i] += b[7] * A6[i] + b[5] * A4[i] + b[3] * A2[i];
+  for (int i = 0; i < n; ++i) T2[i * n + i] += b[1];
+  matmul(n, As, T2, U);
+  /* V = A6 (b12 A6 + b10 A4 + b8 A2) + b6 A6 + b4 A4 + b2 A2 + b0 I */
+  for (size_t i = 0; i < nn; ++i) T1[i] = b[12] * A6[i] + b[10] * A4[i] + b[8] * A2[i];
+  matmul(n, A6, T1, V);
+  for (size_t i = 0; i < nn; ++i) V[i] += b[6] * A6[i] + b[4] * A4[i] + b[2] * A2[i];
+  for (int i = 0; i < n; ++i) V[i * n + i] += b[0];
+  /* Solve (V - U) R = (V + U) by LU with partial pivoting. */
+  for (size_t i = 0; i < nn; ++i) { Qm[i] = V[i] - U[i]; Pm[i] = V[i] + U[i]; }
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(Qm[r * n + c]) > fabs(Qm[p * n + c])) p = r;
+    piv[c] = p;
+    if (p != c)
+      for (int j = 0; j < n; ++j) {
+        double t = Qm[c * n + j]; Qm[c * n + j] = Qm[p * n + j]; Qm[p * n + j] = t;
+        t = Pm[c * n + j]; Pm[c * n + j] = Pm[p * n + j]; Pm[p * n + j] = t;
+      }
+    double d = Qm[c * n + c];
+    if (d == 0.0) { free(W); free(piv); return ORC_ERR_ARG; }
+    for (int r = c + 1; r < n; ++r) {
+      double l = Qm[r * n + c] / d;
+      if (l == 0.0) continue;
+      for (int j = c; j < n; ++j) Qm[r * n + j] -= l * Qm[c * n + j];
+      for (int j = 0; j < n; ++j) Pm[r * n + j] -= l * Pm[c * n + j];
+    }
+  }
+  for (int j = 0; j < n; ++j)
+    for (int r = n - 1; r >= 0; --r) {
+      double s = Pm[r * n + j];
+      for (int c = r + 1; c < n; ++c) s -= Qm[r * n + c] * R[c * n + j];
+      R[r * n + j] = s / Qm[r * n + r];
+    }
+  for (int q = 0; q < sc; ++q) {
+    matmul(n, R, R, T3);
+    memcpy(R, T3, sizeof(double) * nn);
+  }
+  memcpy(E, R, sizeof(double) * nn);
+  free(W);
+  free(piv);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gillespie's direct method (D. T. Gillespie, J. Phys. Chem. 81 (1977)     */
+/* 2340), cited by the paper for simulating MJPs (Sec. 2.1.1).  Random      */
+/* numbers: splitmix64 seeding xoshiro256** (Blackman & Vigna, 2018).       */
+/* ------------------------------------------------------------------------ */
+
+static uint64_t splitmix64(uint64_t* s) {
+  uint64_t z = (*s += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+static uint64_t rotl(uint64_t x, int k) { return (x << k) | (x >> (64 - k)); }
+static uint64_t xoshiro(uint64_t* s) {
+  uint64_t r = rotl(s[1] * 5, 7) * 9;
+  uint64_t t = s[1] << 17;
+  s[2] ^= s[0]; s[3] ^= s[1]; s[1] ^= s[2]; s[0] ^= s[3];
+  s[2] ^= t;
+  s[3] = rotl(s[3], 45);
+  return r;
+}
+static double unif_open(uint64_t* s) { /* (0, 1) */
+  return ((double)(xoshiro(s) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+/*
+ * Simulate nruns independent trajectories from state s0 and record the state
+ * occupied at each (ascending) observation time: counts[i*n + s] += 1.
+ */
+int orc_gillespie(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                  const double* val, int64_t s0, const double* times,
+                  int ntimes, int64_t nruns, uint64_t seed, int64_t* counts) {
+  if (n < 1 || s0 < 0 || s0 >= n || ntimes < 1) return ORC_ERR_ARG;
+  for (int i = 1; i < ntimes; ++i)
+    if (times[i] < times[i - 1]) return ORC_ERR_ARG;
+  uint64_t sm = seed, st[4];
+  for (int q = 0; q < 4; ++q) st[q] = splitmix64(&sm);
+  for (int64_t r = 0; r < nruns; ++r) {
+    int64_t s = s0;
+    double tau = 0.0;
+    int j = 0;
+    while (j < ntimes) {
+      double e = 0.0;
+      for (int64_t q = row_ptr[s]; q < row_ptr[s + 1]; ++q) e += val[q];
+      if (e <= 0.0) {
+        for (; j < ntimes; ++j) counts[(size_t)j * n + s] += 1;
+        break;
+      }
+      double dt = -log(unif_open(st)) / e;
+      while (j < ntimes && tau + dt > times[j]) {
+        counts[(size_t)j * n + s] += 1;
+        ++j;
+      }
+      if (j >= ntimes) break;
+      tau += dt;
+      double u = unif_open(st) * e, acc = 0.0;
+      int64_t nxt = col[row_ptr[s + 1] - 1];
+      for (int64_t q = row_ptr[s]; q < row_ptr[s + 1]; ++q) {
+        acc += val[q];
+        if (u < acc) { nxt = col[q]; break; }
+      }
+      s = nxt;
+    }
+  }
+  return ORC_OK;
+}
