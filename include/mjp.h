@@ -1,0 +1,195 @@
+/*
+ * mjp.h -- C ABI of the GB300 R-MJP library (libmjp.so).
+ *
+ * The library computes transient distributions rho(t) = rho(0) exp(A_theta t)
+ * of a Markov jump process with the jump-truncated uniformisation series of
+ * Pessoa, Schweiger & Presse (arXiv 2312.05647), Method #3 "R-MJP":
+ *
+ *   rho*(t) = sum_{k=0}^{K} rho0 B^k Poisson(k | Omega t)
+ *             + (1 - sum_{k=0}^{K} Poisson(k | Omega t)) rho0 B^K,
+ *   B = I + A/Omega (Eq. B_def), Omega = 1.1 max_n |a_nn|,
+ *   K = floor(Omega t + 6 sqrt(Omega t)) + 1  (Eq. R-MJP_expansion, Alg. 2),
+ *
+ * and the snapshot log-likelihood built from it (Sec. 2.1.2).  All work runs
+ * in the library's own CUDA kernels on the calling device; there is no CPU
+ * fallback.  Plain C99: no C++ or framework types cross this boundary.
+ *
+ * Conventions for every entry point:
+ *  - Return value: MJP_OK (0) or a negative MJP_ERR_* code; the message of
+ *    the most recent failure on the calling thread is mjp_last_error().
+ *  - "device" pointers are CUDA device addresses on the current device;
+ *    "host" pointers are ordinary CPU memory.  The caller owns every buffer
+ *    it passes; the library owns the handles it creates until *_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).
+ *    Calls with device inputs and outputs are asynchronous on that stream;
+ *    calls that take or return host data synchronise it before returning.
+ *  - A handle carries scratch memory, so calls on one handle must be ordered
+ *    (one stream, or explicit synchronisation between streams).
+ */
+#ifndef MJP_H
+#define MJP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MJP_OK 0
+#define MJP_ERR_ARG (-1)            /* invalid argument (NULL, size, NaN, t < 0, ...) */
+#define MJP_ERR_CSR (-2)            /* malformed CSR (row_ptr not monotone, column out of range, diagonal entry, negative rate) */
+#define MJP_ERR_ALLOC (-3)          /* device or host allocation failed */
+#define MJP_ERR_CUDA (-4)           /* a CUDA runtime call failed */
+#define MJP_ERR_DEVICE_TIMEOUT (-5) /* a bounded device wait ran out */
+#define MJP_ERR_KCAP (-6)           /* truncation index K above the configured cap */
+#define MJP_ERR_NUMERIC (-7)        /* non-finite or negative probability produced */
+#define MJP_ERR_UNSUPPORTED (-8)    /* valid request this build does not handle */
+
+/* ---- model kinds ------------------------------------------------------- */
+/* Birth-death, Eq. BD_def (Sec. 3.1.1). dims = {N}; theta = {beta, gamma}:
+ * lambda_{n,n+1} = beta (n < N-1), lambda_{n,n-1} = gamma n. */
+#define MJP_BD1D 1
+/* Two-state birth-death, Eq. Gene_def / Eq. 2S_chem (Sec. 3.1.2).
+ * dims = {N_R}; N = 2 N_R, n = n_R + sigma N_R (sigma 0 active, 1 inactive);
+ * theta = {beta, gamma, lambda_act, lambda_ina}: birth beta in the active
+ * state (n_R < N_R-1), death gamma n_R, active->inactive lambda_ina,
+ * inactive->active lambda_act. */
+#define MJP_TWOSTATE 2
+/* mRNA/protein birth-death (the R -> R+P production of Eq. STS_chem without
+ * gene switching).  dims = {M, P}; n = m + M p; theta = {k_m, gamma_m, k_p,
+ * gamma_p}: m+1 at k_m, m-1 at gamma_m m, p+1 at k_p m, p-1 at gamma_p p;
+ * births that would leave the box are dropped. */
+#define MJP_MRNA_PROT2D 3
+/* General sparse rate matrix given as CSR (rows = source state). */
+#define MJP_CSR 4
+
+/* ---- chain precision --------------------------------------------------- */
+#define MJP_FP32 1 /* FP32 chain, Kahan-compensated FP32 accumulation, FP64 Omega/K/weights */
+#define MJP_FP64 2 /* FP64 chain and accumulation */
+
+/* ---- truncation rule --------------------------------------------------- */
+#define MJP_TRUNC_PAPER 0 /* K = floor(x + 6 sqrt x) + 1, x = Omega t (Algorithm 2) */
+#define MJP_TRUNC_TOL 1   /* smallest K with Poisson tail mass <= tol (1e-20 <= tol < 0.5) */
+
+/* ---- pointer kinds for batched calls ----------------------------------- */
+#define MJP_PTR_HOST 0
+#define MJP_PTR_DEVICE 1
+
+/* ---- model options (rate_model_set_option) ----------------------------- */
+#define MJP_OPT_RENORM_PERIOD 1 /* FP32 chains: rescale rho to its initial mass every r jumps (0 = off, default) */
+#define MJP_OPT_K_CAP 2         /* largest K accepted (default 2^26) */
+#define MJP_OPT_THREADS 3       /* threads per CTA for stencil chains (0 = automatic) */
+#define MJP_OPT_CLUSTER 4       /* CTAs per instance for stencil chains (0 = automatic; 1, 2, 4, 8, 16) */
+
+typedef struct mjp_model mjp_model;
+typedef struct mjp_obs mjp_obs;
+
+/* Per-call report of the truncation (Eq. R-MJP_expansion, Alg. 2).  Arrays
+ * are host memory of length ntimes supplied by the caller (or NULL). */
+typedef struct {
+  double omega;    /* Omega = 1.1 max_n |a_nn| (0 when every rate is zero) */
+  int64_t* K;      /* K_i per time, in the caller's time order */
+  double* eps;     /* epsilon_i = 1 - sum_{k<=K_i} Poisson(k|Omega t_i), the tail moved onto rho0 B^K */
+} mjp_series_info;
+
+/* Message of the last failure on this thread ("" if none). */
+const char* mjp_last_error(void);
+
+/* Library version string. */
+const char* mjp_version(void);
+
+/*
+ * Create a stencil model (rates built matrix-free on the device from theta).
+ * kind/dims/theta as documented beside MJP_BD1D, MJP_TWOSTATE,
+ * MJP_MRNA_PROT2D; rates must be finite and >= 0.  precision is MJP_FP32 or
+ * MJP_FP64.  Errors: MJP_ERR_ARG.
+ * Paper: Eq. A_def (generator from rates), Eqs. BD_def and Gene_def.
+ */
+int rate_model_create_stencil(mjp_model** out, int kind, const int64_t* dims, int ndims,
+                              const double* theta, int ntheta, int precision);
+
+/*
+ * Create a model from a general rate matrix Lambda in CSR form (host arrays):
+ * row_ptr[n+1] (monotone, row_ptr[0] = 0), col[nnz] in [0, n) with no
+ * diagonal entries, rate[nnz] >= 0 finite.  Rows are source states
+ * (lambda_nm = rate of n -> m, Sec. 2.1).  The library copies the data,
+ * forms the exit rates e_n = sum_m lambda_nm and stores B^T (incoming
+ * transitions) on the device.  Errors: MJP_ERR_ARG, MJP_ERR_CSR, MJP_ERR_ALLOC.
+ */
+int rate_model_create_csr(mjp_model** out, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                          const double* rate, int precision);
+
+/* Replace theta of a stencil model (host array). Errors: MJP_ERR_ARG. */
+int rate_model_set_theta(mjp_model* m, const double* theta, int ntheta);
+
+/* Set an MJP_OPT_* option.  Errors: MJP_ERR_ARG. */
+int rate_model_set_option(mjp_model* m, int option, int64_t value);
+
+/* Number of states N of the model (or -1 for a NULL handle). */
+int64_t rate_model_num_states(const mjp_model* m);
+
+/* Free the model and its device memory (NULL is ignored). */
+void rate_model_destroy(mjp_model* m);
+
+/*
+ * Transient distributions at several times (Algorithm 2 per time; one jump
+ * chain rho0 B^k is shared by all times, each time with its own K_i, window
+ * of weights and tail).
+ *   rho0   device, N values in the model's precision (float or double), >= 0.
+ *   times  host, ntimes values, finite and >= 0, any order, 1 <= ntimes <= 256.
+ *   out    device, ntimes x N row-major in the model's precision; row i is
+ *          rho*(times[i]).
+ *   info   host, nullable; when given the call synchronises `stream`.
+ * Errors: MJP_ERR_ARG, MJP_ERR_KCAP, MJP_ERR_ALLOC, MJP_ERR_CUDA.
+ */
+int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes, void* out,
+                mjp_series_info* info, int trunc_mode, double tol, void* stream);
+
+/*
+ * Snapshot observations (Sec. 2.1.2): at each time T^i a set of observation
+ * groups; group g holds the states whose probabilities are summed (a hidden
+ * component, e.g. the gene state of Sec. 3.1.2, is summed out this way) and a
+ * count c_g >= 0.  Host arrays:
+ *   times[ntimes]            observation times (>= 0, any order),
+ *   group_ptr[ntimes+1]      groups of time i are [group_ptr[i], group_ptr[i+1]),
+ *   counts[G]                multiplicity of each group,
+ *   member_ptr[G+1]          states of group g are members[member_ptr[g] ..],
+ *   members[]                state indices in [0, n),
+ *   rho0[n]                  initial distribution rho(0) (FP64, >= 0).
+ * The library copies everything.  Limits: ntimes <= 256, G <= 8192.
+ * Errors: MJP_ERR_ARG, MJP_ERR_ALLOC.
+ */
+int mjp_obs_create(mjp_obs** out, int64_t n, int ntimes, const double* times,
+                   const int64_t* group_ptr, const double* counts, const int64_t* member_ptr,
+                   const int32_t* members, const double* rho0);
+void mjp_obs_destroy(mjp_obs* obs);
+
+/*
+ * Log-likelihood of the observations for B parameter vectors:
+ *   out[b] = sum_i sum_g c_g log( sum_{s in g} rho*(T^i | theta_b)_s ),
+ * rho* from the R-MJP series above (p(s^i|theta) = rho(T^i)_{s^i}, Sec. 2.1.2;
+ * hidden states summed as in Sec. 3.1.2).  The prior is not included.
+ *   theta  B x ntheta row-major (stencil models; ignored for CSR, where B = 1)
+ *   out    B values
+ *   where  MJP_PTR_HOST: theta and out are host memory (the call copies and
+ *          synchronises); MJP_PTR_DEVICE: both are device memory (async).
+ * An observed group with probability 0 gives -inf (not an error).
+ * Errors: MJP_ERR_ARG, MJP_ERR_KCAP, MJP_ERR_ALLOC, MJP_ERR_CUDA.
+ */
+int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double* out, int where,
+           int trunc_mode, double tol, void* stream);
+
+/*
+ * Synchronise `stream` and report device-side errors recorded by earlier
+ * asynchronous calls on this model (K above the cap, non-finite values, a
+ * bounded wait that ran out).  Clears the record.  Returns MJP_OK or the
+ * first recorded MJP_ERR_*.
+ */
+int rate_model_check(mjp_model* m, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MJP_H */

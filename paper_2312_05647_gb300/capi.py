@@ -1,0 +1,86 @@
+"""ctypes binding of libmjp.so (include/mjp.h): argument marshalling only.
+
+Every numerical step runs in the library's CUDA kernels.  PyTorch supplies
+device memory and the current stream; there is no CPU fallback, and loading
+fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libmjp.so")
+
+MJP_OK = 0
+ERRORS = {-1: "MJP_ERR_ARG", -2: "MJP_ERR_CSR", -3: "MJP_ERR_ALLOC", -4: "MJP_ERR_CUDA",
+          -5: "MJP_ERR_DEVICE_TIMEOUT", -6: "MJP_ERR_KCAP", -7: "MJP_ERR_NUMERIC",
+          -8: "MJP_ERR_UNSUPPORTED"}
+BD1D, TWOSTATE, MRNA_PROT2D, CSR = 1, 2, 3, 4
+FP32, FP64 = 1, 2
+TRUNC_PAPER, TRUNC_TOL = 0, 1
+PTR_HOST, PTR_DEVICE = 0, 1
+OPT_RENORM_PERIOD, OPT_K_CAP, OPT_THREADS, OPT_CLUSTER = 1, 2, 3, 4
+
+# Every entry point of include/mjp.h: name -> (restype, argtypes).
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_f32p = ctypes.POINTER(ctypes.c_float)
+
+
+class SeriesInfo(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("K", _i64p), ("eps", _f64p)]
+
+
+SIGNATURES = {
+    "mjp_last_error": (ctypes.c_char_p, []),
+    "mjp_version": (ctypes.c_char_p, []),
+    "rate_model_create_stencil": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64p, ctypes.c_int,
+                                                 _f64p, ctypes.c_int, ctypes.c_int]),
+    "rate_model_create_csr": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, _i64p, _i32p, _f64p,
+                                             ctypes.c_int]),
+    "rate_model_set_theta": (ctypes.c_int, [_vp, _f64p, ctypes.c_int]),
+    "rate_model_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64]),
+    "rate_model_num_states": (ctypes.c_int64, [_vp]),
+    "rate_model_destroy": (None, [_vp]),
+    "rate_model_check": (ctypes.c_int, [_vp, _vp]),
+    "expv_series": (ctypes.c_int, [_vp, _vp, _f64p, ctypes.c_int, _vp, ctypes.POINTER(SeriesInfo),
+                                   ctypes.c_int, ctypes.c_double, _vp]),
+    "mjp_obs_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_int, _f64p, _i64p, _f64p,
+                                      _i64p, _i32p, _f64p]),
+    "mjp_obs_destroy": (None, [_vp]),
+    "loglik": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                              _vp]),
+}
+
+_LIB = None
+
+
+class MJPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libmjp.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2312_05647_gb300.build.build() "
+                              "(or __graft_entry__.build()) first; there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def check(rc: int):
+    if rc != MJP_OK:
+        raise MJPError(rc, lib().mjp_last_error().decode())
+    return rc

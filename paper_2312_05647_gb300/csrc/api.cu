@@ -1,0 +1,459 @@
+// api.cu -- the C ABI declared in include/mjp.h: handles, argument checks,
+// workspace and the launch sequence planner -> chain.  Every numerical step
+// runs in the library's kernels; this file only marshals.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace mjp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define MJP_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      cudaGetLastError();                                                                \
+      return fail(MJP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    }                                                                                    \
+  } while (0)
+
+// Grow-only device buffer.  Growing synchronises the device first so that no
+// queued kernel still uses the old allocation.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  int ensure(size_t bytes) {
+    if (bytes <= cap) return MJP_OK;
+    cudaDeviceSynchronize();
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMalloc(&p, bytes < 256 ? 256 : bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MJP_ERR_ALLOC, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    cap = bytes < 256 ? 256 : bytes;
+    return MJP_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <typename T>
+  T* as() const {
+    return reinterpret_cast<T*>(p);
+  }
+};
+
+bool finite_nonneg(const double* v, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!(v[i] >= 0.0) || !std::isfinite(v[i])) return false;
+  return true;
+}
+
+int ntheta_of(int kind) {
+  switch (kind) {
+    case MJP_BD1D: return 2;
+    case MJP_TWOSTATE: return 4;
+    case MJP_MRNA_PROT2D: return 4;
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+struct mjp_model {
+  int kind = 0;
+  int precision = MJP_FP32;
+  int64_t N = 0, M = 0, P = 1;
+  std::vector<double> theta;
+  // options
+  int renorm = 0;
+  int64_t kcap = (int64_t)1 << 26;
+  int threads = 0;
+  int cluster = 0;
+  // workspace (scratch owned by the handle)
+  DevBuf d_times, d_orig, d_win, d_info, d_theta, d_comp, d_status, d_ll;
+  ~mjp_model() {
+    d_times.release(); d_orig.release(); d_win.release(); d_info.release();
+    d_theta.release(); d_comp.release(); d_status.release(); d_ll.release();
+  }
+};
+
+struct mjp_obs {
+  int64_t n = 0;
+  int ntimes = 0;
+  int G = 0;
+  DevBuf d_times, d_gptr, d_counts, d_mptr, d_members, d_rho64, d_rho32;
+  ~mjp_obs() {
+    d_times.release(); d_gptr.release(); d_counts.release(); d_mptr.release();
+    d_members.release(); d_rho64.release(); d_rho32.release();
+  }
+};
+
+namespace {
+
+int ensure_status(mjp_model* m) {
+  if (m->d_status.p) return MJP_OK;
+  int rc = m->d_status.ensure(sizeof(int));
+  if (rc) return rc;
+  MJP_CUDA(cudaMemset(m->d_status.p, 0, sizeof(int)));
+  return MJP_OK;
+}
+
+// Pick cluster size and threads for a stencil chain of this model.
+int stencil_config(mjp_model* m, int loglik_mode, int nt, int G, int* cluster, int* threads,
+                   int64_t* slab) {
+  const size_t kSmemMax = 227 * 1024;
+  int C = m->cluster;
+  auto slab_of = [&](int c) {
+    int64_t s = (m->N + c - 1) / c;
+    return (s + 3) / 4 * 4;
+  };
+  if (C <= 0) {
+    C = 0;
+    for (int c = 1; c <= 16; c *= 2) {
+      if (chain_stencil_smem(m->precision, loglik_mode, slab_of(c), nt, G) <= kSmemMax) {
+        C = c;
+        break;
+      }
+    }
+    if (C == 0) return fail(MJP_ERR_UNSUPPORTED, "state space too large for an on-chip stencil chain");
+  }
+  if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16) return fail(MJP_ERR_ARG, "cluster must be 1, 2, 4, 8 or 16");
+  int64_t s = slab_of(C);
+  size_t smem = chain_stencil_smem(m->precision, loglik_mode, s, nt, G);
+  if (smem > kSmemMax) return fail(MJP_ERR_UNSUPPORTED, "slab does not fit shared memory; raise the cluster size");
+  int t = m->threads;
+  if (t <= 0) {
+    int64_t want = (s + 1) / 2;
+    want = (want + 31) / 32 * 32;
+    t = (int)std::min<int64_t>(1024, std::max<int64_t>(64, want));
+  }
+  if (t % 32 != 0 || t < 32 || t > 1024) return fail(MJP_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
+  int nclusters = chain_stencil_max_cluster_blocks(m->kind, m->precision, loglik_mode, C, t, smem);
+  if (nclusters <= 0) return fail(MJP_ERR_UNSUPPORTED, "stencil chain configuration cannot be made resident");
+  *cluster = C;
+  *threads = t;
+  *slab = s;
+  return MJP_OK;
+}
+
+int map_status(int st) {
+  switch (st) {
+    case kStatusOk: return MJP_OK;
+    case kStatusKcap: return fail(MJP_ERR_KCAP, "truncation index K above the cap");
+    case kStatusNumeric: return fail(MJP_ERR_NUMERIC, "non-finite or negative probability");
+    case kStatusTimeout: return fail(MJP_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
+    default: return fail(MJP_ERR_ARG, "device rejected an argument");
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mjp_last_error(void) { return g_err.c_str(); }
+
+const char* mjp_version(void) { return "mjp-gb300 0.1 (sm_103a)"; }
+
+int rate_model_create_stencil(mjp_model** out, int kind, const int64_t* dims, int ndims,
+                              const double* theta, int ntheta, int precision) {
+  if (!out) return fail(MJP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (kind != MJP_BD1D && kind != MJP_TWOSTATE && kind != MJP_MRNA_PROT2D)
+    return fail(MJP_ERR_ARG, "unknown stencil kind");
+  if (precision != MJP_FP32 && precision != MJP_FP64) return fail(MJP_ERR_ARG, "precision must be MJP_FP32 or MJP_FP64");
+  if (!dims || !theta) return fail(MJP_ERR_ARG, "dims/theta is NULL");
+  if (ntheta != ntheta_of(kind)) return fail(MJP_ERR_ARG, "wrong number of parameters for this kind");
+  if (!finite_nonneg(theta, ntheta)) return fail(MJP_ERR_ARG, "rates must be finite and >= 0");
+  auto* m = new mjp_model();
+  m->kind = kind;
+  m->precision = precision;
+  m->theta.assign(theta, theta + ntheta);
+  if (kind == MJP_BD1D) {
+    if (ndims != 1 || dims[0] < 1) { delete m; return fail(MJP_ERR_ARG, "BD1D needs dims = {N}, N >= 1"); }
+    m->M = dims[0]; m->P = 1; m->N = dims[0];
+  } else if (kind == MJP_TWOSTATE) {
+    if (ndims != 1 || dims[0] < 2) { delete m; return fail(MJP_ERR_ARG, "TWOSTATE needs dims = {N_R}, N_R >= 2"); }
+    m->M = dims[0]; m->P = 2; m->N = 2 * dims[0];
+  } else {
+    if (ndims != 2 || dims[0] < 2 || dims[1] < 1) { delete m; return fail(MJP_ERR_ARG, "MRNA_PROT2D needs dims = {M >= 2, P >= 1}"); }
+    m->M = dims[0]; m->P = dims[1]; m->N = dims[0] * dims[1];
+  }
+  if (m->N > ((int64_t)1 << 31) - 1) { delete m; return fail(MJP_ERR_ARG, "too many states"); }
+  *out = m;
+  return MJP_OK;
+}
+
+int rate_model_create_csr(mjp_model** out, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                          const double* rate, int precision) {
+  (void)n; (void)row_ptr; (void)col; (void)rate; (void)precision;
+  if (out) *out = nullptr;
+  return fail(MJP_ERR_UNSUPPORTED, "CSR models are not built in this version");
+}
+
+int rate_model_set_theta(mjp_model* m, const double* theta, int ntheta) {
+  if (!m || !theta) return fail(MJP_ERR_ARG, "NULL argument");
+  if (m->kind == MJP_CSR) return fail(MJP_ERR_ARG, "CSR models have no theta");
+  if (ntheta != ntheta_of(m->kind)) return fail(MJP_ERR_ARG, "wrong number of parameters");
+  if (!finite_nonneg(theta, ntheta)) return fail(MJP_ERR_ARG, "rates must be finite and >= 0");
+  m->theta.assign(theta, theta + ntheta);
+  return MJP_OK;
+}
+
+int rate_model_set_option(mjp_model* m, int option, int64_t value) {
+  if (!m) return fail(MJP_ERR_ARG, "NULL model");
+  switch (option) {
+    case MJP_OPT_RENORM_PERIOD:
+      if (value < 0 || value > (1 << 30)) return fail(MJP_ERR_ARG, "renorm period out of range");
+      m->renorm = (int)value;
+      return MJP_OK;
+    case MJP_OPT_K_CAP:
+      if (value < 1 || value > ((int64_t)1 << 40)) return fail(MJP_ERR_ARG, "K cap must be in [1, 2^40]");
+      m->kcap = value;
+      return MJP_OK;
+    case MJP_OPT_THREADS:
+      if (value != 0 && (value % 32 != 0 || value < 32 || value > 1024)) return fail(MJP_ERR_ARG, "threads must be 0 or a multiple of 32 in [32, 1024]");
+      m->threads = (int)value;
+      return MJP_OK;
+    case MJP_OPT_CLUSTER:
+      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16) return fail(MJP_ERR_ARG, "cluster must be 0, 1, 2, 4, 8 or 16");
+      m->cluster = (int)value;
+      return MJP_OK;
+    default:
+      return fail(MJP_ERR_ARG, "unknown option");
+  }
+}
+
+int64_t rate_model_num_states(const mjp_model* m) { return m ? m->N : -1; }
+
+void rate_model_destroy(mjp_model* m) { delete m; }
+
+int rate_model_check(mjp_model* m, void* stream) {
+  if (!m) return fail(MJP_ERR_ARG, "NULL model");
+  MJP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (!m->d_status.p) return MJP_OK;
+  int st = 0;
+  MJP_CUDA(cudaMemcpy(&st, m->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  MJP_CUDA(cudaMemset(m->d_status.p, 0, sizeof(int)));
+  return map_status(st);
+}
+
+int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes, void* out,
+                mjp_series_info* info, int trunc_mode, double tol, void* stream) {
+  if (!m || !rho0 || !times || !out) return fail(MJP_ERR_ARG, "NULL argument");
+  if (ntimes < 1 || ntimes > kMaxTimes) return fail(MJP_ERR_ARG, "ntimes must be in [1, 256]");
+  if (trunc_mode != MJP_TRUNC_PAPER && trunc_mode != MJP_TRUNC_TOL) return fail(MJP_ERR_ARG, "unknown truncation mode");
+  if (trunc_mode == MJP_TRUNC_TOL && !(tol >= 1e-20 && tol < 0.5)) return fail(MJP_ERR_ARG, "tol must be in [1e-20, 0.5)");
+  for (int i = 0; i < ntimes; ++i)
+    if (!(times[i] >= 0.0) || !std::isfinite(times[i])) return fail(MJP_ERR_ARG, "times must be finite and >= 0");
+  if (m->kind == MJP_CSR) return fail(MJP_ERR_UNSUPPORTED, "CSR series not built in this version");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nt = ntimes;
+  std::vector<int32_t> order(nt);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return times[a] < times[b]; });
+  std::vector<double> st(nt);
+  for (int i = 0; i < nt; ++i) st[i] = times[order[i]];
+
+  int C, T;
+  int64_t slab;
+  int rc = stencil_config(m, 0, nt, 0, &C, &T, &slab);
+  if (rc) return rc;
+  if ((rc = ensure_status(m))) return rc;
+  if ((rc = m->d_times.ensure(sizeof(double) * nt))) return rc;
+  if ((rc = m->d_orig.ensure(sizeof(int32_t) * nt))) return rc;
+  if ((rc = m->d_win.ensure(sizeof(Win) * nt))) return rc;
+  if ((rc = m->d_info.ensure(sizeof(JobInfo)))) return rc;
+  if ((rc = m->d_theta.ensure(sizeof(double) * m->theta.size()))) return rc;
+  if (m->precision == MJP_FP32 && (rc = m->d_comp.ensure(sizeof(float) * (size_t)nt * m->N))) return rc;
+  MJP_CUDA(cudaMemcpyAsync(m->d_times.p, st.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_orig.p, order.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_theta.p, m->theta.data(), sizeof(double) * m->theta.size(), cudaMemcpyHostToDevice, s));
+
+  PlanParams pp = {};
+  pp.kind = m->kind; pp.M = (int32_t)m->M; pp.P = (int32_t)m->P; pp.N = m->N;
+  pp.ntheta = (int)m->theta.size(); pp.theta = m->d_theta.as<double>(); pp.B = 1;
+  pp.ntimes = nt; pp.times = m->d_times.as<double>();
+  pp.trunc_mode = trunc_mode; pp.tol = tol; pp.omega_factor = 1.1; pp.omega_fixed = -1.0;
+  pp.kcap = m->kcap; pp.win = m->d_win.as<Win>(); pp.info = m->d_info.as<JobInfo>();
+  pp.status = m->d_status.as<int>();
+  MJP_CUDA(launch_plan(pp, s));
+
+  ChainParams cp = {};
+  cp.M = (int32_t)m->M; cp.P = (int32_t)m->P; cp.N = m->N;
+  cp.ntheta = pp.ntheta; cp.theta = pp.theta; cp.B = 1; cp.ntimes = nt;
+  cp.orig = m->d_orig.as<int32_t>(); cp.win = pp.win; cp.info = pp.info; cp.rho0 = rho0;
+  cp.out = out; cp.out_stride = 0; cp.comp = m->d_comp.as<float>(); cp.comp_stride = 0;
+  cp.renorm = (m->precision == MJP_FP32) ? m->renorm : 0;
+  cp.slab = slab; cp.status = pp.status;
+  MJP_CUDA(launch_chain_stencil(m->kind, m->precision, 0, cp, C, T, s));
+
+  if (info) {
+    std::vector<Win> w(nt);
+    JobInfo ji;
+    MJP_CUDA(cudaMemcpyAsync(w.data(), m->d_win.p, sizeof(Win) * nt, cudaMemcpyDeviceToHost, s));
+    MJP_CUDA(cudaMemcpyAsync(&ji, m->d_info.p, sizeof(JobInfo), cudaMemcpyDeviceToHost, s));
+    MJP_CUDA(cudaStreamSynchronize(s));
+    info->omega = ji.omega;
+    for (int i = 0; i < nt; ++i) {
+      if (info->K) info->K[order[i]] = w[i].K;
+      if (info->eps) info->eps[order[i]] = w[i].tail;
+    }
+    return rate_model_check(m, stream);
+  }
+  return MJP_OK;
+}
+
+int mjp_obs_create(mjp_obs** out, int64_t n, int ntimes, const double* times,
+                   const int64_t* group_ptr, const double* counts, const int64_t* member_ptr,
+                   const int32_t* members, const double* rho0) {
+  if (!out) return fail(MJP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || ntimes < 1 || ntimes > kMaxTimes) return fail(MJP_ERR_ARG, "bad n or ntimes");
+  if (!times || !group_ptr || !counts || !member_ptr || !members || !rho0) return fail(MJP_ERR_ARG, "NULL argument");
+  if (group_ptr[0] != 0) return fail(MJP_ERR_ARG, "group_ptr[0] must be 0");
+  for (int i = 0; i < ntimes; ++i) {
+    if (group_ptr[i + 1] < group_ptr[i]) return fail(MJP_ERR_ARG, "group_ptr not monotone");
+    if (!(times[i] >= 0.0) || !std::isfinite(times[i])) return fail(MJP_ERR_ARG, "times must be finite and >= 0");
+  }
+  const int64_t G = group_ptr[ntimes];
+  if (G > kMaxGroups) return fail(MJP_ERR_ARG, "too many observation groups (limit 8192)");
+  if (member_ptr[0] != 0) return fail(MJP_ERR_ARG, "member_ptr[0] must be 0");
+  for (int64_t g = 0; g < G; ++g) {
+    if (member_ptr[g + 1] < member_ptr[g]) return fail(MJP_ERR_ARG, "member_ptr not monotone");
+    if (!(counts[g] >= 0.0) || !std::isfinite(counts[g])) return fail(MJP_ERR_ARG, "counts must be finite and >= 0");
+  }
+  const int64_t nm = member_ptr[G];
+  for (int64_t q = 0; q < nm; ++q)
+    if (members[q] < 0 || members[q] >= n) return fail(MJP_ERR_ARG, "member state out of range");
+  if (!finite_nonneg(rho0, n)) return fail(MJP_ERR_ARG, "rho0 must be finite and >= 0");
+
+  // Reorder times ascending (groups follow their time).
+  std::vector<int> order(ntimes);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return times[a] < times[b]; });
+  std::vector<double> st(ntimes), cnt;
+  std::vector<int64_t> gp(ntimes + 1, 0), mp(1, 0);
+  std::vector<int32_t> mem;
+  for (int ii = 0; ii < ntimes; ++ii) {
+    int i = order[ii];
+    st[ii] = times[i];
+    for (int64_t g = group_ptr[i]; g < group_ptr[i + 1]; ++g) {
+      cnt.push_back(counts[g]);
+      for (int64_t q = member_ptr[g]; q < member_ptr[g + 1]; ++q) mem.push_back(members[q]);
+      mp.push_back((int64_t)mem.size());
+    }
+    gp[ii + 1] = (int64_t)cnt.size();
+  }
+  if (mem.empty()) mem.push_back(0);
+  if (cnt.empty()) cnt.push_back(0.0);
+  std::vector<float> r32(n);
+  for (int64_t i = 0; i < n; ++i) r32[i] = (float)rho0[i];
+
+  auto* o = new mjp_obs();
+  o->n = n;
+  o->ntimes = ntimes;
+  o->G = (int)G;
+  int rc = 0;
+  if ((rc = o->d_times.ensure(sizeof(double) * ntimes)) || (rc = o->d_gptr.ensure(sizeof(int64_t) * gp.size())) ||
+      (rc = o->d_counts.ensure(sizeof(double) * cnt.size())) || (rc = o->d_mptr.ensure(sizeof(int64_t) * mp.size())) ||
+      (rc = o->d_members.ensure(sizeof(int32_t) * mem.size())) || (rc = o->d_rho64.ensure(sizeof(double) * n)) ||
+      (rc = o->d_rho32.ensure(sizeof(float) * n))) {
+    delete o;
+    return rc;
+  }
+  auto up = [](DevBuf& b, const void* src, size_t bytes) { return cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice); };
+  if (up(o->d_times, st.data(), sizeof(double) * ntimes) != cudaSuccess ||
+      up(o->d_gptr, gp.data(), sizeof(int64_t) * gp.size()) != cudaSuccess ||
+      up(o->d_counts, cnt.data(), sizeof(double) * cnt.size()) != cudaSuccess ||
+      up(o->d_mptr, mp.data(), sizeof(int64_t) * mp.size()) != cudaSuccess ||
+      up(o->d_members, mem.data(), sizeof(int32_t) * mem.size()) != cudaSuccess ||
+      up(o->d_rho64, rho0, sizeof(double) * n) != cudaSuccess ||
+      up(o->d_rho32, r32.data(), sizeof(float) * n) != cudaSuccess) {
+    cudaGetLastError();
+    delete o;
+    return fail(MJP_ERR_CUDA, "copying observations to the device failed");
+  }
+  *out = o;
+  return MJP_OK;
+}
+
+void mjp_obs_destroy(mjp_obs* obs) { delete obs; }
+
+int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double* out, int where,
+           int trunc_mode, double tol, void* stream) {
+  if (!m || !obs || !out) return fail(MJP_ERR_ARG, "NULL argument");
+  if (B < 1) return fail(MJP_ERR_ARG, "B must be >= 1");
+  if (where != MJP_PTR_HOST && where != MJP_PTR_DEVICE) return fail(MJP_ERR_ARG, "where must be MJP_PTR_HOST or MJP_PTR_DEVICE");
+  if (obs->n != m->N) return fail(MJP_ERR_ARG, "observations were built for a different state space");
+  if (trunc_mode != MJP_TRUNC_PAPER && trunc_mode != MJP_TRUNC_TOL) return fail(MJP_ERR_ARG, "unknown truncation mode");
+  if (trunc_mode == MJP_TRUNC_TOL && !(tol >= 1e-20 && tol < 0.5)) return fail(MJP_ERR_ARG, "tol must be in [1e-20, 0.5)");
+  if (m->kind == MJP_CSR) return fail(MJP_ERR_UNSUPPORTED, "CSR loglik not built in this version");
+  if (!theta) return fail(MJP_ERR_ARG, "theta is NULL");
+  const int ntheta = ntheta_of(m->kind);
+  if (where == MJP_PTR_HOST)
+    for (int b = 0; b < B; ++b)
+      if (!finite_nonneg(theta + (int64_t)b * ntheta, ntheta)) return fail(MJP_ERR_ARG, "rates must be finite and >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nt = obs->ntimes;
+  int C, T;
+  int64_t slab;
+  int rc = stencil_config(m, 1, nt, obs->G, &C, &T, &slab);
+  if (rc) return rc;
+  if ((rc = ensure_status(m))) return rc;
+  if ((rc = m->d_win.ensure(sizeof(Win) * (size_t)nt * B))) return rc;
+  if ((rc = m->d_info.ensure(sizeof(JobInfo) * (size_t)B))) return rc;
+  const double* d_theta = theta;
+  double* d_out = out;
+  if (where == MJP_PTR_HOST) {
+    if ((rc = m->d_theta.ensure(sizeof(double) * (size_t)B * ntheta))) return rc;
+    if ((rc = m->d_ll.ensure(sizeof(double) * (size_t)B))) return rc;
+    MJP_CUDA(cudaMemcpyAsync(m->d_theta.p, theta, sizeof(double) * (size_t)B * ntheta, cudaMemcpyHostToDevice, s));
+    d_theta = m->d_theta.as<double>();
+    d_out = m->d_ll.as<double>();
+  }
+  PlanParams pp = {};
+  pp.kind = m->kind; pp.M = (int32_t)m->M; pp.P = (int32_t)m->P; pp.N = m->N;
+  pp.ntheta = ntheta; pp.theta = d_theta; pp.B = B;
+  pp.ntimes = nt; pp.times = obs->d_times.as<double>();
+  pp.trunc_mode = trunc_mode; pp.tol = tol; pp.omega_factor = 1.1; pp.omega_fixed = -1.0;
+  pp.kcap = m->kcap; pp.win = m->d_win.as<Win>(); pp.info = m->d_info.as<JobInfo>();
+  pp.status = m->d_status.as<int>();
+  MJP_CUDA(launch_plan(pp, s));
+
+  ChainParams cp = {};
+  cp.M = (int32_t)m->M; cp.P = (int32_t)m->P; cp.N = m->N;
+  cp.ntheta = ntheta; cp.theta = d_theta; cp.B = B; cp.ntimes = nt;
+  cp.orig = nullptr; cp.win = pp.win; cp.info = pp.info;
+  cp.rho0 = (m->precision == MJP_FP64) ? obs->d_rho64.p : obs->d_rho32.p;
+  cp.gptr = obs->d_gptr.as<int64_t>(); cp.counts = obs->d_counts.as<double>();
+  cp.mptr = obs->d_mptr.as<int64_t>(); cp.members = obs->d_members.as<int32_t>();
+  cp.G = obs->G; cp.ll = d_out;
+  cp.renorm = (m->precision == MJP_FP32) ? m->renorm : 0;
+  cp.slab = slab; cp.status = pp.status;
+  MJP_CUDA(launch_chain_stencil(m->kind, m->precision, 1, cp, C, T, s));
+  if (where == MJP_PTR_HOST) {
+    MJP_CUDA(cudaMemcpyAsync(out, d_out, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    return rate_model_check(m, stream);
+  }
+  return MJP_OK;
+}
+
+}  // extern "C"

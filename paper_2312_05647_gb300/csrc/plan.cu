@@ -1,0 +1,246 @@
+// plan.cu -- the FP64 planner: Omega, truncation index K and Poisson weight
+// window of every (instance, time) pair (Eq. B_def, Algorithm 2).
+//
+// One CTA per instance.  Omega = 1.1 max_n e_n is a block max-reduction over
+// the matrix-free exit rates (stencil models) or taken from the model (CSR).
+// Each warp then plans one time: K = floor(x + 6 sqrt x) + 1 with x = Omega t
+// computed with exactly the roundings of Algorithm 2 (no fused multiply-add),
+// and the Poisson weights around the mode m = floor(x) as ratios to w_m = 1,
+// formed by warp-shuffle inclusive product scans of x/k (upwards) and
+// (k+1)/x (downwards).  No exp(-x) is ever formed, so nothing underflows; the
+// window sum W normalises the weights, and the tail mass beyond K is summed
+// explicitly (equal to 1 - sum_{k<=K} P_k, Algorithm 2's last line).
+#include "internal.cuh"
+
+namespace mjp {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double warp_incl_prod(double v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double t = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v = __dmul_rn(v, t);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_incl_sum(double v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double t = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+struct Kahan {
+  double s = 0.0, c = 0.0;
+  __device__ void add(double v) {
+    double y = v - c;
+    double t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+// Exit rate e_n = sum_m lambda_nm of a stencil model, summed in ascending
+// target order (the column order of the rate matrix row) so that Omega is
+// bit-identical to a row sum over a CSR with sorted columns.
+__device__ double exit_rate(int kind, int64_t M, int64_t P, int64_t n, const double* th) {
+  double e = 0.0;
+  if (kind == MJP_BD1D) {  // Eq. BD_def
+    if (n >= 1) e = __dadd_rn(e, __dmul_rn(th[1], (double)n));
+    if (n + 1 < M) e = __dadd_rn(e, th[0]);
+  } else if (kind == MJP_TWOSTATE) {  // Eq. Gene_def, sigma = 0 active
+    int64_t sg = n / M, nr = n - sg * M;
+    if (sg == 0) {
+      if (nr >= 1) e = __dadd_rn(e, __dmul_rn(th[1], (double)nr));
+      if (nr + 1 < M) e = __dadd_rn(e, th[0]);
+      e = __dadd_rn(e, th[3]);
+    } else {
+      e = __dadd_rn(e, th[2]);
+      if (nr >= 1) e = __dadd_rn(e, __dmul_rn(th[1], (double)nr));
+    }
+  } else {  // MRNA_PROT2D: targets n-M, n-1, n+1, n+M
+    int64_t p = n / M, m = n - p * M;
+    if (p >= 1) e = __dadd_rn(e, __dmul_rn(th[3], (double)p));
+    if (m >= 1) e = __dadd_rn(e, __dmul_rn(th[1], (double)m));
+    if (m + 1 < M) e = __dadd_rn(e, th[0]);
+    if (p + 1 < P && m >= 1) e = __dadd_rn(e, __dmul_rn(th[2], (double)m));
+  }
+  return e;
+}
+
+__device__ void set_status(int* st, int code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+// Plan one time on one warp.
+__device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst, int lane) {
+  Win r;
+  double x = __dmul_rn(omega, t);
+  r.x = x;
+  if (x == 0.0) {  // t = 0 or no transitions: rho*(t) = rho0
+    r.L = 0;
+    r.K = (p.trunc_mode == MJP_TRUNC_PAPER) ? 1 : 0;
+    r.PL = 1.0;
+    r.tail = 0.0;
+    if (lane == 0) *dst = r;
+    return;
+  }
+  double s = __dsqrt_rn(x);
+  double kstar = __dadd_rn(x, __dmul_rn(6.0, s));  // Omega t + 6 sqrt(Omega t)
+  if (!(kstar + 1.0 <= (double)p.kcap)) {  // also catches inf/NaN; nothing loops
+    if (lane == 0) {
+      set_status(p.status, kStatusKcap);
+      r.L = 0; r.K = 0; r.PL = 1.0; r.tail = 0.0;
+      *dst = r;
+    }
+    return;
+  }
+  int64_t K = (int64_t)floor(kstar) + 1;  // Algorithm 2's last k
+  int64_t m = (int64_t)floor(x);
+  double lo = x - 10.0 * s;  // Poisson left tail below x - 10 sqrt x is < e^-50
+  int64_t L = lo > 0.0 ? (int64_t)floor(lo) : 0;
+  int64_t R = (int64_t)floor(x + 10.0 * s) + 10;
+
+  // Upward from the mode: w_k = w_{k-1} x / k, w_m = 1.
+  Kahan sum, tailsum;
+  if (lane == 0) sum.add(1.0);
+  double carry = 1.0;
+  for (int64_t base = m + 1; base <= R; base += 32) {
+    int64_t k = base + lane;
+    double term = (k <= R) ? __ddiv_rn(x, (double)k) : 1.0;
+    double w = __dmul_rn(warp_incl_prod(term, lane), carry);
+    carry = __shfl_sync(kFull, w, 31);
+    if (k <= R) {
+      sum.add(w);
+      if (p.trunc_mode == MJP_TRUNC_PAPER && k > K) tailsum.add(w);
+    }
+  }
+  double wR = carry;
+  // Downward from the mode: w_k = w_{k+1} (k+1) / x.
+  double wL = (L == m) ? 1.0 : 0.0;
+  carry = 1.0;
+  for (int64_t base = m - 1; base >= L; base -= 32) {
+    int64_t k = base - lane;
+    double term = (k >= L) ? __ddiv_rn((double)(k + 1), x) : 1.0;
+    double w = __dmul_rn(warp_incl_prod(term, lane), carry);
+    carry = __shfl_sync(kFull, w, 31);
+    if (k >= L) sum.add(w);
+    if (k == L) wL = w;
+  }
+  double W = warp_sum(sum.s) - warp_sum(sum.c);
+  // wL sits in exactly one lane (or lane-uniformly 1.0 when L == m).
+  wL = (L == m) ? 1.0 : warp_sum(wL);
+
+  double tail;
+  if (p.trunc_mode == MJP_TRUNC_PAPER) {
+    tail = (warp_sum(tailsum.s) - warp_sum(tailsum.c)) / W;
+  } else {
+    // Smallest K with sum_{j>K} w_j <= tol W: walk down from R with suffix sums.
+    double thr = p.tol * W;
+    double S = 0.0;   // sum_{j > base}
+    double wnext = wR;  // w_{base+1} after the first chunk; starts as w_R for base = R-1
+    int64_t Kt = R;
+    bool found = false;
+    for (int64_t base = R - 1; base >= m && !found; base -= 32) {
+      int64_t k = base - lane;
+      bool valid = k >= m;
+      double term = valid ? __ddiv_rn((double)(k + 1), x) : 1.0;
+      double w = __dmul_rn(warp_incl_prod(term, lane), wnext);  // w_k
+      // S_k = sum_{j>k} w_j = S + w_{base+1} + ... + w_{k+1}; w_{base+1} = wnext.
+      double incl = warp_incl_sum(valid ? w : 0.0, lane);
+      double excl = incl - (valid ? w : 0.0);
+      double Sk = S + wnext + excl;
+      unsigned ok = __ballot_sync(kFull, valid && Sk <= thr);
+      unsigned vmask = __ballot_sync(kFull, valid);
+      if ((ok & vmask) != vmask) {
+        int j = __ffs(~ok) - 1;  // first failing lane: passing lanes form a prefix
+        Kt = base - j + 1;
+        found = true;
+      } else {
+        Kt = base - (__popc(vmask) - 1);
+      }
+      S = S + wnext + __shfl_sync(kFull, incl, 31) - __shfl_sync(kFull, valid ? w : 0.0, 31);
+      wnext = __shfl_sync(kFull, w, 31);
+    }
+    K = Kt;
+    // tail = sum_{j > K} w_j / W, recomputed upward from the mode for clarity.
+    Kahan ts;
+    carry = 1.0;
+    for (int64_t base = m + 1; base <= R; base += 32) {
+      int64_t k = base + lane;
+      double term = (k <= R) ? __ddiv_rn(x, (double)k) : 1.0;
+      double w = __dmul_rn(warp_incl_prod(term, lane), carry);
+      carry = __shfl_sync(kFull, w, 31);
+      if (k <= R && k > K) ts.add(w);
+    }
+    tail = (warp_sum(ts.s) - warp_sum(ts.c)) / W;
+  }
+  r.L = L;
+  r.K = K;
+  r.PL = wL / W;
+  r.tail = tail;
+  if (lane == 0) *dst = r;
+}
+
+__global__ void __launch_bounds__(256) plan_kernel(PlanParams p) {
+  const int job = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ double red[8];
+  __shared__ double s_omega;
+  double omega;
+  if (p.omega_fixed >= 0.0) {
+    omega = p.omega_fixed;
+  } else {
+    const double* th = p.theta + (int64_t)job * p.ntheta;
+    double mx = 0.0;
+    for (int64_t n = tid; n < p.N; n += blockDim.x) {
+      double e = exit_rate(p.kind, p.M, p.P, n, th);
+      mx = e > mx ? e : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double t = __shfl_xor_sync(kFull, mx, o);
+      mx = t > mx ? t : mx;
+    }
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = red[w] > v ? red[w] : v;
+      s_omega = (v > 0.0) ? __dmul_rn(p.omega_factor, v) : 0.0;
+    }
+    __syncthreads();
+    omega = s_omega;
+  }
+  Win* wj = p.win + (int64_t)job * p.ntimes;
+  for (int i = warp; i < p.ntimes; i += blockDim.x >> 5) plan_time(p, omega, p.times[i], wj + i, lane);
+  __syncthreads();
+  if (tid == 0) {
+    int64_t kmax = 0;
+    for (int i = 0; i < p.ntimes; ++i) kmax = wj[i].K > kmax ? wj[i].K : kmax;
+    p.info[job].omega = omega;
+    p.info[job].Kmax = kmax;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_plan(const PlanParams& p, cudaStream_t s) {
+  if (p.B <= 0) return cudaSuccess;
+  plan_kernel<<<p.B, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace mjp
