@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark: R-MJP log-likelihood evaluations per second on one GB300.
+
+Workload (synthetic, the mRNA/protein configuration): a 200 x 200 box of
+(mRNA, protein) counts (N = 40,000 states, matrix-free 5-point stencil),
+k_m = 20, gamma_m = 1, k_p = 5, gamma_p = 0.1, rho0 = delta(0, 0), 20
+log-spaced observation times in [0.1, 50], 100 Gillespie-simulated cells per
+time.  One step = the log-likelihood of a batch of B parameter vectors
+(theta jittered +-20%): planner (Omega, K, Poisson windows) + persistent
+chain kernel (FP32 chain, Kahan accumulation, FP64 weights), K up to ~83,000
+jumps per theta.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank evaluates its own
+batch (independent thetas, no collective on the data path: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "loglik evals/s & achieved GB/s vs peak; ESS/s surrogate-DA vs plain MCMC"
+WORKLOAD = "mrna_protein_200x200_20times_loglik_batch"
+FLOPS_PER_UPDATE = 10  # 5-point stencil: 5 multiply-adds per state and jump
+ALU_FP32_FMA_PER_CLK_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=152, help="thetas per step and GPU")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(rank: int, batch: int):
+    import synth
+    cfg = synth.mrna_protein()
+    snaps = synth.gillespie_snapshots(cfg["kind"], cfg["dims"], cfg["theta"], cfg["times"], 100, synth.rng(2, 0))
+    obs = synth.snapshot_obs(cfg["kind"], cfg["dims"], snaps)
+    thetas = synth.jitter(cfg["theta"], batch, 0.2, synth.rng(2, 1000 + rank))
+    return cfg, obs, thetas
+
+
+def kmax_of(theta, dims, tmax):
+    """Jumps of the shared chain for one theta: K at the last time (Algorithm 2)."""
+    import numpy as np
+    M, P = dims
+    km, gm, kp, gp = theta
+    m = np.arange(M)[None, :]
+    p = np.arange(P)[:, None]
+    e = gp * p + gm * m + np.where(m < M - 1, km, 0.0) + np.where(p < P - 1, kp * m, 0.0)
+    x = 1.1 * float(e.max()) * tmax
+    return int(math.floor(x + 6.0 * math.sqrt(x))) + 1
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _noop(x):
+    return x
+
+
+def _oracle_one(args):
+    theta, times, obs = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    import synth
+    cfg = synth.mrna_protein()
+    csr = oracle.build_model(cfg["kind"], cfg["dims"], theta)
+    return oracle.loglik(csr, cfg["rho0"], times, obs)
+
+
+def oracle_batch(thetas, times, obs, workers: int):
+    """Time the CPU oracle on len(thetas) log-likelihoods over `workers` processes."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        pool.map(_noop, range(workers))  # process start-up outside the timed region
+        t0 = time.perf_counter()
+        vals = pool.map(_oracle_one, [(th, times, obs) for th in thetas])
+        dt = time.perf_counter() - t0
+    return vals, dt
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2312_05647_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles():
+    """DRAM bytes per chain launch from the committed ncu summary, if it was
+    taken on the current kernel sources (else null)."""
+    p = os.path.join(ROOT, "profiles", "chain_mrna_protein_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    cfg, obs, thetas = workload(0, args.batch)
+    workers = min(cpu_cores(), 16)
+    sample = thetas[:workers]
+    for _ in range(args.warmup):
+        oracle_batch(sample, cfg["times"], obs, workers)
+    total = 0.0
+    for _ in range(args.steps):
+        _, dt = oracle_batch(sample, cfg["times"], obs, workers)
+        total += dt
+    value = args.steps * len(sample) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "loglik evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "thetas_per_step": len(sample), "states": 40000, "times": 20,
+                   "cells_per_time": 100},
+        "cpu_baseline": {"value": value, "unit": "loglik evals/s", "cores": workers, "kind": "oracle",
+                         "sample": f"{len(sample)} thetas per step, one per process, full 20-time loglik"},
+        "e2e": {"value": value, "unit": "loglik evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build() if rank == 0 or world == 1 else None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.barrier()
+        __graft_entry__.build()
+    import paper_2312_05647_gb300 as mjp
+
+    cfg, obs, thetas = workload(rank, args.batch)
+    B = len(thetas)
+    model = mjp.Model(cfg["kind"], cfg["dims"], cfg["theta"], mjp.FP32)
+    model.set_option(mjp.OPT_PROFILE, 1)
+    ob = mjp.Obs(40000, cfg["times"], obs, cfg["rho0"])
+    dev = torch.device("cuda", local)
+    theta_dev = torch.tensor(thetas, dtype=torch.float64, device=dev)
+    out = torch.empty(B, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        mjp.loglik(model, ob, theta_dev, out=out)
+    model.check()
+    sync_all()
+
+    # ---- device-resident timed region --------------------------------------
+    visible = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    clocks = Clocks(int(visible[local]) if len(visible) > local and visible[local].isdigit() else local)
+    clocks.start()
+    time.sleep(0.5)
+    step_ms, chain_ms, plan_ms = [], [], []
+    launches = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        sync_all()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mjp.loglik(model, ob, theta_dev, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        pm, cm = model.last_timing()
+        plan_ms.append(pm)
+        chain_ms.append(cm)
+        launches += 2
+    clk = clocks.stop()
+    model.check()
+    ll_dev = out.cpu().numpy()
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms_max = float(t.item())
+    value = world * B * args.steps / (total_ms_max / 1e3)
+
+    # ---- end to end through the public API (host theta in, host loglik out) -
+    pinned_theta = torch.tensor(thetas, dtype=torch.float64).pin_memory()
+    th_host = pinned_theta.numpy()
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        sync_all()
+        t0 = time.perf_counter()
+        ll_host = mjp.loglik(model, ob, th_host)
+        e2e_s += time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = world * B * args.steps / float(t.item())
+    assert np.array_equal(ll_host, ll_dev), "host and device calls disagree"
+
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel (the chain) -----------------------
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    updates = sum(kmax_of(th, cfg["dims"], float(cfg["times"].max())) for th in thetas) * 40000
+    flops = FLOPS_PER_UPDATE * updates
+    chain_avg_s = statistics.mean(chain_ms) / 1e3
+    max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * ALU_FP32_FMA_PER_CLK_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    achieved = flops / chain_avg_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic_from_profiles(), "kernel": "chain_kernel<float, MRNA_PROT2D, loglik>",
+            "peak_basis": f"{sms} SMs x 128 FP32 FMA/clk x 2 x {max_mhz:.0f} MHz (derived, no measured ALU peak)",
+            "flops_per_launch": flops, "chain_ms_avg": statistics.mean(chain_ms),
+            "plan_ms_avg": statistics.mean(plan_ms)}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        workers = min(cpu_cores(), 16)
+        vals, dt = oracle_batch(thetas[:workers], cfg["times"], obs, workers)
+        err = max(abs(a - b) for a, b in zip(vals, ll_dev[:workers]))
+        cpu = {"value": workers / dt, "unit": "loglik evals/s", "cores": workers, "kind": "oracle",
+               "sample": f"{workers} of the {B} thetas, one full 20-time loglik per process",
+               "max_abs_loglik_diff_vs_gpu": err}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "loglik evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "thetas_per_step": B, "states": 40000, "times": 20,
+                   "cells_per_time": 100, "theta_jitter": 0.2,
+                   "jumps_per_theta_mean": updates / 40000 / B, "chain": "fp32 + kahan, fp64 weights",
+                   "l2": "flushed (256 MB write) between steps"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "loglik evals/s", "h2d_bytes_per_step": int(thetas.nbytes),
+                "d2h_bytes_per_step": int(B * 8)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

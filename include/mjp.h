@@ -82,6 +82,7 @@ extern "C" {
 #define MJP_OPT_K_CAP 2         /* largest K accepted (default 2^26) */
 #define MJP_OPT_THREADS 3       /* threads per CTA for stencil chains (0 = automatic) */
 #define MJP_OPT_CLUSTER 4       /* CTAs per instance for stencil chains (0 = automatic; 1, 2, 4, 8, 16) */
+#define MJP_OPT_PROFILE 5       /* 1: record CUDA events around each kernel of a call (see rate_model_last_timing) */
 
 typedef struct mjp_model mjp_model;
 typedef struct mjp_obs mjp_obs;
@@ -180,6 +181,16 @@ void mjp_obs_destroy(mjp_obs* obs);
  */
 int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double* out, int where,
            int trunc_mode, double tol, void* stream);
+
+/*
+ * Device time of the kernels of the most recent expv_series/loglik call on
+ * this model, measured with CUDA events recorded on the call's stream around
+ * each kernel (needs MJP_OPT_PROFILE = 1 before the call).  Waits for the
+ * call to finish.  ms_plan: the planner kernel (Omega, K, weights);
+ * ms_chain: the jump-chain kernel.  Either pointer may be NULL.
+ * Errors: MJP_ERR_ARG (profiling off or no call yet), MJP_ERR_CUDA.
+ */
+int rate_model_last_timing(mjp_model* m, double* ms_plan, double* ms_chain);
 
 /*
  * Synchronise `stream` and report device-side errors recorded by earlier

@@ -13,8 +13,9 @@ import ctypes
 import numpy as np
 
 from . import capi
-from .capi import (BD1D, CSR, FP32, FP64, MRNA_PROT2D, OPT_CLUSTER, OPT_K_CAP, OPT_RENORM_PERIOD,
-                   OPT_THREADS, PTR_DEVICE, PTR_HOST, TRUNC_PAPER, TRUNC_TOL, TWOSTATE, MJPError)
+from .capi import (BD1D, CSR, FP32, FP64, MRNA_PROT2D, OPT_CLUSTER, OPT_K_CAP, OPT_PROFILE,
+                   OPT_RENORM_PERIOD, OPT_THREADS, PTR_DEVICE, PTR_HOST, TRUNC_PAPER, TRUNC_TOL, TWOSTATE,
+                   MJPError)
 
 __all__ = ["Model", "Obs", "loglik", "BD1D", "TWOSTATE", "MRNA_PROT2D", "CSR", "FP32", "FP64",
            "TRUNC_PAPER", "TRUNC_TOL", "MJPError"]
@@ -100,6 +101,12 @@ class Model:
 
     def check(self, stream=None):
         capi.check(capi.lib().rate_model_check(self._h, _stream_ptr(stream)))
+
+    def last_timing(self):
+        """(planner ms, chain ms) of the last call (needs OPT_PROFILE = 1)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        capi.check(capi.lib().rate_model_last_timing(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -20,7 +20,7 @@ BD1D, TWOSTATE, MRNA_PROT2D, CSR = 1, 2, 3, 4
 FP32, FP64 = 1, 2
 TRUNC_PAPER, TRUNC_TOL = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
-OPT_RENORM_PERIOD, OPT_K_CAP, OPT_THREADS, OPT_CLUSTER = 1, 2, 3, 4
+OPT_RENORM_PERIOD, OPT_K_CAP, OPT_THREADS, OPT_CLUSTER, OPT_PROFILE = 1, 2, 3, 4, 5
 
 # Every entry point of include/mjp.h: name -> (restype, argtypes).
 _vp = ctypes.c_void_p
@@ -46,6 +46,7 @@ SIGNATURES = {
     "rate_model_num_states": (ctypes.c_int64, [_vp]),
     "rate_model_destroy": (None, [_vp]),
     "rate_model_check": (ctypes.c_int, [_vp, _vp]),
+    "rate_model_last_timing": (ctypes.c_int, [_vp, _f64p, _f64p]),
     "expv_series": (ctypes.c_int, [_vp, _vp, _f64p, ctypes.c_int, _vp, ctypes.POINTER(SeriesInfo),
                                    ctypes.c_int, ctypes.c_double, _vp]),
     "mjp_obs_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_int, _f64p, _i64p, _f64p,

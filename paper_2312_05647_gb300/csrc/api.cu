@@ -87,11 +87,16 @@ struct mjp_model {
   int64_t kcap = (int64_t)1 << 26;
   int threads = 0;
   int cluster = 0;
+  int profile = 0;
+  bool timed = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   // workspace (scratch owned by the handle)
   DevBuf d_times, d_orig, d_win, d_info, d_theta, d_comp, d_status, d_ll;
   ~mjp_model() {
     d_times.release(); d_orig.release(); d_win.release(); d_info.release();
     d_theta.release(); d_comp.release(); d_status.release(); d_ll.release();
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
   }
 };
 
@@ -99,6 +104,7 @@ struct mjp_obs {
   int64_t n = 0;
   int ntimes = 0;
   int G = 0;
+  int nmem = 0;
   DevBuf d_times, d_gptr, d_counts, d_mptr, d_members, d_rho64, d_rho32;
   ~mjp_obs() {
     d_times.release(); d_gptr.release(); d_counts.release(); d_mptr.release();
@@ -117,18 +123,18 @@ int ensure_status(mjp_model* m) {
 }
 
 // Pick cluster size and threads for a stencil chain of this model.
-int stencil_config(mjp_model* m, int loglik_mode, int nt, int G, int* cluster, int* threads,
+int stencil_config(mjp_model* m, int loglik_mode, int nt, int G, int nmem, int* cluster, int* threads,
                    int64_t* slab) {
   const size_t kSmemMax = 227 * 1024;
   int C = m->cluster;
-  auto slab_of = [&](int c) {
-    int64_t s = (m->N + c - 1) / c;
-    return (s + 3) / 4 * 4;
+  auto smem_of = [&](int c) {
+    return chain_stencil_smem(m->kind, m->precision, loglik_mode, m->M, m->P,
+                              chain_stencil_slab(m->kind, m->M, m->P, c), nt, G, nmem);
   };
   if (C <= 0) {
     C = 0;
     for (int c = 1; c <= 16; c *= 2) {
-      if (chain_stencil_smem(m->precision, loglik_mode, slab_of(c), nt, G) <= kSmemMax) {
+      if (smem_of(c) <= kSmemMax) {
         C = c;
         break;
       }
@@ -136,12 +142,20 @@ int stencil_config(mjp_model* m, int loglik_mode, int nt, int G, int* cluster, i
     if (C == 0) return fail(MJP_ERR_UNSUPPORTED, "state space too large for an on-chip stencil chain");
   }
   if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16) return fail(MJP_ERR_ARG, "cluster must be 1, 2, 4, 8 or 16");
-  int64_t s = slab_of(C);
-  size_t smem = chain_stencil_smem(m->precision, loglik_mode, s, nt, G);
+  int64_t s = chain_stencil_slab(m->kind, m->M, m->P, C);
+  size_t smem = smem_of(C);
   if (smem > kSmemMax) return fail(MJP_ERR_UNSUPPORTED, "slab does not fit shared memory; raise the cluster size");
   int t = m->threads;
   if (t <= 0) {
-    int64_t want = (s + 1) / 2;
+    // One thread per column when a row fits the CTA, ~8+ states per thread.
+    int64_t W = (m->kind == MJP_BD1D) ? s : m->M;
+    int64_t rows = (m->kind == MJP_BD1D) ? 1 : s / m->M;
+    int64_t want;
+    if (W >= 1024) want = 1024;
+    else {
+      int64_t groups = std::max<int64_t>(1, std::min<int64_t>(rows / 8, 1024 / W));
+      want = W * groups;
+    }
     want = (want + 31) / 32 * 32;
     t = (int)std::min<int64_t>(1024, std::max<int64_t>(64, want));
   }
@@ -151,6 +165,16 @@ int stencil_config(mjp_model* m, int loglik_mode, int nt, int G, int* cluster, i
   *cluster = C;
   *threads = t;
   *slab = s;
+  return MJP_OK;
+}
+
+// Record profiling event i (0: before the planner, 1: before the chain,
+// 2: after the chain) when MJP_OPT_PROFILE is on.
+int mark(mjp_model* m, int i, cudaStream_t s) {
+  if (!m->profile) return MJP_OK;
+  if (!m->ev[i]) MJP_CUDA(cudaEventCreate(&m->ev[i]));
+  MJP_CUDA(cudaEventRecord(m->ev[i], s));
+  if (i == 2) m->timed = true;
   return MJP_OK;
 }
 
@@ -232,6 +256,11 @@ int rate_model_set_option(mjp_model* m, int option, int64_t value) {
       if (value != 0 && (value % 32 != 0 || value < 32 || value > 1024)) return fail(MJP_ERR_ARG, "threads must be 0 or a multiple of 32 in [32, 1024]");
       m->threads = (int)value;
       return MJP_OK;
+    case MJP_OPT_PROFILE:
+      if (value != 0 && value != 1) return fail(MJP_ERR_ARG, "profile must be 0 or 1");
+      m->profile = (int)value;
+      m->timed = false;
+      return MJP_OK;
     case MJP_OPT_CLUSTER:
       if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16) return fail(MJP_ERR_ARG, "cluster must be 0, 1, 2, 4, 8 or 16");
       m->cluster = (int)value;
@@ -244,6 +273,18 @@ int rate_model_set_option(mjp_model* m, int option, int64_t value) {
 int64_t rate_model_num_states(const mjp_model* m) { return m ? m->N : -1; }
 
 void rate_model_destroy(mjp_model* m) { delete m; }
+
+int rate_model_last_timing(mjp_model* m, double* ms_plan, double* ms_chain) {
+  if (!m) return fail(MJP_ERR_ARG, "NULL model");
+  if (!m->profile || !m->timed) return fail(MJP_ERR_ARG, "no profiled call (set MJP_OPT_PROFILE first)");
+  MJP_CUDA(cudaEventSynchronize(m->ev[2]));
+  float a = 0.f, b = 0.f;
+  MJP_CUDA(cudaEventElapsedTime(&a, m->ev[0], m->ev[1]));
+  MJP_CUDA(cudaEventElapsedTime(&b, m->ev[1], m->ev[2]));
+  if (ms_plan) *ms_plan = a;
+  if (ms_chain) *ms_chain = b;
+  return MJP_OK;
+}
 
 int rate_model_check(mjp_model* m, void* stream) {
   if (!m) return fail(MJP_ERR_ARG, "NULL model");
@@ -274,7 +315,7 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
 
   int C, T;
   int64_t slab;
-  int rc = stencil_config(m, 0, nt, 0, &C, &T, &slab);
+  int rc = stencil_config(m, 0, nt, 0, 0, &C, &T, &slab);
   if (rc) return rc;
   if ((rc = ensure_status(m))) return rc;
   if ((rc = m->d_times.ensure(sizeof(double) * nt))) return rc;
@@ -294,7 +335,9 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
   pp.trunc_mode = trunc_mode; pp.tol = tol; pp.omega_factor = 1.1; pp.omega_fixed = -1.0;
   pp.kcap = m->kcap; pp.win = m->d_win.as<Win>(); pp.info = m->d_info.as<JobInfo>();
   pp.status = m->d_status.as<int>();
+  if ((rc = mark(m, 0, s))) return rc;
   MJP_CUDA(launch_plan(pp, s));
+  if ((rc = mark(m, 1, s))) return rc;
 
   ChainParams cp = {};
   cp.M = (int32_t)m->M; cp.P = (int32_t)m->P; cp.N = m->N;
@@ -304,6 +347,7 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
   cp.renorm = (m->precision == MJP_FP32) ? m->renorm : 0;
   cp.slab = slab; cp.status = pp.status;
   MJP_CUDA(launch_chain_stencil(m->kind, m->precision, 0, cp, C, T, s));
+  if ((rc = mark(m, 2, s))) return rc;
 
   if (info) {
     std::vector<Win> w(nt);
@@ -371,6 +415,7 @@ int mjp_obs_create(mjp_obs** out, int64_t n, int ntimes, const double* times,
   o->n = n;
   o->ntimes = ntimes;
   o->G = (int)G;
+  o->nmem = (int)(mp.back());
   int rc = 0;
   if ((rc = o->d_times.ensure(sizeof(double) * ntimes)) || (rc = o->d_gptr.ensure(sizeof(int64_t) * gp.size())) ||
       (rc = o->d_counts.ensure(sizeof(double) * cnt.size())) || (rc = o->d_mptr.ensure(sizeof(int64_t) * mp.size())) ||
@@ -415,7 +460,7 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   const int nt = obs->ntimes;
   int C, T;
   int64_t slab;
-  int rc = stencil_config(m, 1, nt, obs->G, &C, &T, &slab);
+  int rc = stencil_config(m, 1, nt, obs->G, obs->nmem, &C, &T, &slab);
   if (rc) return rc;
   if ((rc = ensure_status(m))) return rc;
   if ((rc = m->d_win.ensure(sizeof(Win) * (size_t)nt * B))) return rc;
@@ -436,7 +481,9 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   pp.trunc_mode = trunc_mode; pp.tol = tol; pp.omega_factor = 1.1; pp.omega_fixed = -1.0;
   pp.kcap = m->kcap; pp.win = m->d_win.as<Win>(); pp.info = m->d_info.as<JobInfo>();
   pp.status = m->d_status.as<int>();
+  if ((rc = mark(m, 0, s))) return rc;
   MJP_CUDA(launch_plan(pp, s));
+  if ((rc = mark(m, 1, s))) return rc;
 
   ChainParams cp = {};
   cp.M = (int32_t)m->M; cp.P = (int32_t)m->P; cp.N = m->N;
@@ -445,10 +492,11 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   cp.rho0 = (m->precision == MJP_FP64) ? obs->d_rho64.p : obs->d_rho32.p;
   cp.gptr = obs->d_gptr.as<int64_t>(); cp.counts = obs->d_counts.as<double>();
   cp.mptr = obs->d_mptr.as<int64_t>(); cp.members = obs->d_members.as<int32_t>();
-  cp.G = obs->G; cp.ll = d_out;
+  cp.G = obs->G; cp.nmem = obs->nmem; cp.ll = d_out;
   cp.renorm = (m->precision == MJP_FP32) ? m->renorm : 0;
   cp.slab = slab; cp.status = pp.status;
   MJP_CUDA(launch_chain_stencil(m->kind, m->precision, 1, cp, C, T, s));
+  if ((rc = mark(m, 2, s))) return rc;
   if (where == MJP_PTR_HOST) {
     MJP_CUDA(cudaMemcpyAsync(out, d_out, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
     return rate_model_check(m, stream);

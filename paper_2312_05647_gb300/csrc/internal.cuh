@@ -82,9 +82,10 @@ struct ChainParams {
   const int64_t* mptr;     // device, G + 1
   const int32_t* members;  // device
   int G;
+  int nmem;                // members in all groups
   double* ll;              // device, B
   int renorm;              // period in jumps (0 = off)
-  int64_t slab;            // states per CTA of the cluster
+  int64_t slab;            // states per CTA of the cluster (whole rows for 2-D models)
   int* status;
 };
 
@@ -95,7 +96,9 @@ namespace mjp {
 cudaError_t launch_plan(const PlanParams& p, cudaStream_t s);
 cudaError_t launch_chain_stencil(int kind, int precision, int loglik_mode, const ChainParams& p,
                                  int cluster, int threads, cudaStream_t s);
-size_t chain_stencil_smem(int precision, int loglik_mode, int64_t slab, int ntimes, int G);
+int64_t chain_stencil_slab(int kind, int64_t M, int64_t P, int cluster);
+size_t chain_stencil_smem(int kind, int precision, int loglik_mode, int64_t M, int64_t P, int64_t slab,
+                          int ntimes, int G, int nmem);
 int chain_stencil_max_cluster_blocks(int kind, int precision, int loglik_mode, int cluster,
                                      int threads, size_t smem);
 }  // namespace mjp
