@@ -80,7 +80,7 @@ extern "C" {
 /* ---- model options (rate_model_set_option) ----------------------------- */
 #define MJP_OPT_RENORM_PERIOD 1 /* FP32 chains: rescale rho to its initial mass every r jumps (0 = off, default) */
 #define MJP_OPT_K_CAP 2         /* largest K accepted (default 2^26) */
-#define MJP_OPT_THREADS 3       /* threads per CTA for stencil chains (0 = automatic) */
+#define MJP_OPT_THREADS 3       /* threads per CTA for stencil chains, one warp of which forms the weights (0 = automatic; else a multiple of 32 in [64, 1024]) */
 #define MJP_OPT_CLUSTER 4       /* CTAs per instance for stencil chains (0 = automatic; 1, 2, 4, 8, 16) */
 #define MJP_OPT_PROFILE 5       /* 1: record CUDA events around each kernel of a call (see rate_model_last_timing) */
 

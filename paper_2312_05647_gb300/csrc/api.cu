@@ -147,19 +147,28 @@ int stencil_config(mjp_model* m, int loglik_mode, int nt, int G, int nmem, int* 
   if (smem > kSmemMax) return fail(MJP_ERR_UNSUPPORTED, "slab does not fit shared memory; raise the cluster size");
   int t = m->threads;
   if (t <= 0) {
-    // One thread per column when a row fits the CTA, ~8+ states per thread.
+    // One thread per column when a row fits the CTA, ~8+ states per thread,
+    // plus one warp that forms the Poisson weights.
+    // Two-dimensional models: runs of about 20 pair-rows per thread measured
+    // best on GB300 (fewer threads hide less latency, more add overhead).
     int64_t W = (m->kind == MJP_BD1D) ? s : m->M;
     int64_t rows = (m->kind == MJP_BD1D) ? 1 : s / m->M;
     int64_t want;
-    if (W >= 1024) want = 1024;
+    if (W >= 992) want = 992;
     else {
-      int64_t groups = std::max<int64_t>(1, std::min<int64_t>(rows / 8, 1024 / W));
+      int64_t pair_rows = (rows + 1) / 2;
+      int64_t groups = std::max<int64_t>(1, std::min<int64_t>((pair_rows + 19) / 20, 992 / W));
       want = W * groups;
     }
-    want = (want + 31) / 32 * 32;
+    want = (want + 31) / 32 * 32 + 32;
     t = (int)std::min<int64_t>(1024, std::max<int64_t>(64, want));
   }
-  if (t % 32 != 0 || t < 32 || t > 1024) return fail(MJP_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
+  if (t % 32 != 0 || t < 64 || t > 1024) return fail(MJP_ERR_ARG, "threads must be a multiple of 32 in [64, 1024]");
+  // Two-dimensional models give each stencil thread one column.
+  if (m->kind != MJP_BD1D && m->M > t - 32) {
+    if (m->M > 992) return fail(MJP_ERR_UNSUPPORTED, "rows longer than 992 states are not supported");
+    return fail(MJP_ERR_ARG, "threads - 32 must be >= the row length M");
+  }
   int nclusters = chain_stencil_max_cluster_blocks(m->kind, m->precision, loglik_mode, C, t, smem);
   if (nclusters <= 0) return fail(MJP_ERR_UNSUPPORTED, "stencil chain configuration cannot be made resident");
   *cluster = C;
@@ -253,7 +262,7 @@ int rate_model_set_option(mjp_model* m, int option, int64_t value) {
       m->kcap = value;
       return MJP_OK;
     case MJP_OPT_THREADS:
-      if (value != 0 && (value % 32 != 0 || value < 32 || value > 1024)) return fail(MJP_ERR_ARG, "threads must be 0 or a multiple of 32 in [32, 1024]");
+      if (value != 0 && (value % 32 != 0 || value < 64 || value > 1024)) return fail(MJP_ERR_ARG, "threads must be 0 or a multiple of 32 in [64, 1024]");
       m->threads = (int)value;
       return MJP_OK;
     case MJP_OPT_PROFILE:

@@ -51,12 +51,19 @@ __device__ __forceinline__ void cluster_wait() {
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Local tile geometry of one CTA: a padded (rows + 2) x (width + 2) array.
+// Local tile geometry of one CTA.
+//  - birth-death chain: one row of W owned columns plus one zero pad cell on
+//    each side;
+//  - two-dimensional models: owned rows [p0, p1) stored as row PAIRS
+//    (rows 2j and 2j+1 of a column side by side, i.e. a float2/double2 per
+//    column), with a pad pair-row below and above and a pad column on each
+//    side, so a thread updates two states with packed arithmetic.
 struct Geo {
   int p0, p1, m0, m1;  // owned rows [p0, p1) and columns [m0, m1)
   int W, H;            // width and height of the owned block
-  int Wp;              // padded row stride (W + 2)
-  int size;            // padded elements ((H + 2) * Wp)
+  int Hp;              // owned pair-rows (2-D)
+  int Wp;              // padded row stride in cells (W + 2)
+  int size;            // padded tile in scalar elements
 };
 
 __host__ __device__ inline Geo geometry(int kind, int M, int P, int N, int slab, int rank) {
@@ -66,22 +73,21 @@ __host__ __device__ inline Geo geometry(int kind, int M, int P, int N, int slab,
   if (n1 < n0) n1 = n0;
   if (kind == MJP_BD1D) {
     g.p0 = 0; g.p1 = 1; g.m0 = n0; g.m1 = n1;
-  } else {  // slab is a whole number of rows
+  } else {  // slab is an even number of whole rows
     g.p0 = n0 / M; g.p1 = (n1 + M - 1) / M; g.m0 = 0; g.m1 = M;
     if (g.p1 < g.p0) g.p1 = g.p0;
   }
   g.W = g.m1 - g.m0;
   g.H = g.p1 - g.p0;
+  g.Hp = (g.H + 1) / 2;
   g.Wp = g.W + 2;
-  // The birth-death chain has no vertical neighbours: no pad rows.
-  g.size = (kind == MJP_BD1D) ? g.Wp : (g.H + 2) * g.Wp;
+  g.size = (kind == MJP_BD1D) ? g.Wp : (g.Hp + 2) * g.Wp * 2;
   return g;
 }
 
-// Padded-row offset of owned row 0 in the local tile.
-template <int KIND>
-__device__ __forceinline__ int row_off() {
-  return KIND == MJP_BD1D ? 0 : 1;
+// Scalar element of owned local row r, local column c of a 2-D tile.
+__host__ __device__ inline int elem2d(const Geo& g, int r, int c) {
+  return (((r >> 1) + 1) * g.Wp + c + 1) * 2 + (r & 1);
 }
 
 // Largest padded tile over the ranks of a cluster (rank 0 is never smaller).
@@ -91,7 +97,7 @@ __host__ __device__ inline int tile_elems(int kind, int M, int P, int N, int sla
 }
 
 struct Smem {
-  size_t buf1, tx, tPL, ttail, tL, tK, torig, pw, red, memloc, acc_s, acc_c, total;
+  size_t buf1, tx, tPL, ttail, tL, tK, torig, pw, red, memloc, gptr, mptr, acc_s, acc_c, total;
 };
 
 __host__ __device__ inline Smem smem_layout(size_t elt, int tile, int nt, int G, int nmem, bool ll) {
@@ -109,6 +115,10 @@ __host__ __device__ inline Smem smem_layout(size_t elt, int tile, int nt, int G,
   s.red = o; o += 8 * 2 * 33;
   s.memloc = o;
   if (ll) o += align_up(4 * (size_t)nmem, 8);
+  s.gptr = o;
+  if (ll) o += align_up(4 * (size_t)(nt + 1), 8);
+  s.mptr = o;
+  if (ll) o += align_up(4 * (size_t)(G + 1), 8);
   s.acc_s = o;
   if (ll) {
     o += align_up(elt * (size_t)G, 8);
@@ -138,6 +148,37 @@ __device__ __forceinline__ Coef<T> make_coef(const double* th, double omega) {
   return k;
 }
 
+// Fixed-order arithmetic (no contraction): every thread layout and cluster
+// shape produces bit-identical chains.
+__device__ __forceinline__ float f_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double f_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float f_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double f_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float f_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double f_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float f_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double f_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Pairs of chain values (two rows of one column).  FP32 pairs use the packed
+// sm_100+ FP32x2 instructions; FP64 pairs are two scalar operations.
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+__device__ __forceinline__ float2 v_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 v_mul(double2 a, double2 b) {
+  return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 v_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 v_add(double2 a, double2 b) {
+  return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 v_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 v_fma(double2 a, double2 b, double2 c) {
+  return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 v_make(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 v_make(double a, double b) { return make_double2(a, b); }
+
 template <typename T, int KIND, bool LL>
 __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -153,7 +194,12 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   const int tile = tile_elems(KIND, M, P, N, S);
 
   const Smem L = smem_layout(sizeof(T), tile, nt, p.G, p.nmem, LL);
-  T* buf[2] = {reinterpret_cast<T*>(smem), reinterpret_cast<T*>(smem + L.buf1)};
+  // Tile buffers are always formed from the __shared__ base (never through a
+  // runtime-indexed pointer array), so accesses compile to shared-memory
+  // instructions with 32-bit addressing.
+  const unsigned buf_off[2] = {0u, (unsigned)L.buf1};
+  T* const buf0 = reinterpret_cast<T*>(smem);
+  T* const buf1 = reinterpret_cast<T*>(smem + L.buf1);
   double* t_x = reinterpret_cast<double*>(smem + L.tx);
   double* t_PL = reinterpret_cast<double*>(smem + L.tPL);
   double* t_tail = reinterpret_cast<double*>(smem + L.ttail);
@@ -163,25 +209,30 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   double* pw = reinterpret_cast<double*>(smem + L.pw);   // [2][nt]
   double* red = reinterpret_cast<double*>(smem + L.red);  // [2][33]
   int* memloc = reinterpret_cast<int*>(smem + L.memloc);
+  int* s_gptr = reinterpret_cast<int*>(smem + L.gptr);  // group ranges per time
+  int* s_mptr = reinterpret_cast<int*>(smem + L.mptr);  // member ranges per group
   T* acc_s = reinterpret_cast<T*>(smem + L.acc_s);
   float* acc_c = reinterpret_cast<float*>(smem + L.acc_c);
 
-  // Remote tiles of the neighbouring CTAs (same layout, same offsets).
-  const T* up_rem[2] = {nullptr, nullptr};
-  const T* dn_rem[2] = {nullptr, nullptr};
-  int up_W = 0, dn_W = 0, dn_H = 0;
+  // Pad cells of the neighbouring CTAs that receive this CTA's boundary
+  // values after every jump (pushed through distributed shared memory), so
+  // that every stencil read is a local one.
+  T* push_dn[2] = {nullptr, nullptr};  // rank-1: top pad pair-row (2-D) / right pad cell (1-D)
+  T* push_up[2] = {nullptr, nullptr};  // rank+1: bottom pad pair-row (2-D) / left pad cell (1-D)
   if (C > 1) {
-    if (rank + 1 < C) {
-      up_rem[0] = cluster.map_shared_rank(buf[0], rank + 1);
-      up_rem[1] = cluster.map_shared_rank(buf[1], rank + 1);
-      up_W = geometry(KIND, M, P, N, S, rank + 1).Wp;
-    }
     if (rank > 0) {
-      dn_rem[0] = cluster.map_shared_rank(buf[0], rank - 1);
-      dn_rem[1] = cluster.map_shared_rank(buf[1], rank - 1);
       Geo gd = geometry(KIND, M, P, N, S, rank - 1);
-      dn_W = gd.Wp;
-      dn_H = gd.H;
+      int off = (KIND == MJP_BD1D) ? gd.Wp - 1 : (gd.Hp + 1) * gd.Wp * 2;
+      push_dn[0] = cluster.map_shared_rank(buf0, rank - 1) + off;
+      push_dn[1] = cluster.map_shared_rank(buf1, rank - 1) + off;
+    }
+    if (rank + 1 < C) {
+      Geo gu = geometry(KIND, M, P, N, S, rank + 1);
+      if (gu.W > 0 && gu.H > 0)
+      {
+        push_up[0] = cluster.map_shared_rank(buf0, rank + 1);
+        push_up[1] = cluster.map_shared_rank(buf1, rank + 1);
+      }
     }
   }
 
@@ -201,30 +252,47 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   const int64_t Kmax = p.info[job].Kmax;
   const Coef<T> co = make_coef<T, KIND>(p.theta + (int64_t)job * p.ntheta, omega);
   const T* rho0 = reinterpret_cast<const T*>(p.rho0);
-  for (int j = tid; j < 2 * tile; j += nthr) (j < tile ? buf[0] : buf[1])[j < tile ? j : j - tile] = (T)0;
+  for (int j = tid; j < tile; j += nthr) {
+    buf0[j] = (T)0;
+    buf1[j] = (T)0;
+  }
   __syncthreads();
   T msum = (T)0;
   for (int j = tid; j < g.W * g.H; j += nthr) {
     int r = j / g.W, c = j - r * g.W;
-    int gi = (g.p0 + r) * M + g.m0 + c;
-    T v = rho0[gi];
-    buf[0][(r + row_off<KIND>()) * g.Wp + c + 1] = v;
+    T v = rho0[(g.p0 + r) * M + g.m0 + c];
+    buf0[KIND == MJP_BD1D ? c + 1 : elem2d(g, r, c)] = v;
     msum += v;
+  }
+  // Halo of rho0 from global memory (later jumps receive it by push): the
+  // row below a 2-D slab is the odd half of the bottom pad pair, the row above
+  // the even half of the top pad pair.
+  if (KIND == MJP_BD1D) {
+    if (tid == 0 && g.W > 0 && g.m0 >= 1) buf0[0] = rho0[g.m0 - 1];
+    if (tid == 0 && g.W > 0 && g.m1 < M) buf0[g.Wp - 1] = rho0[g.m1];
+  } else if (g.H > 0) {
+    for (int c = tid; c < g.W; c += nthr) {
+      if (g.p0 >= 1) buf0[(c + 1) * 2 + 1] = rho0[(g.p0 - 1) * M + c];
+      if (g.p1 < P) buf0[((g.Hp + 1) * g.Wp + c + 1) * 2] = rho0[g.p1 * M + c];
+    }
   }
   if (LL) {
     for (int q = tid; q < p.nmem; q += nthr) {
       int s = p.members[q];
       int ps = s / M, ms = s - ps * M;
       bool mine = ps >= g.p0 && ps < g.p1 && ms >= g.m0 && ms < g.m1;
-      memloc[q] = mine ? (ps - g.p0 + row_off<KIND>()) * g.Wp + (ms - g.m0) + 1 : -1;
+      memloc[q] = !mine ? -1 : (KIND == MJP_BD1D ? ms - g.m0 + 1 : elem2d(g, ps - g.p0, ms));
     }
     for (int q = tid; q < p.G; q += nthr) {
       acc_s[q] = (T)0;
       if (sizeof(T) == 4) acc_c[q] = 0.0f;
     }
+    for (int q = tid; q <= p.G; q += nthr) s_mptr[q] = (int)p.mptr[q];
+    for (int q = tid; q <= nt; q += nthr) s_gptr[q] = (int)p.gptr[q];
   }
+  const bool rn = p.renorm > 0;
   double mass0 = 1.0;
-  if (p.renorm > 0) {
+  if (rn) {
     double v = (double)msum;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -232,14 +300,15 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   }
   if (C > 1) cluster.sync();
   else __syncthreads();
-  if (p.renorm > 0) {
+  auto cluster_total = [&](const double* r0) {
     double tot = 0.0;
     for (int r = 0; r < C; ++r) {
-      const double* rr = (C == 1) ? red : cluster.map_shared_rank(red, r);
+      const double* rr = (C == 1) ? r0 : cluster.map_shared_rank(r0, r);
       for (int w = 0; w < nwarps; ++w) tot += rr[w];
     }
-    mass0 = tot;
-  }
+    return tot;
+  };
+  if (rn) mass0 = cluster_total(red);
 
   // Active times of jump k form a contiguous range [lo, hi] (times sorted).
   int lo = 0, hi = -1;
@@ -249,215 +318,243 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   };
   advance(0, lo, hi);
 
-  // LOGLIK: acc_g += w_i * sum_{s in g} rho_k[s] over this CTA's states.
-  auto group_accumulate = [&](const T* cur, int l, int h, int64_t k, const double* wts) {
+  // Thread layout: the last warp forms the Poisson weights (FP64, off the
+  // stencil's critical path); the other warps own columns and runs of rows.
+  const int nthr_c = nthr - 32;
+  const bool wwarp = warp == nwarps - 1;
+  const int TX = (KIND == MJP_BD1D) ? (g.W < nthr_c ? (g.W > 0 ? g.W : 1) : nthr_c) : (g.W > 0 ? g.W : 1);
+  const int TY = nthr_c / TX > 0 ? nthr_c / TX : 1;
+  const int tx = tid % TX, ty = wwarp ? TY : tid / TX;
+  // 2-D threads walk a run of R pair-rows [ja, jb) of their column.
+  const int R = (KIND == MJP_BD1D) ? 1 : (g.Hp + TY - 1) / TY;
+  const int ja = ty * R;
+  const int jb = (ty < TY) ? min(g.Hp, ja + R) : ja;
+  const bool rows = !wwarp && tx < g.W && ja < jb;  // 2-D models
+  // Observation groups are folded in by the weights warp when the stencil
+  // threads are busy (>= 8 states each), otherwise by every thread.
+  const int spt = (KIND == MJP_BD1D) ? (g.W + nthr_c - 1) / nthr_c : 2 * R;
+  const bool acc_ww = spt >= 8;
+  const bool acc_me = acc_ww ? wwarp : true;
+  const int acc_id = acc_ww ? lane : tid, acc_stride = acc_ww ? 32 : nthr;
+
+  // LOGLIK: acc_g += w_i f sum_{s in g} rho_k[s] over this CTA's states.
+  auto group_accumulate = [&](const T* cur, int l, int h, int64_t k, const double* wts, T f) {
     for (int i = l; i <= h; ++i) {
       double wd = wts[i] + (k == t_K[i] ? t_tail[i] : 0.0);
-      T w = (T)wd;
-      int g0 = (int)p.gptr[i], g1 = (int)p.gptr[i + 1];
-      for (int gq = g0 + tid; gq < g1; gq += nthr) {
-        int q0 = (int)p.mptr[gq], q1 = (int)p.mptr[gq + 1];
+      T w = f_mul((T)wd, f);
+      const int g0 = s_gptr[i], g1 = s_gptr[i + 1];
+      for (int gq = g0 + acc_id; gq < g1; gq += acc_stride) {
+        const int q0 = s_mptr[gq], q1 = s_mptr[gq + 1];
         T v = (T)0;
         bool any = false;
         for (int q = q0; q < q1; ++q) {
           int li = memloc[q];
           if (li >= 0) {
-            v += cur[li];
+            v = f_add(v, cur[li]);
             any = true;
           }
         }
         if (!any) continue;
         if (sizeof(T) == 4) {
-          float y = (float)w * (float)v - acc_c[gq];
-          float t = (float)acc_s[gq] + y;
-          acc_c[gq] = (t - (float)acc_s[gq]) - y;
+          float y = __fsub_rn(__fmul_rn((float)w, (float)v), acc_c[gq]);
+          float s0 = (float)acc_s[gq];
+          float t = __fadd_rn(s0, y);
+          acc_c[gq] = __fsub_rn(__fsub_rn(t, s0), y);
           acc_s[gq] = (T)t;
         } else {
-          acc_s[gq] += w * v;
+          acc_s[gq] = f_fma(w, v, acc_s[gq]);
         }
       }
     }
   };
 
-  // Thread layout over the owned block.
-  const int TX = g.W < nthr ? (g.W > 0 ? g.W : 1) : nthr;
-  const int TY = nthr / TX;
-  const int tx = tid % TX, ty = tid / TX;
-  const int R = (g.H + TY - 1) / TY;
-  const int ra = g.p0 + ty * R;
-  const int rb = (ty < TY) ? min(g.p1, ra + R) : ra;
-  const T one = (T)1;
+  // EXPV: rho*_i += w rho_{k-1}[n] for the active times (Kahan in FP32).
+  auto expv_accumulate = [&](T rv, int64_t gidx, int64_t kp, int l, int h, const double* wts) {
+    for (int i = l; i <= h; ++i) {
+      double wd = wts[i] + (kp == t_K[i] ? t_tail[i] : 0.0);
+      T w = (T)wd;
+      T* o = reinterpret_cast<T*>(p.out) + (int64_t)job * p.out_stride + (int64_t)t_orig[i] * N + gidx;
+      if (sizeof(T) == 4) {
+        float* cp = p.comp + (int64_t)job * p.comp_stride + (int64_t)i * N + gidx;
+        float s, cc;
+        if (kp == t_L[i]) {
+          s = __fmul_rn((float)w, (float)rv);
+          cc = 0.0f;
+        } else {
+          s = (float)*o;
+          cc = *cp;
+          float y = __fsub_rn(__fmul_rn((float)w, (float)rv), cc);
+          float t = __fadd_rn(s, y);
+          cc = __fsub_rn(__fsub_rn(t, s), y);
+          s = t;
+        }
+        if (kp == t_K[i]) *o = (T)__fsub_rn(s, cc);
+        else {
+          *o = (T)s;
+          *cp = cc;
+        }
+      } else {
+        if (kp == t_L[i]) *o = f_mul(w, rv);
+        else *o = f_fma(w, rv, *o);
+      }
+    }
+  };
 
-  double f_prev = 1.0;  // renormalisation factor carried onto rho_{k-1}
-  if (LL) group_accumulate(buf[0], lo, hi, 0, pw);
+  // Column constants of a 2-D thread as pairs (rates into column m, scaled
+  // by 1/Omega); the pair holds the values for rows 2j and 2j+1.
+  using T2 = typename Pair<T>::type;
+  const int mc = tx;  // 2-D slabs span all columns (m0 = 0)
+  const T one = (T)1;
+  T cd = (T)0;
+  T2 c_l = v_make((T)0, (T)0), c_r = c_l, c_d = c_l, c_dg = c_l, c_sw = c_l, c_gp = c_l, c_ngp = c_l;
+  if (KIND == MJP_TWOSTATE) {
+    // Active row (x): birth from m-1, death from m+1, reactivation of the
+    // inactive state; inactive row (y): death from m+1, deactivation.
+    const T bm = f_mul(co.b, (T)mc);
+    const T cr = f_mul(co.b, (T)(mc + 1));
+    c_l = v_make(co.a, (T)0);
+    c_r = v_make(cr, cr);
+    c_dg = v_make(f_sub(one, f_add(f_add(bm, mc + 1 < M ? co.a : (T)0), co.d)), f_sub(one, f_add(co.c, bm)));
+    c_sw = v_make(co.c, co.d);
+  } else if (KIND == MJP_MRNA_PROT2D) {
+    const T fm = (T)mc;
+    const T cr = f_mul(co.b, (T)(mc + 1));                 // gamma_m (m+1) from m+1
+    cd = f_mul(co.c, fm);                                  // k_p m from p-1
+    const T d0 = f_sub(one, f_add(f_add(f_mul(co.b, fm), mc + 1 < M ? co.a : (T)0), cd));
+    c_l = v_make(co.a, co.a);                              // k_m from m-1
+    c_r = v_make(cr, cr);
+    c_d = v_make(cd, cd);
+    c_dg = v_make(d0, d0);                                 // 1 - e without gamma_p p
+    c_gp = v_make(co.d, co.d);                             // gamma_p
+    c_ngp = v_make(-co.d, -co.d);
+  }
+  const T2 two2 = v_make((T)2, (T)2);
 
   // ---- the jump chain -----------------------------------------------------
-  for (int64_t k = 1; k <= Kmax + (LL ? 0 : 1); ++k) {
+  bool renorm_prev = false;  // was rho_{k-1}'s mass reduced at jump k-1?
+  for (int64_t k = 1; k <= Kmax + 1; ++k) {
     const int par = (int)((k - 1) & 1);
-    const T* src = buf[par];
-    T* dst = buf[par ^ 1];
+    const T* src = reinterpret_cast<const T*>(smem + buf_off[par]);
+    T* dst = reinterpret_cast<T*>(smem + buf_off[par ^ 1]);
     const double* wprev = pw + par * nt;
     double* wcur = pw + (par ^ 1) * nt;
     const int plo = lo, phi = hi;
     int clo = lo, chi = hi;
     advance(k, clo, chi);
-    if (warp == 0 && k <= Kmax) {  // weights of jump k (Algorithm 2: P *= x/k)
+    const bool jump = k <= Kmax;
+    T f = one;  // renormalisation factor carried by rho_{k-1}
+    if (renorm_prev) {
+      double tot = cluster_total(red + (int)((k - 1) & 1) * 33);
+      f = (T)(tot > 0.0 ? mass0 / tot : 1.0);
+    }
+    if (wwarp && jump) {  // weights of jump k (Algorithm 2: P *= x/k)
       for (int i = clo + lane; i <= chi; i += 32)
         wcur[i] = (k == t_L[i]) ? t_PL[i] : __dmul_rn(wprev[i], __ddiv_rn(t_x[i], (double)k));
     }
-    const T f = (T)f_prev;
-    const bool jump = k <= Kmax;
+    if (LL && acc_me) group_accumulate(src, plo, phi, k - 1, wprev, f);
     T part = (T)0;
-    for (int m = g.m0 + tx; m < g.m1; m += TX) {
-      const int lc = m - g.m0 + 1;  // local column (padded)
-      // Column coefficients (scaled rates into this column's states).
-      T cl, cr, cd, cu, ebase;
-      if (KIND == MJP_BD1D) {
-        cl = co.a;                                   // birth from m-1
-        cr = co.b * (T)(m + 1);                      // death from m+1
-        cd = (T)0;
-        cu = (T)0;
-        ebase = co.b * (T)m + (m + 1 < M ? co.a : (T)0);
-      } else if (KIND == MJP_TWOSTATE) {
-        cl = co.a;                                   // birth (active row only)
-        cr = co.b * (T)(m + 1);                      // death from m+1
-        cd = co.d;                                   // row 1 <- row 0 at lambda_ina
-        cu = co.c;                                   // row 0 <- row 1 at lambda_act
-        ebase = co.b * (T)m;
-      } else {
-        cl = co.a;                                   // k_m from m-1
-        cr = co.b * (T)(m + 1);                      // gamma_m (m+1) from m+1
-        cd = co.c * (T)m;                            // k_p m from p-1
-        cu = (T)0;                                   // gamma_p (p+1), per row
-        ebase = co.b * (T)m + (m + 1 < M ? co.a : (T)0) + co.c * (T)m;
-      }
-      // Left/right neighbours outside a column slab (birth-death clusters).
-      T left_rem = (T)0, right_rem = (T)0;
-      if (KIND == MJP_BD1D && C > 1 && jump) {
-        // A neighbour's tile is one padded row: its last owned column sits at
-        // Wp - 2, its first at 1.
-        if (m == g.m0 && m >= 1 && dn_rem[par]) left_rem = dn_rem[par][dn_W - 2];
-        if (m == g.m1 - 1 && m + 1 < M && up_rem[par]) right_rem = up_rem[par][1];
-      }
-      int li = (ra - g.p0 + row_off<KIND>()) * g.Wp + lc;
-      T down = (T)0;
-      if (KIND != MJP_BD1D && ra < rb && ra >= 1) {
-        if (ra - 1 >= g.p0) down = src[li - g.Wp];
-        else if (dn_rem[par]) down = dn_rem[par][dn_H * dn_W + lc];  // last owned row of rank-1
-      }
-      T cur = (ra < rb) ? src[li] : (T)0;
-      for (int pp = ra; pp < rb; ++pp, li += g.Wp) {
-        T up = (T)0;
-        if (KIND != MJP_BD1D && pp + 1 < P) {
-          if (pp + 1 < g.p1) up = src[li + g.Wp];
-          else if (up_rem[par]) up = up_rem[par][g.Wp + lc];  // first owned row of rank+1
-        }
-        T left = src[li - 1], right = src[li + 1];
-        if (KIND == MJP_BD1D && C > 1) {
-          if (m == g.m0) left = left_rem;
-          if (m == g.m1 - 1) right = right_rem;
-        }
-        if (!LL) {
-          // EXPV: accumulate rho_{k-1} (its value is `cur`).
-          const int64_t kp = k - 1;
-          const T rv = cur * f;
-          const int64_t gidx = (int64_t)pp * M + m;
-          for (int i = plo; i <= phi; ++i) {
-            double wd = wprev[i] + (kp == t_K[i] ? t_tail[i] : 0.0);
-            T w = (T)wd;
-            T* o = reinterpret_cast<T*>(p.out) + (int64_t)job * p.out_stride + (int64_t)t_orig[i] * N + gidx;
-            if (sizeof(T) == 4) {
-              float* c = p.comp + (int64_t)job * p.comp_stride + (int64_t)i * N + gidx;
-              float s, cc;
-              if (kp == t_L[i]) {
-                s = (float)w * (float)rv;
-                cc = 0.0f;
-              } else {
-                s = (float)*o;
-                cc = *c;
-                float y = (float)w * (float)rv - cc;
-                float t = s + y;
-                cc = (t - s) - y;
-                s = t;
-              }
-              if (kp == t_K[i]) *o = (T)(s - cc);
-              else {
-                *o = (T)s;
-                *c = cc;
-              }
-            } else {
-              if (kp == t_L[i]) *o = w * rv;
-              else *o += w * rv;
-            }
-          }
-        }
+    if (KIND == MJP_BD1D) {
+      for (int m = wwarp ? g.m1 : g.m0 + tx; m < g.m1; m += TX) {
+        const int li = m - g.m0 + 1;
+        const T cur = src[li];
+        if (!LL) expv_accumulate(rn ? f_mul(cur, f) : cur, m, k - 1, plo, phi, wprev);
         if (jump) {
-          T y;
-          if (KIND == MJP_BD1D) {
-            y = (one - ebase) * cur + cl * left + cr * right;
-          } else if (KIND == MJP_TWOSTATE) {
-            if (pp == 0) {  // active: births, deaths, reactivation from row 1
-              T e = ebase + (m + 1 < M ? co.a : (T)0) + co.d;
-              y = (one - e) * cur + cl * left + cr * right + cu * up;
-            } else {        // inactive: deaths, deactivation from row 0
-              T e = ebase + co.c;
-              y = (one - e) * cur + cr * right + cd * down;
-            }
-          } else {
-            const T gp = co.d * (T)pp;
-            T e = ebase + gp - (pp + 1 < P ? (T)0 : cd);  // no protein birth in the top row
-            T cup = co.d * (T)(pp + 1);
-            y = (one - e) * cur + cl * left + cr * right + cd * down + cup * up;
-          }
-          if (p.renorm > 0) {
-            y *= f;
+          const T fm = (T)m;
+          const T e = f_add(f_mul(co.b, fm), m + 1 < M ? co.a : (T)0);
+          T y = f_mul(f_sub(one, e), cur);
+          y = f_fma(co.a, src[li - 1], y);
+          y = f_fma(f_mul(co.b, f_add(fm, one)), src[li + 1], y);
+          if (rn) {
+            y = f_mul(y, f);
             part += y;
           }
           dst[li] = y;
+          if (m == g.m0 && push_dn[par ^ 1]) *push_dn[par ^ 1] = y;
+          if (m == g.m1 - 1 && push_up[par ^ 1]) *push_up[par ^ 1] = y;
         }
-        down = cur;
-        cur = up;
+      }
+    } else if (rows) {
+      // The two ping-pong buffers never overlap.
+      const T2* __restrict__ sp = reinterpret_cast<const T2*>(src) + (ja + 1) * g.Wp + mc + 1;
+      T2* __restrict__ dp = reinterpret_cast<T2*>(dst) + (ja + 1) * g.Wp + mc + 1;
+      T2* const dfirst = dp;
+      const int W2 = g.Wp;
+      int pp = g.p0 + 2 * ja;  // row of the pair's first half
+      T2 prev = sp[-W2];
+      T2 cur = sp[0];
+      T2 fpp = v_make((T)pp, (T)(pp + 1));
+      const T2 f2 = v_make(f, f);
+      T2 y = v_make((T)0, (T)0);
+      // One pair-row: rows pp and pp+1 of column mc.  `top` marks the pair
+      // that holds row P-1 (no protein birth out of it; row P absent).
+      auto pair_row = [&](bool top) {
+        const T2 next = sp[W2];
+        const T2 left = sp[-1], right = sp[1];
+        if (!LL) {
+          expv_accumulate(rn ? f_mul(cur.x, f) : cur.x, (int64_t)pp * M + mc, k - 1, plo, phi, wprev);
+          if (pp + 1 < g.p1)
+            expv_accumulate(rn ? f_mul(cur.y, f) : cur.y, (int64_t)(pp + 1) * M + mc, k - 1, plo, phi, wprev);
+        }
+        if (jump) {
+          if (KIND == MJP_TWOSTATE) {
+            const T2 t1 = v_fma(c_l, left, v_mul(c_dg, cur));
+            const T2 t2 = v_fma(c_sw, v_make(cur.y, cur.x), v_mul(c_r, right));
+            y = v_add(t1, t2);
+          } else {
+            T2 dg = v_fma(c_ngp, fpp, c_dg);        // 1 - e_{m,p}
+            const T2 cup = v_fma(c_gp, fpp, c_gp);  // gamma_p (p+1) from p+1
+            if (top) {
+              if (pp == P - 1) dg.x = f_add(dg.x, cd);
+              else dg.y = f_add(dg.y, cd);
+            }
+            y = v_fma(c_r, right, v_fma(c_l, left, v_mul(dg, cur)));
+            y.x = f_fma(cup.x, cur.y, f_fma(cd, prev.y, y.x));  // rows below / above
+            y.y = f_fma(cup.y, next.x, f_fma(cd, cur.x, y.y));
+            if (top && pp + 1 >= P) y.y = (T)0;     // row P does not exist
+            fpp = v_add(fpp, two2);
+          }
+          if (rn) {
+            y = v_mul(y, f2);
+            part += y.x + y.y;
+          }
+          *dp = y;
+        }
+        prev = cur;
+        cur = next;
+        sp += W2;
+        dp += W2;
+        pp += 2;
+      };
+      const bool has_top = (KIND == MJP_MRNA_PROT2D) && jb == g.Hp && g.p1 == P;
+      const int jend = has_top ? jb - 1 : jb;
+#pragma unroll 2
+      for (int j = ja; j < jend; ++j) pair_row(false);
+      if (has_top) pair_row(true);
+      if (jump) {
+        if (push_dn[par ^ 1] && ja == 0) reinterpret_cast<T2*>(push_dn[par ^ 1])[mc + 1] = *dfirst;
+        if (push_up[par ^ 1] && jb == g.Hp) reinterpret_cast<T2*>(push_up[par ^ 1])[mc + 1] = y;
       }
     }
-    const bool do_renorm = p.renorm > 0 && jump && (k % p.renorm) == 0;
-    double* redk = red + (k & 1) * 33;
+    const bool do_renorm = rn && jump && (k % p.renorm) == 0;
     if (do_renorm) {
       double v = (double)part;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-      if (lane == 0) redk[warp] = v;
+      if (lane == 0) red[(int)(k & 1) * 33 + warp] = v;
     }
-    __syncthreads();
+    renorm_prev = do_renorm;
+    if (C > 1) {
+      cluster_arrive();
+      cluster_wait();
+    } else {
+      __syncthreads();
+    }
     lo = clo;
     hi = chi;
-    if (!jump) break;
-    f_prev = 1.0;
-    if (do_renorm) {
-      if (C > 1) cluster.sync();
-      double tot = 0.0;
-      for (int r = 0; r < C; ++r) {
-        const double* rr = (C == 1) ? redk : cluster.map_shared_rank(redk, r);
-        for (int w = 0; w < nwarps; ++w) tot += rr[w];
-      }
-      f_prev = tot > 0.0 ? mass0 / tot : 1.0;
-      if (LL && f_prev != 1.0) {
-        for (int j = tid; j < tile; j += nthr) dst[j] = (T)(dst[j] * (T)f_prev);
-        f_prev = 1.0;
-        __syncthreads();
-      }
-      if (LL) group_accumulate(dst, lo, hi, k, wcur);
-      if (C > 1) cluster.sync();  // remote reads of red and of dst are complete
-    } else {
-      if (C > 1) cluster_arrive();
-      if (LL) group_accumulate(dst, lo, hi, k, wcur);
-      if (C > 1) cluster_wait();
-    }
   }
 
   if (LL) {
     // ---- epilogue: sum_g c_g log(a_g), partial sums of all CTAs ------------
-    if (C > 1) cluster.sync();
-    else __syncthreads();
     if (rank == 0) {
       double ll = 0.0;
       bool bad = false;
@@ -573,6 +670,7 @@ int64_t chain_stencil_slab(int kind, int64_t M, int64_t P, int cluster) {
   int64_t N = M * P;
   if (kind == MJP_BD1D) return (N + cluster - 1) / cluster;
   int64_t rows = (P + cluster - 1) / cluster;
+  rows += rows & 1;  // row pairs never straddle two CTAs
   return rows * M;
 }
 

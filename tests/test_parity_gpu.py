@@ -65,7 +65,7 @@ def test_two_state_promoter(prec):
     assert np.abs(g - r).max() <= TOL[prec]
 
 
-@pytest.mark.parametrize("cluster,threads", [(1, 64), (2, 96), (4, 256), (8, 128)])
+@pytest.mark.parametrize("cluster,threads", [(1, 96), (2, 128), (4, 288), (8, 96)])
 @pytest.mark.parametrize("prec", [2, 1])
 def test_mrna_protein_clusters_ragged(cluster, threads, prec):
     # 37 x 23 = 851 states: slabs of ragged size, halos across CTAs.
