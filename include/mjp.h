@@ -193,6 +193,45 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
 int rate_model_last_timing(mjp_model* m, double* ms_plan, double* ms_chain);
 
 /*
+ * ---- batches of uneven instances --------------------------------------
+ * Many birth-death models (Eq. BD_def) with different sizes N_j, rates
+ * theta_j = {beta_j, gamma_j} and one observation time t_j each, rho0 =
+ * delta at s0_j, evaluated in one call: every instance is its own R-MJP
+ * series (Algorithm 2).  The library orders instances by estimated work
+ * (K_j N_j, longest first), runs light instances one CTA each and splits
+ * heavy ones over a thread-block cluster, launching the groups concurrently;
+ * the whole call can be captured once as a CUDA graph and replayed.
+ */
+typedef struct mjp_batch mjp_batch;
+
+/* Host arrays of n_inst entries (theta: n_inst x 2; s0 may be NULL = 0).
+ * precision: MJP_FP32 or MJP_FP64.  Errors: MJP_ERR_ARG, MJP_ERR_ALLOC. */
+int expv_batch_create(mjp_batch** out, int kind, int n_inst, const int64_t* N, const double* theta,
+                      const double* t, const int64_t* s0, int precision);
+
+/* offsets[j] (host, n_inst + 1 entries): instance j's distribution occupies
+ * out[offsets[j] .. offsets[j+1]) of the output of expv_batch_run. */
+int expv_batch_offsets(const mjp_batch* b, int64_t* offsets);
+
+/* Evaluate all instances; out is device memory of offsets[n_inst] values in
+ * the batch precision.  Asynchronous on `stream`.  With use_graph = 1 the
+ * launch sequence is captured as a CUDA graph on the first call for a given
+ * (out, stream) and replayed afterwards.  Errors: MJP_ERR_ALLOC, MJP_ERR_CUDA. */
+int expv_batch_run(mjp_batch* b, void* out, int use_graph, void* stream);
+
+/* Autotune the launch configuration (threads of light CTAs, cluster size and
+ * threads of heavy instances, the heavy threshold) by timing candidate
+ * configurations on `stream` with CUDA events (runs the batch several times
+ * into `out`).  Writes the chosen configuration as text into cfg (nullable,
+ * cfg_len bytes).  Errors: as expv_batch_run. */
+int expv_batch_tune(mjp_batch* b, void* out, void* stream, char* cfg, int cfg_len);
+
+/* Device-side error check of the last run (synchronises `stream`). */
+int expv_batch_check(mjp_batch* b, void* stream);
+
+void expv_batch_destroy(mjp_batch* b);
+
+/*
  * Synchronise `stream` and report device-side errors recorded by earlier
  * asynchronous calls on this model (K above the cap, non-finite values, a
  * bounded wait that ran out).  Clears the record.  Returns MJP_OK or the

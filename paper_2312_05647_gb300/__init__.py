@@ -17,7 +17,7 @@ from .capi import (BD1D, CSR, FP32, FP64, MRNA_PROT2D, OPT_CLUSTER, OPT_K_CAP, O
                    OPT_RENORM_PERIOD, OPT_THREADS, PTR_DEVICE, PTR_HOST, TRUNC_PAPER, TRUNC_TOL, TWOSTATE,
                    MJPError)
 
-__all__ = ["Model", "Obs", "loglik", "BD1D", "TWOSTATE", "MRNA_PROT2D", "CSR", "FP32", "FP64",
+__all__ = ["Model", "Obs", "Batch", "loglik", "BD1D", "TWOSTATE", "MRNA_PROT2D", "CSR", "FP32", "FP64",
            "TRUNC_PAPER", "TRUNC_TOL", "MJPError"]
 
 _NTHETA = {BD1D: 2, TWOSTATE: 4, MRNA_PROT2D: 4}
@@ -185,3 +185,59 @@ def loglik(model: Model, obs: Obs, theta, trunc: int = TRUNC_PAPER, tol: float =
     capi.check(L.loglik(model._h, obs._h, ctypes.c_void_p(th.ctypes.data), B, ctypes.c_void_p(res.ctypes.data),
                         PTR_HOST, int(trunc), float(tol), _stream_ptr(stream)))
     return res
+
+
+class Batch:
+    """Uneven birth-death instances evaluated in one call (expv_batch_*)."""
+
+    def __init__(self, N, theta, t, s0=None, precision: int = FP32, kind: int = BD1D):
+        L = capi.lib()
+        n = np.ascontiguousarray(N, dtype=np.int64)
+        th = _f64(theta).reshape(len(n), 2)
+        tt = _f64(t)
+        s = None if s0 is None else np.ascontiguousarray(s0, dtype=np.int64)
+        self._h = ctypes.c_void_p()
+        capi.check(L.expv_batch_create(ctypes.byref(self._h), int(kind), len(n), n.ctypes.data_as(capi._i64p),
+                                       th.ctypes.data_as(capi._f64p), tt.ctypes.data_as(capi._f64p),
+                                       None if s is None else s.ctypes.data_as(capi._i64p), int(precision)))
+        self.n, self.precision = len(n), precision
+        self.offsets = np.zeros(len(n) + 1, np.int64)
+        capi.check(L.expv_batch_offsets(self._h, self.offsets.ctypes.data_as(capi._i64p)))
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.precision == FP64 else torch.float32
+
+    def empty_out(self, device="cuda"):
+        import torch
+        return torch.empty(int(self.offsets[-1]), dtype=self.torch_dtype, device=device)
+
+    def run(self, out, use_graph: bool = False, stream=None):
+        capi.check(capi.lib().expv_batch_run(self._h, ctypes.c_void_p(out.data_ptr()), int(use_graph),
+                                             _stream_ptr(stream)))
+        return out
+
+    def tune(self, out, stream=None) -> str:
+        buf = ctypes.create_string_buffer(512)
+        capi.check(capi.lib().expv_batch_tune(self._h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream), buf,
+                                              512))
+        return buf.value.decode()
+
+    def check(self, stream=None):
+        capi.check(capi.lib().expv_batch_check(self._h, _stream_ptr(stream)))
+
+    def split(self, out):
+        """Per-instance views of a run's output."""
+        return [out[self.offsets[j]:self.offsets[j + 1]] for j in range(self.n)]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            capi.lib().expv_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -54,6 +54,13 @@ SIGNATURES = {
     "mjp_obs_destroy": (None, [_vp]),
     "loglik": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                               _vp]),
+    "expv_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, _i64p, _f64p, _f64p,
+                                         _i64p, ctypes.c_int]),
+    "expv_batch_offsets": (ctypes.c_int, [_vp, _i64p]),
+    "expv_batch_run": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
+    "expv_batch_tune": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_char_p, ctypes.c_int]),
+    "expv_batch_check": (ctypes.c_int, [_vp, _vp]),
+    "expv_batch_destroy": (None, [_vp]),
 }
 
 _LIB = None

@@ -9,56 +9,19 @@
 #include <string>
 #include <vector>
 
+#include "host_util.h"
 #include "internal.cuh"
 
 using namespace mjp;
 
-namespace {
-
-thread_local std::string g_err;
-
-int fail(int code, const std::string& msg) {
-  g_err = msg;
-  return code;
+namespace mjp {
+std::string& last_error() {
+  static thread_local std::string msg;
+  return msg;
 }
+}  // namespace mjp
 
-#define MJP_CUDA(call)                                                                   \
-  do {                                                                                   \
-    cudaError_t e_ = (call);                                                             \
-    if (e_ != cudaSuccess) {                                                             \
-      cudaGetLastError();                                                                \
-      return fail(MJP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
-    }                                                                                    \
-  } while (0)
-
-// Grow-only device buffer.  Growing synchronises the device first so that no
-// queued kernel still uses the old allocation.
-struct DevBuf {
-  void* p = nullptr;
-  size_t cap = 0;
-  int ensure(size_t bytes) {
-    if (bytes <= cap) return MJP_OK;
-    cudaDeviceSynchronize();
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    if (cudaMalloc(&p, bytes < 256 ? 256 : bytes) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(MJP_ERR_ALLOC, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
-    }
-    cap = bytes < 256 ? 256 : bytes;
-    return MJP_OK;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-  }
-  template <typename T>
-  T* as() const {
-    return reinterpret_cast<T*>(p);
-  }
-};
+namespace {
 
 bool finite_nonneg(const double* v, int64_t n) {
   for (int64_t i = 0; i < n; ++i)
@@ -90,9 +53,17 @@ struct mjp_model {
   int profile = 0;
   bool timed = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  // general CSR: B^T in SELL-32 form over states renumbered by in-degree
+  double csr_omega = 0.0;
+  int64_t nslices = 0;
+  DevBuf d_slice_ptr, d_slice_len, d_col, d_val, d_diag, d_perm;
   // workspace (scratch owned by the handle)
   DevBuf d_times, d_orig, d_win, d_info, d_theta, d_comp, d_status, d_ll;
+  DevBuf d_rho2, d_outp, d_wtab, d_woff, d_L, d_K;
   ~mjp_model() {
+    d_slice_ptr.release(); d_slice_len.release(); d_col.release(); d_val.release(); d_diag.release();
+    d_perm.release(); d_rho2.release(); d_outp.release(); d_wtab.release(); d_woff.release();
+    d_L.release(); d_K.release();
     d_times.release(); d_orig.release(); d_win.release(); d_info.release();
     d_theta.release(); d_comp.release(); d_status.release(); d_ll.release();
     for (auto& e : ev)
@@ -105,6 +76,7 @@ struct mjp_obs {
   int ntimes = 0;
   int G = 0;
   int nmem = 0;
+  std::vector<double> times;  // ascending (host copy)
   DevBuf d_times, d_gptr, d_counts, d_mptr, d_members, d_rho64, d_rho32;
   ~mjp_obs() {
     d_times.release(); d_gptr.release(); d_counts.release(); d_mptr.release();
@@ -187,6 +159,83 @@ int mark(mjp_model* m, int i, cudaStream_t s) {
   return MJP_OK;
 }
 
+int map_status(int st);
+
+// The general-CSR chain: planner, windows back to the host (the number of
+// launches is the largest K), weight table, rho0 into the in-degree order,
+// then one launch per jump.  Leaves the outputs (times in ascending order,
+// states in the internal order) in m->d_outp.
+int csr_run(mjp_model* m, const void* rho0, const double* sorted_times, int nt, int trunc_mode, double tol,
+            cudaStream_t s, std::vector<Win>* wins) {
+  const size_t elt = m->precision == MJP_FP64 ? 8 : 4;
+  const int64_t n = m->N;
+  int rc = 0;
+  if ((rc = ensure_status(m)) || (rc = m->d_times.ensure(sizeof(double) * nt)) ||
+      (rc = m->d_win.ensure(sizeof(Win) * nt)) || (rc = m->d_info.ensure(sizeof(JobInfo))) ||
+      (rc = m->d_rho2.ensure(2 * elt * n)) || (rc = m->d_outp.ensure(elt * (size_t)nt * n)) ||
+      (rc = m->d_woff.ensure(sizeof(int64_t) * nt)) || (rc = m->d_L.ensure(sizeof(int64_t) * nt)) ||
+      (rc = m->d_K.ensure(sizeof(int64_t) * nt)))
+    return rc;
+  if (m->precision == MJP_FP32 && (rc = m->d_comp.ensure(sizeof(float) * (size_t)nt * n))) return rc;
+  MJP_CUDA(cudaMemcpyAsync(m->d_times.p, sorted_times, sizeof(double) * nt, cudaMemcpyHostToDevice, s));
+  PlanParams pp = {};
+  pp.kind = MJP_CSR; pp.M = 1; pp.P = 1; pp.N = n; pp.ntheta = 0; pp.theta = nullptr; pp.B = 1;
+  pp.ntimes = nt; pp.times = m->d_times.as<double>();
+  pp.trunc_mode = trunc_mode; pp.tol = tol; pp.omega_factor = 1.1; pp.omega_fixed = m->csr_omega;
+  pp.kcap = m->kcap; pp.win = m->d_win.as<Win>(); pp.info = m->d_info.as<JobInfo>();
+  pp.status = m->d_status.as<int>();
+  if ((rc = mark(m, 0, s))) return rc;
+  MJP_CUDA(launch_plan(pp, s));
+  wins->resize(nt);
+  MJP_CUDA(cudaMemcpyAsync(wins->data(), m->d_win.p, sizeof(Win) * nt, cudaMemcpyDeviceToHost, s));
+  MJP_CUDA(cudaStreamSynchronize(s));
+  int st = 0;
+  MJP_CUDA(cudaMemcpy(&st, m->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    MJP_CUDA(cudaMemset(m->d_status.p, 0, sizeof(int)));
+    return map_status(st);
+  }
+  std::vector<int64_t> woff(nt), L(nt), K(nt);
+  int64_t tot = 0, kmax = 0;
+  for (int i = 0; i < nt; ++i) {
+    woff[i] = tot;
+    L[i] = (*wins)[i].L;
+    K[i] = (*wins)[i].K;
+    tot += K[i] - L[i] + 1;
+    kmax = std::max(kmax, K[i]);
+  }
+  if ((rc = m->d_wtab.ensure(sizeof(double) * std::max<int64_t>(tot, 1)))) return rc;
+  MJP_CUDA(cudaMemcpyAsync(m->d_woff.p, woff.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_L.p, L.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_K.p, K.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(launch_fill_weights(m->d_win.as<Win>(), nt, m->d_woff.as<int64_t>(), m->d_wtab.as<double>(), s));
+  char* rho = m->d_rho2.as<char>();
+  MJP_CUDA(launch_permute_in(m->precision, rho0, m->d_perm.as<int32_t>(), rho, n, s));
+  if ((rc = mark(m, 1, s))) return rc;
+  CsrJumpParams jp = {};
+  jp.n = n; jp.nslices = m->nslices;
+  jp.slice_ptr = m->d_slice_ptr.as<int64_t>(); jp.slice_len = m->d_slice_len.as<int32_t>();
+  jp.col = m->d_col.as<int32_t>(); jp.val = m->d_val.p; jp.diag = m->d_diag.p;
+  jp.wtab = m->d_wtab.as<double>(); jp.woff = m->d_woff.as<int64_t>();
+  jp.L = m->d_L.as<int64_t>(); jp.K = m->d_K.as<int64_t>();
+  jp.out = m->d_outp.p; jp.comp = m->d_comp.as<float>();
+  int lo = 0, hi = -1;  // times whose window holds jump k-1 (ascending times)
+  for (int64_t k = 1; k <= kmax + 1; ++k) {
+    const int64_t kp = k - 1;
+    while (lo < nt && K[lo] < kp) ++lo;
+    while (hi + 1 < nt && L[hi + 1] <= kp) ++hi;
+    jp.k = k;
+    jp.jump = k <= kmax;
+    jp.tlo = lo;
+    jp.thi = hi;
+    jp.rho_prev = rho + ((kp & 1) ? elt * n : 0);
+    jp.rho_next = rho + ((kp & 1) ? 0 : elt * n);
+    MJP_CUDA(launch_csr_jump(m->precision, jp, s));
+  }
+  if ((rc = mark(m, 2, s))) return rc;
+  return MJP_OK;
+}
+
 int map_status(int st) {
   switch (st) {
     case kStatusOk: return MJP_OK;
@@ -201,7 +250,7 @@ int map_status(int st) {
 
 extern "C" {
 
-const char* mjp_last_error(void) { return g_err.c_str(); }
+const char* mjp_last_error(void) { return mjp::last_error().c_str(); }
 
 const char* mjp_version(void) { return "mjp-gb300 0.1 (sm_103a)"; }
 
@@ -236,9 +285,109 @@ int rate_model_create_stencil(mjp_model** out, int kind, const int64_t* dims, in
 
 int rate_model_create_csr(mjp_model** out, int64_t n, const int64_t* row_ptr, const int32_t* col,
                           const double* rate, int precision) {
-  (void)n; (void)row_ptr; (void)col; (void)rate; (void)precision;
-  if (out) *out = nullptr;
-  return fail(MJP_ERR_UNSUPPORTED, "CSR models are not built in this version");
+  if (!out) return fail(MJP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > ((int64_t)1 << 31) - 1) return fail(MJP_ERR_ARG, "n out of range");
+  if (!row_ptr || !col || !rate) return fail(MJP_ERR_ARG, "NULL CSR array");
+  if (precision != MJP_FP32 && precision != MJP_FP64) return fail(MJP_ERR_ARG, "precision must be MJP_FP32 or MJP_FP64");
+  if (row_ptr[0] != 0) return fail(MJP_ERR_CSR, "row_ptr[0] must be 0");
+  for (int64_t i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return fail(MJP_ERR_CSR, "row_ptr is not monotone");
+  const int64_t nnz = row_ptr[n];
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+      if (col[j] < 0 || col[j] >= n) return fail(MJP_ERR_CSR, "column index out of range");
+      if (col[j] == i) return fail(MJP_ERR_CSR, "diagonal entries are not rates (lambda_nn = 0)");
+      if (!(rate[j] >= 0.0) || !std::isfinite(rate[j])) return fail(MJP_ERR_CSR, "rates must be finite and >= 0");
+    }
+  // Exit rates e_n = sum_m lambda_nm, each row summed in ascending column order.
+  std::vector<int64_t> ord(nnz);
+  std::vector<double> e(n, 0.0);
+  std::vector<int64_t> indeg(n, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) ord[j] = j;
+    std::stable_sort(ord.begin() + row_ptr[i], ord.begin() + row_ptr[i + 1],
+                     [&](int64_t a, int64_t b) { return col[a] < col[b]; });
+    double acc = 0.0;
+    for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+      acc = acc + rate[ord[j]];
+      indeg[col[ord[j]]] += 1;
+    }
+    e[i] = acc;
+  }
+  double maxe = 0.0;
+  for (int64_t i = 0; i < n; ++i) maxe = e[i] > maxe ? e[i] : maxe;
+  volatile double factor = 1.1;  // Omega = 1.1 max_n |a_nn| with one rounding
+  const double omega = maxe > 0.0 ? factor * maxe : 0.0;
+  // Renumber states by decreasing in-degree; slices of 32 states.
+  std::vector<int32_t> iperm(n), perm(n);
+  for (int64_t i = 0; i < n; ++i) iperm[i] = (int32_t)i;
+  std::stable_sort(iperm.begin(), iperm.end(), [&](int32_t a, int32_t b) { return indeg[a] > indeg[b]; });
+  for (int64_t q = 0; q < n; ++q) perm[iperm[q]] = (int32_t)q;
+  const int64_t nslices = (n + 31) / 32;
+  std::vector<int32_t> slen(nslices, 0);
+  std::vector<int64_t> sptr(nslices + 1, 0);
+  for (int64_t s0 = 0; s0 < nslices; ++s0) {
+    int64_t w = 0;
+    for (int64_t l = 0; l < 32 && s0 * 32 + l < n; ++l) w = std::max(w, indeg[iperm[s0 * 32 + l]]);
+    slen[s0] = (int32_t)w;
+    sptr[s0 + 1] = sptr[s0] + w * 32;
+  }
+  const int64_t npad = sptr[nslices];
+  std::vector<int32_t> ecol(npad);
+  std::vector<double> eval(npad, 0.0);
+  for (int64_t q = 0; q < n; ++q) {  // padding: self index, weight 0
+    int64_t s0 = q / 32, l = q % 32;
+    for (int64_t j = 0; j < slen[s0]; ++j) ecol[sptr[s0] + j * 32 + l] = (int32_t)q;
+  }
+  std::vector<int32_t> fill(n, 0);
+  for (int64_t i = 0; i < n; ++i)  // incoming entries in ascending source order
+    for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+      const int64_t t = col[ord[j]];
+      const int64_t q = perm[t], s0 = q / 32, l = q % 32;
+      const int64_t slot = sptr[s0] + (int64_t)fill[t]++ * 32 + l;
+      ecol[slot] = perm[i];
+      eval[slot] = omega > 0.0 ? rate[ord[j]] / omega : 0.0;
+    }
+  std::vector<double> diag(n);
+  for (int64_t q = 0; q < n; ++q) diag[q] = omega > 0.0 ? 1.0 - e[iperm[q]] / omega : 1.0;
+
+  auto* m = new mjp_model();
+  m->kind = MJP_CSR;
+  m->precision = precision;
+  m->N = n; m->M = n; m->P = 1;
+  m->csr_omega = omega;
+  m->nslices = nslices;
+  const size_t elt = precision == MJP_FP64 ? 8 : 4;
+  int rc = 0;
+  if ((rc = m->d_slice_ptr.ensure(sizeof(int64_t) * nslices)) || (rc = m->d_slice_len.ensure(sizeof(int32_t) * nslices)) ||
+      (rc = m->d_col.ensure(sizeof(int32_t) * std::max<int64_t>(npad, 1))) ||
+      (rc = m->d_val.ensure(elt * std::max<int64_t>(npad, 1))) || (rc = m->d_diag.ensure(elt * n)) ||
+      (rc = m->d_perm.ensure(sizeof(int32_t) * n))) {
+    delete m;
+    return rc;
+  }
+  auto up = [](DevBuf& b, const void* src, size_t bytes) { return cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice); };
+  cudaError_t ce = cudaSuccess;
+  if (precision == MJP_FP64) {
+    ce = up(m->d_val, eval.data(), 8 * npad);
+    if (ce == cudaSuccess) ce = up(m->d_diag, diag.data(), 8 * n);
+  } else {
+    std::vector<float> v32(eval.begin(), eval.end()), d32(diag.begin(), diag.end());
+    ce = up(m->d_val, v32.data(), 4 * npad);
+    if (ce == cudaSuccess) ce = up(m->d_diag, d32.data(), 4 * n);
+  }
+  if (ce == cudaSuccess) ce = up(m->d_slice_ptr, sptr.data(), sizeof(int64_t) * nslices);
+  if (ce == cudaSuccess) ce = up(m->d_slice_len, slen.data(), sizeof(int32_t) * nslices);
+  if (ce == cudaSuccess && npad > 0) ce = up(m->d_col, ecol.data(), sizeof(int32_t) * npad);
+  if (ce == cudaSuccess) ce = up(m->d_perm, perm.data(), sizeof(int32_t) * n);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    return fail(MJP_ERR_CUDA, std::string("uploading the CSR model failed: ") + cudaGetErrorString(ce));
+  }
+  *out = m;
+  return MJP_OK;
 }
 
 int rate_model_set_theta(mjp_model* m, const double* theta, int ntheta) {
@@ -313,7 +462,6 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
   if (trunc_mode == MJP_TRUNC_TOL && !(tol >= 1e-20 && tol < 0.5)) return fail(MJP_ERR_ARG, "tol must be in [1e-20, 0.5)");
   for (int i = 0; i < ntimes; ++i)
     if (!(times[i] >= 0.0) || !std::isfinite(times[i])) return fail(MJP_ERR_ARG, "times must be finite and >= 0");
-  if (m->kind == MJP_CSR) return fail(MJP_ERR_UNSUPPORTED, "CSR series not built in this version");
   cudaStream_t s = (cudaStream_t)stream;
   const int nt = ntimes;
   std::vector<int32_t> order(nt);
@@ -321,6 +469,24 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return times[a] < times[b]; });
   std::vector<double> st(nt);
   for (int i = 0; i < nt; ++i) st[i] = times[order[i]];
+  if (m->kind == MJP_CSR) {
+    std::vector<Win> w;
+    int rc = csr_run(m, rho0, st.data(), nt, trunc_mode, tol, s, &w);
+    if (rc) return rc;
+    if ((rc = m->d_orig.ensure(sizeof(int32_t) * nt))) return rc;
+    MJP_CUDA(cudaMemcpyAsync(m->d_orig.p, order.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
+    MJP_CUDA(launch_permute_out(m->precision, m->d_outp.p, m->d_perm.as<int32_t>(), out, m->N, nt,
+                                m->d_orig.as<int32_t>(), s));
+    if (info) {
+      info->omega = m->csr_omega;
+      for (int i = 0; i < nt; ++i) {
+        if (info->K) info->K[order[i]] = w[i].K;
+        if (info->eps) info->eps[order[i]] = w[i].tail;
+      }
+      return rate_model_check(m, stream);
+    }
+    return MJP_OK;
+  }
 
   int C, T;
   int64_t slab;
@@ -425,6 +591,7 @@ int mjp_obs_create(mjp_obs** out, int64_t n, int ntimes, const double* times,
   o->ntimes = ntimes;
   o->G = (int)G;
   o->nmem = (int)(mp.back());
+  o->times = st;
   int rc = 0;
   if ((rc = o->d_times.ensure(sizeof(double) * ntimes)) || (rc = o->d_gptr.ensure(sizeof(int64_t) * gp.size())) ||
       (rc = o->d_counts.ensure(sizeof(double) * cnt.size())) || (rc = o->d_mptr.ensure(sizeof(int64_t) * mp.size())) ||
@@ -459,7 +626,28 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   if (obs->n != m->N) return fail(MJP_ERR_ARG, "observations were built for a different state space");
   if (trunc_mode != MJP_TRUNC_PAPER && trunc_mode != MJP_TRUNC_TOL) return fail(MJP_ERR_ARG, "unknown truncation mode");
   if (trunc_mode == MJP_TRUNC_TOL && !(tol >= 1e-20 && tol < 0.5)) return fail(MJP_ERR_ARG, "tol must be in [1e-20, 0.5)");
-  if (m->kind == MJP_CSR) return fail(MJP_ERR_UNSUPPORTED, "CSR loglik not built in this version");
+  if (m->kind == MJP_CSR) {
+    // A CSR model has fixed rates: one instance, theta ignored.
+    if (B != 1) return fail(MJP_ERR_ARG, "CSR models evaluate one instance (B = 1)");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Win> w;
+    const void* r0 = (m->precision == MJP_FP64) ? obs->d_rho64.p : obs->d_rho32.p;
+    int rc = csr_run(m, r0, obs->times.data(), obs->ntimes, trunc_mode, tol, s, &w);
+    if (rc) return rc;
+    double* d_out = out;
+    if (where == MJP_PTR_HOST) {
+      if ((rc = m->d_ll.ensure(sizeof(double)))) return rc;
+      d_out = m->d_ll.as<double>();
+    }
+    MJP_CUDA(launch_csr_loglik(m->d_outp.p, m->precision, m->N, obs->d_gptr.as<int64_t>(), obs->ntimes,
+                               obs->d_counts.as<double>(), obs->d_mptr.as<int64_t>(), obs->d_members.as<int32_t>(),
+                               m->d_perm.as<int32_t>(), d_out, m->d_status.as<int>(), s));
+    if (where == MJP_PTR_HOST) {
+      MJP_CUDA(cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+      return rate_model_check(m, stream);
+    }
+    return MJP_OK;
+  }
   if (!theta) return fail(MJP_ERR_ARG, "theta is NULL");
   const int ntheta = ntheta_of(m->kind);
   if (where == MJP_PTR_HOST)

@@ -57,6 +57,10 @@ struct PlanParams {
   Win* win;             // device, B x ntimes
   JobInfo* info;        // device, B
   int* status;
+  // Batches of uneven birth-death instances (nullable): per-job state count
+  // and per-job times (times + job * ntimes).
+  const int32_t* jobN;
+  int times_per_job;
 };
 
 // Chain inputs (stencil models).
@@ -87,6 +91,33 @@ struct ChainParams {
   int renorm;              // period in jumps (0 = off)
   int64_t slab;            // states per CTA of the cluster (whole rows for 2-D models)
   int* status;
+  // Batches of uneven birth-death instances (all nullable):
+  const int32_t* jobN;     // states of each job (BD1D: M = N, P = 1; slab = ceil(N / cluster))
+  const int64_t* job_off;  // element offset of each job's outputs and compensation
+  const int32_t* job_map;  // cluster index -> job (longest first)
+  const int64_t* job_s0;   // rho0 = delta at s0 for each job (instead of rho0)
+  int tile_max;            // padded tile size of the largest job in the launch
+};
+
+// One jump of the general-CSR chain (csr.cu).
+struct CsrJumpParams {
+  int64_t n, nslices;
+  const int64_t* slice_ptr;  // first entry of each slice
+  const int32_t* slice_len;  // entries per state in each slice
+  const int32_t* col;        // permuted source state of each entry
+  const void* val;           // lambda / Omega (T)
+  const void* diag;          // 1 - e_n / Omega (T)
+  const void* rho_prev;      // rho_{k-1} (T, permuted order)
+  void* rho_next;            // rho_k
+  int64_t k;
+  bool jump;                 // form rho_k (false: only accumulate rho_{k-1})
+  int tlo, thi;              // times whose window holds k-1
+  const double* wtab;        // weights table
+  const int64_t* woff;       // table offset per time
+  const int64_t* L;          // window start per time
+  const int64_t* K;          // window end per time
+  void* out;                 // ntimes x n outputs (T, permuted order)
+  float* comp;               // FP32 Kahan compensation, ntimes x n
 };
 
 }  // namespace mjp
@@ -97,8 +128,19 @@ cudaError_t launch_plan(const PlanParams& p, cudaStream_t s);
 cudaError_t launch_chain_stencil(int kind, int precision, int loglik_mode, const ChainParams& p,
                                  int cluster, int threads, cudaStream_t s);
 int64_t chain_stencil_slab(int kind, int64_t M, int64_t P, int cluster);
+int chain_stencil_tile(int kind, int64_t M, int64_t P, int64_t slab);
+size_t chain_stencil_smem_tile(int precision, int loglik_mode, int tile, int ntimes, int G, int nmem);
 size_t chain_stencil_smem(int kind, int precision, int loglik_mode, int64_t M, int64_t P, int64_t slab,
                           int ntimes, int G, int nmem);
 int chain_stencil_max_cluster_blocks(int kind, int precision, int loglik_mode, int cluster,
                                      int threads, size_t smem);
+cudaError_t launch_fill_weights(const Win* win, int ntimes, const int64_t* woff, double* table, cudaStream_t s);
+cudaError_t launch_permute_in(int precision, const void* src, const int32_t* perm, void* dst, int64_t n,
+                              cudaStream_t s);
+cudaError_t launch_permute_out(int precision, const void* src, const int32_t* perm, void* dst, int64_t n,
+                               int ntimes, const int32_t* orig, cudaStream_t s);
+cudaError_t launch_csr_jump(int precision, const CsrJumpParams& p, cudaStream_t s);
+cudaError_t launch_csr_loglik(const void* outp, int precision, int64_t n, const int64_t* gptr, int ntimes,
+                              const double* counts, const int64_t* mptr, const int32_t* members,
+                              const int32_t* perm, double* ll, int* status, cudaStream_t s);
 }  // namespace mjp

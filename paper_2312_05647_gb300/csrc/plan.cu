@@ -204,9 +204,11 @@ __global__ void __launch_bounds__(256) plan_kernel(PlanParams p) {
     omega = p.omega_fixed;
   } else {
     const double* th = p.theta + (int64_t)job * p.ntheta;
+    const int64_t NJ = p.jobN ? (int64_t)p.jobN[job] : p.N;
+    const int64_t MJ = p.jobN ? NJ : p.M;
     double mx = 0.0;
-    for (int64_t n = tid; n < p.N; n += blockDim.x) {
-      double e = exit_rate(p.kind, p.M, p.P, n, th);
+    for (int64_t n = tid; n < NJ; n += blockDim.x) {
+      double e = exit_rate(p.kind, MJ, p.P, n, th);
       mx = e > mx ? e : mx;
     }
 #pragma unroll
@@ -225,7 +227,8 @@ __global__ void __launch_bounds__(256) plan_kernel(PlanParams p) {
     omega = s_omega;
   }
   Win* wj = p.win + (int64_t)job * p.ntimes;
-  for (int i = warp; i < p.ntimes; i += blockDim.x >> 5) plan_time(p, omega, p.times[i], wj + i, lane);
+  const double* tj = p.times + (p.times_per_job ? (int64_t)job * p.ntimes : 0);
+  for (int i = warp; i < p.ntimes; i += blockDim.x >> 5) plan_time(p, omega, tj[i], wj + i, lane);
   __syncthreads();
   if (tid == 0) {
     int64_t kmax = 0;

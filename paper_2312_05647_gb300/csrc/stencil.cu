@@ -185,13 +185,18 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
-  const int job = blockIdx.x / C;
+  const int job = p.job_map ? p.job_map[blockIdx.x / C] : blockIdx.x / C;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = nthr >> 5;
   const int nt = p.ntimes;
-  const int M = p.M, P = p.P, N = (int)p.N, S = (int)p.slab;
+  // Batches of uneven birth-death instances carry their own state count.
+  const int N = p.jobN ? p.jobN[job] : (int)p.N;
+  const int M = p.jobN ? N : p.M, P = p.P;
+  const int S = p.jobN ? (N + C - 1) / C : (int)p.slab;
   const Geo g = geometry(KIND, M, P, N, S, rank);
-  const int tile = tile_elems(KIND, M, P, N, S);
+  const int tile = p.tile_max > 0 ? p.tile_max : tile_elems(KIND, M, P, N, S);
+  const int64_t out_base = p.job_off ? p.job_off[job] : (int64_t)job * p.out_stride;
+  const int64_t comp_base = p.job_off ? p.job_off[job] : (int64_t)job * p.comp_stride;
 
   const Smem L = smem_layout(sizeof(T), tile, nt, p.G, p.nmem, LL);
   // Tile buffers are always formed from the __shared__ base (never through a
@@ -252,6 +257,8 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   const int64_t Kmax = p.info[job].Kmax;
   const Coef<T> co = make_coef<T, KIND>(p.theta + (int64_t)job * p.ntheta, omega);
   const T* rho0 = reinterpret_cast<const T*>(p.rho0);
+  const int64_t s0 = p.job_s0 ? p.job_s0[job] : -1;  // rho0 = delta at s0
+  auto rho0_at = [&](int64_t n) -> T { return s0 >= 0 ? (T)(n == s0 ? 1 : 0) : rho0[n]; };
   for (int j = tid; j < tile; j += nthr) {
     buf0[j] = (T)0;
     buf1[j] = (T)0;
@@ -260,7 +267,7 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   T msum = (T)0;
   for (int j = tid; j < g.W * g.H; j += nthr) {
     int r = j / g.W, c = j - r * g.W;
-    T v = rho0[(g.p0 + r) * M + g.m0 + c];
+    T v = rho0_at((int64_t)(g.p0 + r) * M + g.m0 + c);
     buf0[KIND == MJP_BD1D ? c + 1 : elem2d(g, r, c)] = v;
     msum += v;
   }
@@ -268,12 +275,12 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   // row below a 2-D slab is the odd half of the bottom pad pair, the row above
   // the even half of the top pad pair.
   if (KIND == MJP_BD1D) {
-    if (tid == 0 && g.W > 0 && g.m0 >= 1) buf0[0] = rho0[g.m0 - 1];
-    if (tid == 0 && g.W > 0 && g.m1 < M) buf0[g.Wp - 1] = rho0[g.m1];
+    if (tid == 0 && g.W > 0 && g.m0 >= 1) buf0[0] = rho0_at(g.m0 - 1);
+    if (tid == 0 && g.W > 0 && g.m1 < M) buf0[g.Wp - 1] = rho0_at(g.m1);
   } else if (g.H > 0) {
     for (int c = tid; c < g.W; c += nthr) {
-      if (g.p0 >= 1) buf0[(c + 1) * 2 + 1] = rho0[(g.p0 - 1) * M + c];
-      if (g.p1 < P) buf0[((g.Hp + 1) * g.Wp + c + 1) * 2] = rho0[g.p1 * M + c];
+      if (g.p0 >= 1) buf0[(c + 1) * 2 + 1] = rho0_at((int64_t)(g.p0 - 1) * M + c);
+      if (g.p1 < P) buf0[((g.Hp + 1) * g.Wp + c + 1) * 2] = rho0_at((int64_t)g.p1 * M + c);
     }
   }
   if (LL) {
@@ -322,7 +329,10 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   // stencil's critical path); the other warps own columns and runs of rows.
   const int nthr_c = nthr - 32;
   const bool wwarp = warp == nwarps - 1;
-  const int TX = (KIND == MJP_BD1D) ? (g.W < nthr_c ? (g.W > 0 ? g.W : 1) : nthr_c) : (g.W > 0 ? g.W : 1);
+  // Birth-death tiles are one row: every stencil thread takes columns
+  // tid, tid + nthr_c, ... (threads past the row stay idle), so no state has
+  // two owners.
+  const int TX = (KIND == MJP_BD1D) ? nthr_c : (g.W > 0 ? g.W : 1);
   const int TY = nthr_c / TX > 0 ? nthr_c / TX : 1;
   const int tx = tid % TX, ty = wwarp ? TY : tid / TX;
   // 2-D threads walk a run of R pair-rows [ja, jb) of their column.
@@ -373,9 +383,9 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     for (int i = l; i <= h; ++i) {
       double wd = wts[i] + (kp == t_K[i] ? t_tail[i] : 0.0);
       T w = (T)wd;
-      T* o = reinterpret_cast<T*>(p.out) + (int64_t)job * p.out_stride + (int64_t)t_orig[i] * N + gidx;
+      T* o = reinterpret_cast<T*>(p.out) + out_base + (int64_t)t_orig[i] * N + gidx;
       if (sizeof(T) == 4) {
-        float* cp = p.comp + (int64_t)job * p.comp_stride + (int64_t)i * N + gidx;
+        float* cp = p.comp + comp_base + (int64_t)i * N + gidx;
         float s, cc;
         if (kp == t_L[i]) {
           s = __fmul_rn((float)w, (float)rv);
@@ -594,15 +604,25 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
 
 template <typename T, int KIND, bool LL>
 cudaError_t launch_typed(const ChainParams& p, int cluster, int threads, cudaStream_t s) {
-  int tile = tile_elems(KIND, p.M, p.P, (int)p.N, (int)p.slab);
+  int tile = p.tile_max > 0 ? p.tile_max : tile_elems(KIND, p.M, p.P, (int)p.N, (int)p.slab);
   size_t smem = smem_layout(sizeof(T), tile, p.ntimes, p.G, p.nmem, LL).total;
   auto kern = chain_kernel<T, KIND, LL>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (cluster > 8) {
+  // Attributes are raised only when needed, so that launches made during
+  // CUDA-graph capture issue no attribute calls once a size has been set.
+  static int smem_set = 0;
+  static bool nonportable = false;
+  cudaError_t e;
+  if ((int)smem > smem_set) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set = (int)smem;
+  }
+  if (cluster > 8 && !nonportable) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
+    nonportable = true;
   }
+  if (p.B <= 0) return cudaSuccess;  // attribute preparation only
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(p.B * cluster), 1, 1);
   cfg.blockDim = dim3((unsigned)threads, 1, 1);
@@ -666,12 +686,20 @@ int max_clusters_kind(int kind, int cluster, int threads, size_t smem) {
 
 }  // namespace
 
+int chain_stencil_tile(int kind, int64_t M, int64_t P, int64_t slab) {
+  return tile_elems(kind, (int)M, (int)P, (int)(M * P), (int)slab);
+}
+
 int64_t chain_stencil_slab(int kind, int64_t M, int64_t P, int cluster) {
   int64_t N = M * P;
   if (kind == MJP_BD1D) return (N + cluster - 1) / cluster;
   int64_t rows = (P + cluster - 1) / cluster;
   rows += rows & 1;  // row pairs never straddle two CTAs
   return rows * M;
+}
+
+size_t chain_stencil_smem_tile(int precision, int loglik_mode, int tile, int ntimes, int G, int nmem) {
+  return smem_layout(precision == MJP_FP64 ? 8 : 4, tile, ntimes, G, nmem, loglik_mode != 0).total;
 }
 
 size_t chain_stencil_smem(int kind, int precision, int loglik_mode, int64_t M, int64_t P, int64_t slab,
@@ -682,7 +710,6 @@ size_t chain_stencil_smem(int kind, int precision, int loglik_mode, int64_t M, i
 
 cudaError_t launch_chain_stencil(int kind, int precision, int loglik_mode, const ChainParams& p,
                                  int cluster, int threads, cudaStream_t s) {
-  if (p.B <= 0) return cudaSuccess;
   if (precision == MJP_FP64) {
     return loglik_mode ? launch_kind<double, true>(kind, p, cluster, threads, s)
                        : launch_kind<double, false>(kind, p, cluster, threads, s);

@@ -1,0 +1,93 @@
+"""Batches of uneven birth-death instances against the oracle, instance by
+instance (1e-12 FP64 / 1e-6 FP32 max abs), graph replay, autotuning, and the
+full 4096-instance workload (sampled instances + properties for all)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+TOL = {2: 1e-12, 1: 1e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2312_05647_gb300 import build as lib_build
+    lib_build.build()
+    torch.cuda.set_device(0)
+
+
+def _small_batch(n, seed):
+    gen = np.random.default_rng(seed)
+    N = np.concatenate([[1, 2, 3], np.floor(np.exp(gen.uniform(np.log(5), np.log(3000), n - 3)))]).astype(np.int64)
+    lam = gen.uniform(1.0, np.maximum(N / 4.0, 1.5))
+    mu = gen.uniform(0.5, 2.0, n)
+    t = np.exp(gen.uniform(np.log(0.01), np.log(0.6), n))
+    t[0] = 0.0
+    s0 = (gen.random(n) * N * 0.3).astype(np.int64)
+    return N, np.stack([lam, mu], 1), t, s0
+
+
+def _oracle(N, th, t, s0):
+    csr = oracle.build_model(oracle.BD1D, [N], th)
+    r0 = np.zeros(N)
+    r0[s0] = 1.0
+    out, info = oracle.expv(csr, r0, [t])
+    return out[0]
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_batch_matches_oracle(prec):
+    import paper_2312_05647_gb300 as mjp
+    N, th, t, s0 = _small_batch(96, 11)
+    b = mjp.Batch(N, th, t, s0=s0, precision=prec)
+    out = b.run(b.empty_out())
+    b.check()
+    res = b.split(out.double().cpu().numpy())
+    for j in range(len(N)):
+        ref = _oracle(int(N[j]), th[j], t[j], int(s0[j]))
+        assert np.abs(res[j] - ref).max() <= TOL[prec], j
+
+
+def test_batch_graph_and_tune():
+    import paper_2312_05647_gb300 as mjp
+    N, th, t, s0 = _small_batch(200, 12)
+    b = mjp.Batch(N, th, t, s0=s0, precision=1)
+    a = b.run(b.empty_out()).clone()
+    g1 = b.run(b.empty_out(), use_graph=True).clone()
+    out = b.empty_out()
+    cfg = b.tune(out)
+    assert "heavy_cluster" in cfg
+    g2 = b.run(out, use_graph=True)
+    g3 = b.run(out, use_graph=True).clone()
+    b.check()
+    np.testing.assert_array_equal(a.cpu().numpy(), g1.cpu().numpy())
+    np.testing.assert_array_equal(a.cpu().numpy(), g3.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_full_uneven_batch(prec):
+    import torch
+    import paper_2312_05647_gb300 as mjp
+    cfg = synth.bd_batch()
+    N, th, t = cfg["N"], cfg["theta"], cfg["t"]
+    b = mjp.Batch(N, th, t, precision=prec)
+    out = b.run(b.empty_out(), use_graph=True)
+    b.check()
+    res = b.split(out.double().cpu().numpy())
+    mass = np.array([r.sum() for r in res])
+    assert np.abs(mass - 1.0).max() <= (1e-11 if prec == 2 else 2e-3)
+    assert min(r.min() for r in res) >= 0.0
+    # Sampled instances against the oracle: the smallest, the largest state
+    # space and several of moderate cost.
+    work = np.array([oracle.K_paper(1.1 * max(th[j, 0] + th[j, 1] * (N[j] - 2), th[j, 1] * (N[j] - 1)) * t[j])
+                     * N[j] for j in range(len(N))])
+    pick = [int(np.argmin(N)), int(np.argmin(work))]
+    cheap = np.nonzero(work < 3e8)[0]
+    pick += [int(cheap[np.argmax(work[cheap])]), int(cheap[np.argmax(N[cheap])])]
+    pick += list(np.random.default_rng(0).choice(cheap, 4, replace=False))
+    for j in pick:
+        ref = _oracle(int(N[j]), th[j], t[j], 0)
+        assert np.abs(res[j] - ref).max() <= TOL[prec], j

@@ -105,3 +105,42 @@ def test_obs_validation(L):
                           counts.ctypes.data_as(capi._f64p), mptr.ctypes.data_as(capi._i64p),
                           members.ctypes.data_as(capi._i32p), rho0.ctypes.data_as(capi._f64p))
     assert rc == -1
+
+
+def _csr(L, n, row_ptr, col, rate, prec=capi.FP32):
+    h = ctypes.c_void_p()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    c = np.ascontiguousarray(col, dtype=np.int32)
+    v = np.ascontiguousarray(rate, dtype=np.float64)
+    return L.rate_model_create_csr(ctypes.byref(h), n, rp.ctypes.data_as(capi._i64p), c.ctypes.data_as(capi._i32p),
+                                   v.ctypes.data_as(capi._f64p), prec)
+
+
+def test_csr_validation(L):
+    # Malformed CSR is rejected on the host with MJP_ERR_CSR, before any device work.
+    assert _csr(L, 3, [0, 1, 2, 2], [1, 2], [1.0, 2.0], prec=7) == -1
+    assert _csr(L, 3, [1, 1, 2, 2], [1, 2], [1.0, 2.0]) == -2          # row_ptr[0] != 0
+    assert _csr(L, 3, [0, 2, 1, 2], [1, 2], [1.0, 2.0]) == -2          # not monotone
+    assert _csr(L, 3, [0, 1, 2, 2], [1, 1], [1.0, 2.0]) == -2          # diagonal entry (row 1 -> 1)
+    assert _csr(L, 3, [0, 1, 2, 2], [1, 3], [1.0, 2.0]) == -2          # column out of range
+    assert _csr(L, 3, [0, 1, 2, 2], [1, 2], [1.0, -2.0]) == -2         # negative rate
+    assert _csr(L, 3, [0, 1, 2, 2], [1, 2], [1.0, float("inf")]) == -2
+    assert b"rate" in L.mjp_last_error()
+
+
+def test_batch_validation(L):
+    h = ctypes.c_void_p()
+    N = np.array([10, 0], np.int64)
+    th = np.ones(4)
+    t = np.ones(2)
+    rc = L.expv_batch_create(ctypes.byref(h), capi.BD1D, 2, N.ctypes.data_as(capi._i64p), th.ctypes.data_as(capi._f64p),
+                             t.ctypes.data_as(capi._f64p), None, capi.FP32)
+    assert rc == -1
+    N = np.array([10, 20], np.int64)
+    t = np.array([1.0, -1.0])
+    rc = L.expv_batch_create(ctypes.byref(h), capi.BD1D, 2, N.ctypes.data_as(capi._i64p), th.ctypes.data_as(capi._f64p),
+                             t.ctypes.data_as(capi._f64p), None, capi.FP32)
+    assert rc == -1
+    rc = L.expv_batch_create(ctypes.byref(h), capi.TWOSTATE, 2, N.ctypes.data_as(capi._i64p),
+                             th.ctypes.data_as(capi._f64p), t.ctypes.data_as(capi._f64p), None, capi.FP32)
+    assert rc == -8

@@ -209,3 +209,16 @@ def test_loglik_mrna_protein_cluster():
     for b in range(3):
         ref = oracle.loglik(oracle.build_model(synth.MRNA_PROT2D, dims, thetas[b]), rho0, times, obs)
         assert abs(ll[b] - ref) <= PER_OBS[2] * sum(c.sum() for _, c in obs)
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_more_threads_than_states(prec):
+    # Every state has exactly one owning thread, however wide the CTA.
+    from paper_2312_05647_gb300 import OPT_THREADS
+    for N, threads in [(2, 256), (10, 512), (40, 1024)]:
+        rho0 = synth.delta(N, 0)
+        times = [0.2, 1.0]
+        r, _ = ora_expv(synth.BD1D, [N], [3.0, 1.0], rho0, times)
+        for _ in range(3):
+            g, _ = gpu_expv(synth.BD1D, [N], [3.0, 1.0], prec, rho0, times, opts={OPT_THREADS: threads})
+            assert np.abs(g - r).max() <= TOL[prec]
