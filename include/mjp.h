@@ -232,6 +232,34 @@ int expv_batch_check(mjp_batch* b, void* stream);
 void expv_batch_destroy(mjp_batch* b);
 
 /*
+ * expv_series_static -- the same transient distributions as expv_series for a
+ * stencil model in FP32, for callers that cannot allocate device memory while
+ * they run (applications whose device memory belongs to their own pool or has
+ * a fixed budget, plugins whose host framework owns the allocator, loops that
+ * must not risk the device-wide synchronisation of cudaMalloc/cudaFree).  The
+ * paper has no counterpart: this is an interface variant, not a method.
+ *
+ * No handle: kind/dims/theta describe the model as for
+ * rate_model_create_stencil; rho0 (device, N floats) and out (device,
+ * ntimes x N floats, row i = rho*(times[i])) are the caller's; times are host
+ * memory.  The call allocates no device memory and no host heap memory on its
+ * success path.  Its scratch (sorted times, truncation windows, status word
+ * and the FP32 Kahan compensation, ntimes x N x 4 bytes) is one static array
+ * of 16 MiB inside the library, which every GPU that loads the library keeps
+ * until the process exits; larger requests fail with MJP_ERR_ARG and a
+ * message giving the size needed.  The first call on a device looks up that
+ * array's device address (once per device, with the device current), so make
+ * it before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (the call resets what must start at zero): calls that
+ * overlap on the GPU -- on different streams, threads or devices sharing a
+ * process -- race, so order them.  The call synchronises `stream` and reports
+ * device-side errors (MJP_ERR_KCAP, MJP_ERR_NUMERIC) itself.
+ * Errors: MJP_ERR_ARG, MJP_ERR_UNSUPPORTED, MJP_ERR_KCAP, MJP_ERR_NUMERIC, MJP_ERR_CUDA.
+ */
+int expv_series_static(int kind, const int64_t* dims, int ndims, const double* theta, int ntheta,
+                       const float* rho0, const double* times, int ntimes, float* out, void* stream);
+
+/*
  * Synchronise `stream` and report device-side errors recorded by earlier
  * asynchronous calls on this model (K above the cap, non-finite values, a
  * bounded wait that ran out).  Clears the record.  Returns MJP_OK or the
