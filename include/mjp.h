@@ -83,6 +83,8 @@ extern "C" {
 #define MJP_OPT_THREADS 3       /* threads per CTA for stencil chains, one warp of which forms the weights (0 = automatic; else a multiple of 32 in [64, 1024]) */
 #define MJP_OPT_CLUSTER 4       /* CTAs per instance for stencil chains (0 = automatic; 1, 2, 4, 8, 16) */
 #define MJP_OPT_PROFILE 5       /* 1: record CUDA events around each kernel of a call (see rate_model_last_timing) */
+#define MJP_OPT_ARENA 6         /* capacity (elements) of the planner's Poisson-weight store; 0 = automatic.  Windows
+                                   that do not fit are generated in the chain by Algorithm 2's recurrence instead. */
 
 typedef struct mjp_model mjp_model;
 typedef struct mjp_obs mjp_obs;

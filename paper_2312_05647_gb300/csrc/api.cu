@@ -60,7 +60,13 @@ struct mjp_model {
   // workspace (scratch owned by the handle)
   DevBuf d_times, d_orig, d_win, d_info, d_theta, d_comp, d_status, d_ll;
   DevBuf d_rho2, d_outp, d_wtab, d_woff, d_L, d_K;
+  // Poisson-weight arena filled by the planner (elements of the model precision)
+  DevBuf d_arena, d_arena_ctl;
+  int64_t arena_cap = 0;
+  bool arena_grow = false;
+  bool arena_fixed = false;  // capacity set by MJP_OPT_ARENA (never grown)
   ~mjp_model() {
+    d_arena.release(); d_arena_ctl.release();
     d_slice_ptr.release(); d_slice_len.release(); d_col.release(); d_val.release(); d_diag.release();
     d_perm.release(); d_rho2.release(); d_outp.release(); d_wtab.release(); d_woff.release();
     d_L.release(); d_K.release();
@@ -160,6 +166,50 @@ int mark(mjp_model* m, int i, cudaStream_t s) {
 }
 
 int map_status(int st);
+
+// Closed-form upper bound of max_n e_n for a stencil model (sizes the arena).
+double omega_bound(const mjp_model* m, const double* th) {
+  switch (m->kind) {
+    case MJP_BD1D: return 1.1 * (th[0] + th[1] * (double)(m->M - 1));
+    case MJP_TWOSTATE: return 1.1 * (th[0] + th[1] * (double)(m->M - 1) + th[2] + th[3]);
+    case MJP_MRNA_PROT2D:
+      return 1.1 * (th[0] + (th[1] + th[2]) * (double)(m->M - 1) + th[3] * (double)(m->P - 1));
+    default: return 0.0;
+  }
+}
+
+// Make room in the weight arena for B instances at the given times: windows
+// hold at most 16 sqrt(x) + 3 weights (x = Omega t).  The thetas are the
+// call's when they are on the host, else the model's (the arena then grows
+// after a call that reported overflow).  Fills the arena fields of pp.
+int arena_prepare(mjp_model* m, const double* host_theta, int B, const double* times, int nt, cudaStream_t s,
+                  PlanParams& pp) {
+  const int ntheta = (int)m->theta.size();
+  double need = 0.0;
+  for (int b = 0; b < B; ++b) {
+    const double* th = host_theta ? host_theta + (int64_t)b * ntheta : m->theta.data();
+    const double om = omega_bound(m, th) * (host_theta ? 1.0 : 1.5);
+    for (int i = 0; i < nt; ++i) need += 16.0 * std::sqrt(om * times[i]) + 3.0;
+  }
+  int64_t want = (int64_t)std::min(need, 2.0e9);
+  if (m->arena_grow) want = std::max<int64_t>(want, 2 * m->arena_cap);
+  m->arena_grow = false;
+  if (want > m->arena_cap && !m->arena_fixed) {
+    const size_t elt = m->precision == MJP_FP64 ? 8 : 4;
+    int rc = m->d_arena.ensure(elt * (size_t)want);
+    if (rc) return rc;
+    m->arena_cap = want;
+  }
+  int rc = m->d_arena_ctl.ensure(16);
+  if (rc) return rc;
+  MJP_CUDA(cudaMemsetAsync(m->d_arena_ctl.p, 0, 16, s));
+  pp.arena = m->d_arena.p;
+  pp.arena_cap = m->arena_cap;
+  pp.arena_used = m->d_arena_ctl.as<unsigned long long>();
+  pp.arena_over = reinterpret_cast<int*>(m->d_arena_ctl.as<char>() + 8);
+  pp.arena_fp64 = m->precision == MJP_FP64 ? 1 : 0;
+  return MJP_OK;
+}
 
 // The general-CSR chain: planner, windows back to the host (the number of
 // launches is the largest K), weight table, rho0 into the in-degree order,
@@ -414,6 +464,19 @@ int rate_model_set_option(mjp_model* m, int option, int64_t value) {
       if (value != 0 && (value % 32 != 0 || value < 64 || value > 1024)) return fail(MJP_ERR_ARG, "threads must be 0 or a multiple of 32 in [64, 1024]");
       m->threads = (int)value;
       return MJP_OK;
+    case MJP_OPT_ARENA:
+      if (value < 0) return fail(MJP_ERR_ARG, "arena capacity must be >= 0");
+      m->d_arena.release();
+      m->arena_cap = 0;
+      if (value > 0) {
+        int rc = m->d_arena.ensure((m->precision == MJP_FP64 ? 8 : 4) * (size_t)value);
+        if (rc) return rc;
+        m->arena_cap = value;
+        m->arena_fixed = true;
+      } else {
+        m->arena_fixed = false;
+      }
+      return MJP_OK;
     case MJP_OPT_PROFILE:
       if (value != 0 && value != 1) return fail(MJP_ERR_ARG, "profile must be 0 or 1");
       m->profile = (int)value;
@@ -447,6 +510,11 @@ int rate_model_last_timing(mjp_model* m, double* ms_plan, double* ms_chain) {
 int rate_model_check(mjp_model* m, void* stream) {
   if (!m) return fail(MJP_ERR_ARG, "NULL model");
   MJP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (m->d_arena_ctl.p) {  // windows that did not fit ran the in-kernel recurrence: grow
+    int over = 0;
+    MJP_CUDA(cudaMemcpy(&over, m->d_arena_ctl.as<char>() + 8, sizeof(int), cudaMemcpyDeviceToHost));
+    if (over) m->arena_grow = true;
+  }
   if (!m->d_status.p) return MJP_OK;
   int st = 0;
   MJP_CUDA(cudaMemcpy(&st, m->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
@@ -510,11 +578,13 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
   pp.trunc_mode = trunc_mode; pp.tol = tol; pp.omega_factor = 1.1; pp.omega_fixed = -1.0;
   pp.kcap = m->kcap; pp.win = m->d_win.as<Win>(); pp.info = m->d_info.as<JobInfo>();
   pp.status = m->d_status.as<int>();
+  if ((rc = arena_prepare(m, m->theta.data(), 1, st.data(), nt, s, pp))) return rc;
   if ((rc = mark(m, 0, s))) return rc;
   MJP_CUDA(launch_plan(pp, s));
   if ((rc = mark(m, 1, s))) return rc;
 
   ChainParams cp = {};
+  cp.arena = pp.arena;
   cp.M = (int32_t)m->M; cp.P = (int32_t)m->P; cp.N = m->N;
   cp.ntheta = pp.ntheta; cp.theta = pp.theta; cp.B = 1; cp.ntimes = nt;
   cp.orig = m->d_orig.as<int32_t>(); cp.win = pp.win; cp.info = pp.info; cp.rho0 = rho0;
@@ -678,11 +748,13 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   pp.trunc_mode = trunc_mode; pp.tol = tol; pp.omega_factor = 1.1; pp.omega_fixed = -1.0;
   pp.kcap = m->kcap; pp.win = m->d_win.as<Win>(); pp.info = m->d_info.as<JobInfo>();
   pp.status = m->d_status.as<int>();
+  if ((rc = arena_prepare(m, where == MJP_PTR_HOST ? theta : nullptr, B, obs->times.data(), nt, s, pp))) return rc;
   if ((rc = mark(m, 0, s))) return rc;
   MJP_CUDA(launch_plan(pp, s));
   if ((rc = mark(m, 1, s))) return rc;
 
   ChainParams cp = {};
+  cp.arena = pp.arena;
   cp.M = (int32_t)m->M; cp.P = (int32_t)m->P; cp.N = m->N;
   cp.ntheta = ntheta; cp.theta = d_theta; cp.B = B; cp.ntimes = nt;
   cp.orig = nullptr; cp.win = pp.win; cp.info = pp.info;

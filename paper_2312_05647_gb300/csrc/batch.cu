@@ -58,6 +58,8 @@ struct mjp_batch {
   Group groups[kGroups];
   bool uploaded = false, grouped = false;
   DevBuf d_theta, d_times, d_jobN, d_off, d_s0, d_win, d_info, d_comp, d_status;
+  DevBuf d_arena, d_arena_ctl;  // planner's Poisson-weight store and its counters
+  int64_t arena_cap = 0;
   cudaStream_t side[kGroups] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kGroups] = {};
   cudaGraphExec_t exec = nullptr;
@@ -74,6 +76,7 @@ struct mjp_batch {
     for (auto& g : groups) g.d_map.release();
     d_theta.release(); d_times.release(); d_jobN.release(); d_off.release(); d_s0.release();
     d_win.release(); d_info.release(); d_comp.release(); d_status.release();
+    d_arena.release(); d_arena_ctl.release();
   }
 };
 
@@ -143,7 +146,12 @@ int upload(mjp_batch* b) {
       (rc = b->d_info.ensure(sizeof(JobInfo) * n)) || (rc = b->d_status.ensure(sizeof(int))))
     return rc;
   if (b->precision == MJP_FP32 && (rc = b->d_comp.ensure(sizeof(float) * b->off[n]))) return rc;
-  (void)elt;
+  // Every window holds at most 16 sqrt(x) + 3 weights, x = Omega t (Omega is
+  // known exactly here: the birth-death maximum exit rate).
+  double need = 0.0;
+  for (int j = 0; j < n; ++j) need += 16.0 * std::sqrt(1.1 * bd_max_exit(b->N[j], b->theta[2 * j], b->theta[2 * j + 1]) * b->t[j]) + 4.0;
+  b->arena_cap = (int64_t)std::min(need, 2.0e9);
+  if ((rc = b->d_arena.ensure(elt * (size_t)b->arena_cap)) || (rc = b->d_arena_ctl.ensure(16))) return rc;
   std::vector<int32_t> n32(b->N.begin(), b->N.end());
   MJP_CUDA(cudaMemcpy(b->d_theta.p, b->theta.data(), sizeof(double) * 2 * n, cudaMemcpyHostToDevice));
   MJP_CUDA(cudaMemcpy(b->d_times.p, b->t.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
@@ -169,6 +177,11 @@ int enqueue(mjp_batch* b, void* out, cudaStream_t s) {
   pp.trunc_mode = MJP_TRUNC_PAPER; pp.tol = 0.0; pp.omega_factor = 1.1; pp.omega_fixed = -1.0;
   pp.kcap = (int64_t)1 << 26; pp.win = b->d_win.as<Win>(); pp.info = b->d_info.as<JobInfo>();
   pp.status = b->d_status.as<int>(); pp.jobN = b->d_jobN.as<int32_t>();
+  pp.arena = b->d_arena.p; pp.arena_cap = b->arena_cap;
+  pp.arena_used = b->d_arena_ctl.as<unsigned long long>();
+  pp.arena_over = reinterpret_cast<int*>(b->d_arena_ctl.as<char>() + 8);
+  pp.arena_fp64 = b->precision == MJP_FP64 ? 1 : 0;
+  MJP_CUDA(cudaMemsetAsync(b->d_arena_ctl.p, 0, 16, s));
   MJP_CUDA(launch_plan(pp, s));
   MJP_CUDA(cudaEventRecord(b->ev_fork, s));
   for (int gi = 0; gi < kGroups; ++gi) {
@@ -181,7 +194,7 @@ int enqueue(mjp_batch* b, void* out, cudaStream_t s) {
     cp.out = out; cp.out_stride = 0; cp.comp = b->d_comp.as<float>(); cp.comp_stride = 0;
     cp.renorm = 0; cp.slab = 1; cp.status = pp.status;
     cp.jobN = pp.jobN; cp.job_off = b->d_off.as<int64_t>(); cp.job_map = g.d_map.as<int32_t>();
-    cp.job_s0 = b->d_s0.as<int64_t>(); cp.tile_max = g.tile;
+    cp.job_s0 = b->d_s0.as<int64_t>(); cp.tile_max = g.tile; cp.arena = b->d_arena.p;
     MJP_CUDA(launch_chain_stencil(MJP_BD1D, b->precision, 0, cp, g.cluster, g.threads, b->side[gi]));
     MJP_CUDA(cudaEventRecord(b->ev_join[gi], b->side[gi]));
     MJP_CUDA(cudaStreamWaitEvent(s, b->ev_join[gi], 0));

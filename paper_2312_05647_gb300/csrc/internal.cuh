@@ -12,6 +12,8 @@ namespace mjp {
 constexpr int kMaxTimes = 256;     // observation times per call
 constexpr int kMaxGroups = 8192;   // observation groups per loglik call
 constexpr int kMaxTheta = 8;
+constexpr int kWeightLead = 4;   // jumps the weight prefetch runs ahead
+constexpr int kWeightRing = 6;   // ring slots (> lead + 1)
 
 // Device status word bits (first error wins; read by rate_model_check).
 enum DevStatus : int {
@@ -27,11 +29,12 @@ enum DevStatus : int {
 // the paper's recurrence P_k = P_{k-1} x / k, started from P_L (normalised,
 // log-safe) instead of exp(-x), which underflows for x > 708.
 struct Win {
-  double x;     // Omega * t
-  double PL;    // Poisson(L | x)
-  double tail;  // epsilon = sum_{k > K} Poisson(k | x) = 1 - sum_{k <= K}
-  int64_t L;    // first jump index with non-negligible weight (left mass < 1e-20)
-  int64_t K;    // last jump index (Algorithm 2's loop exit)
+  double x;      // Omega * t
+  double PL;     // Poisson(L | x)
+  double tail;   // epsilon = sum_{k > K} Poisson(k | x) = 1 - sum_{k <= K}
+  int64_t L;     // first jump index with non-negligible weight (left mass < e^-50)
+  int64_t K;     // last jump index (Algorithm 2's loop exit)
+  int64_t woff;  // offset of P_L..P_K (tail folded into P_K) in the weight arena, -1 if absent
 };
 
 struct JobInfo {
@@ -61,6 +64,14 @@ struct PlanParams {
   // and per-job times (times + job * ntimes).
   const int32_t* jobN;
   int times_per_job;
+  // Weight arena (nullable): windows are stored at offsets taken with an
+  // atomic counter; a window that does not fit gets woff = -1 and sets
+  // *arena_over (the chain then runs the recurrence for it).
+  void* arena;
+  int64_t arena_cap;                // elements
+  unsigned long long* arena_used;   // element counter (zeroed before the planner)
+  int* arena_over;
+  int arena_fp64;                   // element type: 1 = double, 0 = float
 };
 
 // Chain inputs (stencil models).
@@ -97,6 +108,7 @@ struct ChainParams {
   const int32_t* job_map;  // cluster index -> job (longest first)
   const int64_t* job_s0;   // rho0 = delta at s0 for each job (instead of rho0)
   int tile_max;            // padded tile size of the largest job in the launch
+  const void* arena;       // planner's weight arena (T), indexed by Win::woff
 };
 
 // One jump of the general-CSR chain (csr.cu).

@@ -94,6 +94,7 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
     r.K = (p.trunc_mode == MJP_TRUNC_PAPER) ? 1 : 0;
     r.PL = 1.0;
     r.tail = 0.0;
+    r.woff = -1;
     if (lane == 0) *dst = r;
     return;
   }
@@ -102,7 +103,7 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
   if (!(kstar + 1.0 <= (double)p.kcap)) {  // also catches inf/NaN; nothing loops
     if (lane == 0) {
       set_status(p.status, kStatusKcap);
-      r.L = 0; r.K = 0; r.PL = 1.0; r.tail = 0.0;
+      r.L = 0; r.K = 0; r.PL = 1.0; r.tail = 0.0; r.woff = -1;
       *dst = r;
     }
     return;
@@ -191,6 +192,44 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
   r.K = K;
   r.PL = wL / W;
   r.tail = tail;
+  r.woff = -1;
+  // Store P_L..P_K (the tail folded into P_K) in the arena, recomputing the
+  // same product scans, so the chain reads the weights instead of running
+  // the recurrence.
+  if (p.arena) {
+    const int64_t size = K - L + 1;
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(p.arena_used, (unsigned long long)size);
+    off = __shfl_sync(kFull, off, 0);
+    if ((int64_t)off + size <= p.arena_cap) {
+      r.woff = (int64_t)off;
+      auto put = [&](int64_t k, double w) {
+        double v = __ddiv_rn(w, W);
+        if (k == K) v = v + tail;
+        if (p.arena_fp64) reinterpret_cast<double*>(p.arena)[off + (k - L)] = v;
+        else reinterpret_cast<float*>(p.arena)[off + (k - L)] = (float)v;
+      };
+      if (lane == 0) put(m, 1.0);
+      carry = 1.0;
+      for (int64_t base = m + 1; base <= K; base += 32) {
+        int64_t k = base + lane;
+        double term = (k <= R) ? __ddiv_rn(x, (double)k) : 1.0;
+        double w = __dmul_rn(warp_incl_prod(term, lane), carry);
+        carry = __shfl_sync(kFull, w, 31);
+        if (k <= K) put(k, w);
+      }
+      carry = 1.0;
+      for (int64_t base = m - 1; base >= L; base -= 32) {
+        int64_t k = base - lane;
+        double term = (k >= L) ? __ddiv_rn((double)(k + 1), x) : 1.0;
+        double w = __dmul_rn(warp_incl_prod(term, lane), carry);
+        carry = __shfl_sync(kFull, w, 31);
+        if (k >= L) put(k, w);
+      }
+    } else if (lane == 0 && p.arena_over) {
+      atomicOr(p.arena_over, 1);
+    }
+  }
   if (lane == 0) *dst = r;
 }
 

@@ -51,6 +51,21 @@ __device__ __forceinline__ void cluster_wait() {
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Asynchronous global -> shared copy of one float or double (cp.async).
+__device__ __forceinline__ void cp_async_elem(float* sdst, const float* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double* sdst, const double* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Local tile geometry of one CTA.
 //  - birth-death chain: one row of W owned columns plus one zero pad cell on
 //    each side;
@@ -97,7 +112,7 @@ __host__ __device__ inline int tile_elems(int kind, int M, int P, int N, int sla
 }
 
 struct Smem {
-  size_t buf1, tx, tPL, ttail, tL, tK, torig, pw, red, memloc, gptr, mptr, acc_s, acc_c, total;
+  size_t buf1, tx, tPL, ttail, tL, tK, twoff, torig, pw, ring, red, memloc, gptr, mptr, acc_s, acc_c, total;
 };
 
 __host__ __device__ inline Smem smem_layout(size_t elt, int tile, int nt, int G, int nmem, bool ll) {
@@ -111,7 +126,9 @@ __host__ __device__ inline Smem smem_layout(size_t elt, int tile, int nt, int G,
   s.tL = o; o += 8 * (size_t)nt;
   s.tK = o; o += 8 * (size_t)nt;
   s.torig = o; o += align_up(4 * (size_t)nt, 8);
+  s.twoff = o; o += 8 * (size_t)nt;
   s.pw = o; o += 16 * (size_t)nt;
+  s.ring = o; o += align_up(elt * kWeightRing * (size_t)nt, 8);
   s.red = o; o += 8 * 2 * 33;
   s.memloc = o;
   if (ll) o += align_up(4 * (size_t)nmem, 8);
@@ -211,7 +228,10 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   long long* t_L = reinterpret_cast<long long*>(smem + L.tL);
   long long* t_K = reinterpret_cast<long long*>(smem + L.tK);
   int* t_orig = reinterpret_cast<int*>(smem + L.torig);
-  double* pw = reinterpret_cast<double*>(smem + L.pw);   // [2][nt]
+  double* pw = reinterpret_cast<double*>(smem + L.pw);   // [2][nt] FP64 recurrence state
+  long long* t_woff = reinterpret_cast<long long*>(smem + L.twoff);
+  T* ring = reinterpret_cast<T*>(smem + L.ring);         // [kWeightRing][nt] weight of each jump
+  const T* arena = reinterpret_cast<const T*>(p.arena);
   double* red = reinterpret_cast<double*>(smem + L.red);  // [2][33]
   int* memloc = reinterpret_cast<int*>(smem + L.memloc);
   int* s_gptr = reinterpret_cast<int*>(smem + L.gptr);  // group ranges per time
@@ -251,7 +271,10 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     t_L[i] = w.L;
     t_K[i] = w.K;
     t_orig[i] = p.orig ? p.orig[i] : i;
-    pw[i] = (w.L == 0) ? w.PL : 0.0;  // weights of jump 0
+    t_woff[i] = w.woff;
+    pw[i] = (w.L == 0) ? w.PL : 0.0;  // recurrence state at jump 0
+    if (w.L == 0)                     // weight of jump 0 (tail folded in)
+      ring[i] = (w.woff >= 0 && arena) ? arena[w.woff] : (T)(w.PL + (w.K == 0 ? w.tail : 0.0));
   }
   const double omega = p.info[job].omega;
   const int64_t Kmax = p.info[job].Kmax;
@@ -324,6 +347,18 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     while (h + 1 < nt && t_L[h + 1] <= k) ++h;
   };
   advance(0, lo, hi);
+  // Weight prefetch pointer: active times of jump k + lead.
+  int flo = 0, fhi = -1;
+  if (warp == nwarps - 1) {  // the weights warp
+    for (int64_t kf = 1; kf <= kWeightLead; ++kf) {
+      advance(kf, flo, fhi);
+      if (kf <= Kmax)
+        for (int i = flo + lane; i <= fhi; i += 32)
+          if (t_woff[i] >= 0)
+            cp_async_elem(ring + (int)(kf % kWeightRing) * nt + i, arena + t_woff[i] + (kf - t_L[i]));
+      cp_async_commit();
+    }
+  }
 
   // Thread layout: the last warp forms the Poisson weights (FP64, off the
   // stencil's critical path); the other warps own columns and runs of rows.
@@ -348,10 +383,9 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   const int acc_id = acc_ww ? lane : tid, acc_stride = acc_ww ? 32 : nthr;
 
   // LOGLIK: acc_g += w_i f sum_{s in g} rho_k[s] over this CTA's states.
-  auto group_accumulate = [&](const T* cur, int l, int h, int64_t k, const double* wts, T f) {
+  auto group_accumulate = [&](const T* cur, int l, int h, const T* wts, T f) {
     for (int i = l; i <= h; ++i) {
-      double wd = wts[i] + (k == t_K[i] ? t_tail[i] : 0.0);
-      T w = f_mul((T)wd, f);
+      T w = f_mul(wts[i], f);
       const int g0 = s_gptr[i], g1 = s_gptr[i + 1];
       for (int gq = g0 + acc_id; gq < g1; gq += acc_stride) {
         const int q0 = s_mptr[gq], q1 = s_mptr[gq + 1];
@@ -379,10 +413,9 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   };
 
   // EXPV: rho*_i += w rho_{k-1}[n] for the active times (Kahan in FP32).
-  auto expv_accumulate = [&](T rv, int64_t gidx, int64_t kp, int l, int h, const double* wts) {
+  auto expv_accumulate = [&](T rv, int64_t gidx, int64_t kp, int l, int h, const T* wts) {
     for (int i = l; i <= h; ++i) {
-      double wd = wts[i] + (kp == t_K[i] ? t_tail[i] : 0.0);
-      T w = (T)wd;
+      const T w = wts[i];
       T* o = reinterpret_cast<T*>(p.out) + out_base + (int64_t)t_orig[i] * N + gidx;
       if (sizeof(T) == 4) {
         float* cp = p.comp + comp_base + (int64_t)i * N + gidx;
@@ -446,8 +479,10 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     const int par = (int)((k - 1) & 1);
     const T* src = reinterpret_cast<const T*>(smem + buf_off[par]);
     T* dst = reinterpret_cast<T*>(smem + buf_off[par ^ 1]);
-    const double* wprev = pw + par * nt;
-    double* wcur = pw + (par ^ 1) * nt;
+    const double* rprev = pw + par * nt;    // FP64 recurrence state, jump k-1
+    double* rcur = pw + (par ^ 1) * nt;     // jump k
+    const T* wprev = ring + (int)((k - 1) % kWeightRing) * nt;  // weights of jump k-1
+    T* wcur = ring + (int)(k % kWeightRing) * nt;
     const int plo = lo, phi = hi;
     int clo = lo, chi = hi;
     advance(k, clo, chi);
@@ -457,11 +492,28 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
       double tot = cluster_total(red + (int)((k - 1) & 1) * 33);
       f = (T)(tot > 0.0 ? mass0 / tot : 1.0);
     }
-    if (wwarp && jump) {  // weights of jump k (Algorithm 2: P *= x/k)
-      for (int i = clo + lane; i <= chi; i += 32)
-        wcur[i] = (k == t_L[i]) ? t_PL[i] : __dmul_rn(wprev[i], __ddiv_rn(t_x[i], (double)k));
+    if (wwarp) {
+      // Weights of jump k + lead from the planner's arena, copied straight
+      // into the ring (cp.async, one group per jump) ...
+      const int64_t kf = k + kWeightLead;
+      advance(kf, flo, fhi);
+      if (kf <= Kmax)
+        for (int i = flo + lane; i <= fhi; i += 32)
+          if (t_woff[i] >= 0)
+            cp_async_elem(ring + (int)(kf % kWeightRing) * nt + i, arena + t_woff[i] + (kf - t_L[i]));
+      cp_async_commit();
+      // ... and, for windows without a stored copy, Algorithm 2's recurrence
+      // P_k = P_{k-1} x / k (the tail is added at k = K).
+      if (jump)
+        for (int i = clo + lane; i <= chi; i += 32) {
+          if (t_woff[i] >= 0) continue;
+          const double P = (k == t_L[i]) ? t_PL[i] : __dmul_rn(rprev[i], __ddiv_rn(t_x[i], (double)k));
+          rcur[i] = P;
+          wcur[i] = (T)(P + (k == t_K[i] ? t_tail[i] : 0.0));
+        }
+      cp_async_wait<kWeightLead>();  // jump k's copy (issued lead jumps ago) has landed
     }
-    if (LL && acc_me) group_accumulate(src, plo, phi, k - 1, wprev, f);
+    if (LL && acc_me) group_accumulate(src, plo, phi, wprev, f);
     T part = (T)0;
     if (KIND == MJP_BD1D) {
       for (int m = wwarp ? g.m1 : g.m0 + tx; m < g.m1; m += TX) {
@@ -563,6 +615,7 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     hi = chi;
   }
 
+  if (wwarp) cp_async_wait<0>();
   if (LL) {
     // ---- epilogue: sum_g c_g log(a_g), partial sums of all CTAs ------------
     if (rank == 0) {

@@ -222,3 +222,18 @@ def test_more_threads_than_states(prec):
         for _ in range(3):
             g, _ = gpu_expv(synth.BD1D, [N], [3.0, 1.0], prec, rho0, times, opts={OPT_THREADS: threads})
             assert np.abs(g - r).max() <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+@pytest.mark.parametrize("cap", [1, 3000])
+def test_weight_store_fallback(prec, cap):
+    # A full weight store (cap 1) or a partly full one (3000 elements: the
+    # short early windows fit, the long late ones do not) sends windows to
+    # the in-kernel recurrence; results stay within tolerance.
+    from paper_2312_05647_gb300 import OPT_ARENA
+    cfg = synth.twostate_promoter(N_R=150)
+    times = [0.3, 1.0, 4.0, 9.0]
+    g, gi = gpu_expv(cfg["kind"], cfg["dims"], cfg["theta"], prec, cfg["rho0"], times, opts={OPT_ARENA: cap})
+    r, ri = ora_expv(cfg["kind"], cfg["dims"], cfg["theta"], cfg["rho0"], times)
+    assert list(gi["K"]) == list(ri["K"])
+    assert np.abs(g - r).max() <= TOL[prec]
