@@ -82,6 +82,7 @@ struct mjp_obs {
   int ntimes = 0;
   int G = 0;
   int nmem = 0;
+  int maxmem = 0;  // most members in one group
   std::vector<double> times;  // ascending (host copy)
   DevBuf d_times, d_gptr, d_counts, d_mptr, d_members, d_rho64, d_rho32;
   ~mjp_obs() {
@@ -661,6 +662,7 @@ int mjp_obs_create(mjp_obs** out, int64_t n, int ntimes, const double* times,
   o->ntimes = ntimes;
   o->G = (int)G;
   o->nmem = (int)(mp.back());
+  for (size_t g = 0; g + 1 < mp.size(); ++g) o->maxmem = std::max<int>(o->maxmem, (int)(mp[g + 1] - mp[g]));
   o->times = st;
   int rc = 0;
   if ((rc = o->d_times.ensure(sizeof(double) * ntimes)) || (rc = o->d_gptr.ensure(sizeof(int64_t) * gp.size())) ||
@@ -727,7 +729,9 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   const int nt = obs->ntimes;
   int C, T;
   int64_t slab;
-  int rc = stencil_config(m, 1, nt, obs->G, obs->nmem, &C, &T, &slab);
+  // The chain keeps a generic member list only for groups of > 2 members.
+  const int nmem_list = obs->maxmem > 2 ? obs->nmem : 0;
+  int rc = stencil_config(m, 1, nt, obs->G, nmem_list, &C, &T, &slab);
   if (rc) return rc;
   if ((rc = ensure_status(m))) return rc;
   if ((rc = m->d_win.ensure(sizeof(Win) * (size_t)nt * B))) return rc;
@@ -761,7 +765,7 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   cp.rho0 = (m->precision == MJP_FP64) ? obs->d_rho64.p : obs->d_rho32.p;
   cp.gptr = obs->d_gptr.as<int64_t>(); cp.counts = obs->d_counts.as<double>();
   cp.mptr = obs->d_mptr.as<int64_t>(); cp.members = obs->d_members.as<int32_t>();
-  cp.G = obs->G; cp.nmem = obs->nmem; cp.ll = d_out;
+  cp.G = obs->G; cp.nmem = nmem_list; cp.ll = d_out;
   cp.renorm = (m->precision == MJP_FP32) ? m->renorm : 0;
   cp.slab = slab; cp.status = pp.status;
   MJP_CUDA(launch_chain_stencil(m->kind, m->precision, 1, cp, C, T, s));

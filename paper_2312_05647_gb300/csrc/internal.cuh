@@ -97,7 +97,7 @@ struct ChainParams {
   const int64_t* mptr;     // device, G + 1
   const int32_t* members;  // device
   int G;
-  int nmem;                // members in all groups
+  int nmem;                // length of the generic member list kept on chip (0: every group has <= 2 members)
   double* ll;              // device, B
   int renorm;              // period in jumps (0 = off)
   int64_t slab;            // states per CTA of the cluster (whole rows for 2-D models)

@@ -112,7 +112,8 @@ __host__ __device__ inline int tile_elems(int kind, int M, int P, int N, int sla
 }
 
 struct Smem {
-  size_t buf1, tx, tPL, ttail, tL, tK, twoff, torig, pw, ring, red, memloc, gptr, mptr, acc_s, acc_c, total;
+  size_t buf1, tx, tPL, ttail, tL, tK, twoff, twb, torig, pw, ring, red, memloc, gptr, mptr, gloc, gtime, acc_s,
+      acc_c, total;
 };
 
 __host__ __device__ inline Smem smem_layout(size_t elt, int tile, int nt, int G, int nmem, bool ll) {
@@ -127,15 +128,23 @@ __host__ __device__ inline Smem smem_layout(size_t elt, int tile, int nt, int G,
   s.tK = o; o += 8 * (size_t)nt;
   s.torig = o; o += align_up(4 * (size_t)nt, 8);
   s.twoff = o; o += 8 * (size_t)nt;
+  s.twb = o; o += 8 * (size_t)nt;
   s.pw = o; o += 16 * (size_t)nt;
   s.ring = o; o += align_up(elt * kWeightRing * (size_t)nt, 8);
   s.red = o; o += 8 * 2 * 33;
+  // nmem > 0 only when some group has more than two members: the generic
+  // member list; otherwise each group's (at most two) members are resolved
+  // once into gloc.
   s.memloc = o;
   if (ll) o += align_up(4 * (size_t)nmem, 8);
   s.gptr = o;
   if (ll) o += align_up(4 * (size_t)(nt + 1), 8);
   s.mptr = o;
-  if (ll) o += align_up(4 * (size_t)(G + 1), 8);
+  if (ll && nmem > 0) o += align_up(4 * (size_t)(G + 1), 8);
+  s.gloc = o;
+  if (ll) o += 8 * (size_t)G;
+  s.gtime = o;
+  if (ll) o += align_up(2 * (size_t)G, 8);
   s.acc_s = o;
   if (ll) {
     o += align_up(elt * (size_t)G, 8);
@@ -234,6 +243,9 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   const T* arena = reinterpret_cast<const T*>(p.arena);
   double* red = reinterpret_cast<double*>(smem + L.red);  // [2][33]
   int* memloc = reinterpret_cast<int*>(smem + L.memloc);
+  int2* gloc = reinterpret_cast<int2*>(smem + L.gloc);     // tile index of a group's first two members
+  short* gtime = reinterpret_cast<short*>(smem + L.gtime);  // time of each group
+  const T** t_wb = reinterpret_cast<const T**>(smem + L.twb);  // arena + woff - L per time
   int* s_gptr = reinterpret_cast<int*>(smem + L.gptr);  // group ranges per time
   int* s_mptr = reinterpret_cast<int*>(smem + L.mptr);  // member ranges per group
   T* acc_s = reinterpret_cast<T*>(smem + L.acc_s);
@@ -272,6 +284,7 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     t_K[i] = w.K;
     t_orig[i] = p.orig ? p.orig[i] : i;
     t_woff[i] = w.woff;
+    t_wb[i] = (w.woff >= 0 && arena) ? arena + (w.woff - w.L) : nullptr;
     pw[i] = (w.L == 0) ? w.PL : 0.0;  // recurrence state at jump 0
     if (w.L == 0)                     // weight of jump 0 (tail folded in)
       ring[i] = (w.woff >= 0 && arena) ? arena[w.woff] : (T)(w.PL + (w.K == 0 ? w.tail : 0.0));
@@ -307,18 +320,24 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     }
   }
   if (LL) {
-    for (int q = tid; q < p.nmem; q += nthr) {
-      int s = p.members[q];
+    // Tile index of state s in this CTA, or -1 when another CTA owns it.
+    auto loc_of = [&](int s) -> int {
       int ps = s / M, ms = s - ps * M;
       bool mine = ps >= g.p0 && ps < g.p1 && ms >= g.m0 && ms < g.m1;
-      memloc[q] = !mine ? -1 : (KIND == MJP_BD1D ? ms - g.m0 + 1 : elem2d(g, ps - g.p0, ms));
-    }
+      return !mine ? -1 : (KIND == MJP_BD1D ? ms - g.m0 + 1 : elem2d(g, ps - g.p0, ms));
+    };
+    for (int q = tid; q < p.nmem; q += nthr) memloc[q] = loc_of(p.members[q]);
     for (int q = tid; q < p.G; q += nthr) {
       acc_s[q] = (T)0;
       if (sizeof(T) == 4) acc_c[q] = 0.0f;
+      const int q0 = (int)p.mptr[q], q1 = (int)p.mptr[q + 1];
+      gloc[q] = make_int2(q1 > q0 ? loc_of(p.members[q0]) : -1, q1 > q0 + 1 ? loc_of(p.members[q0 + 1]) : -1);
+      if (p.nmem > 0) s_mptr[q] = q0;
     }
-    for (int q = tid; q <= p.G; q += nthr) s_mptr[q] = (int)p.mptr[q];
+    if (p.nmem > 0 && tid == 0) s_mptr[p.G] = (int)p.mptr[p.G];
     for (int q = tid; q <= nt; q += nthr) s_gptr[q] = (int)p.gptr[q];
+    for (int i = warp; i < nt; i += nwarps)
+      for (int q = (int)p.gptr[i] + lane; q < (int)p.gptr[i + 1]; q += 32) gtime[q] = (short)i;
   }
   const bool rn = p.renorm > 0;
   double mass0 = 1.0;
@@ -339,6 +358,10 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     return tot;
   };
   if (rn) mass0 = cluster_total(red);
+  // Does any window lack a stored copy of its weights (arena overflow)?
+  bool mine_rec = false;
+  for (int i = tid; i < nt; i += nthr) mine_rec |= t_woff[i] < 0;
+  const bool any_rec = __syncthreads_or(mine_rec) != 0;
 
   // Active times of jump k form a contiguous range [lo, hi] (times sorted).
   int lo = 0, hi = -1;
@@ -354,8 +377,7 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
       advance(kf, flo, fhi);
       if (kf <= Kmax)
         for (int i = flo + lane; i <= fhi; i += 32)
-          if (t_woff[i] >= 0)
-            cp_async_elem(ring + (int)(kf % kWeightRing) * nt + i, arena + t_woff[i] + (kf - t_L[i]));
+          if (t_wb[i]) cp_async_elem(ring + (int)(kf % kWeightRing) * nt + i, t_wb[i] + kf);
       cp_async_commit();
     }
   }
@@ -383,22 +405,29 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   const int acc_id = acc_ww ? lane : tid, acc_stride = acc_ww ? 32 : nthr;
 
   // LOGLIK: acc_g += w_i f sum_{s in g} rho_k[s] over this CTA's states.
+  // The groups of the active times [l, h] are one contiguous index range
+  // (groups are stored time by time), so threads take groups directly.
   auto group_accumulate = [&](const T* cur, int l, int h, const T* wts, T f) {
-    for (int i = l; i <= h; ++i) {
-      T w = f_mul(wts[i], f);
-      const int g0 = s_gptr[i], g1 = s_gptr[i + 1];
-      for (int gq = g0 + acc_id; gq < g1; gq += acc_stride) {
-        const int q0 = s_mptr[gq], q1 = s_mptr[gq + 1];
-        T v = (T)0;
-        bool any = false;
-        for (int q = q0; q < q1; ++q) {
-          int li = memloc[q];
+    if (h < l) return;
+    const int ga = s_gptr[l], gb = s_gptr[h + 1];
+    for (int gq = ga + acc_id; gq < gb; gq += acc_stride) {
+      const int2 lq = gloc[gq];
+      bool any = lq.x >= 0 || lq.y >= 0;
+      T v = lq.x >= 0 ? cur[lq.x] : (T)0;
+      if (lq.y >= 0) v = f_add(v, cur[lq.y]);
+      if (p.nmem > 0) {  // members beyond the second
+        const int q1 = s_mptr[gq + 1];
+        for (int q = s_mptr[gq] + 2; q < q1; ++q) {
+          const int li = memloc[q];
           if (li >= 0) {
             v = f_add(v, cur[li]);
             any = true;
           }
         }
-        if (!any) continue;
+      }
+      if (!any) continue;
+      const T w = f_mul(wts[gtime[gq]], f);
+      {
         if (sizeof(T) == 4) {
           float y = __fsub_rn(__fmul_rn((float)w, (float)v), acc_c[gq]);
           float s0 = (float)acc_s[gq];
@@ -499,12 +528,11 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
       advance(kf, flo, fhi);
       if (kf <= Kmax)
         for (int i = flo + lane; i <= fhi; i += 32)
-          if (t_woff[i] >= 0)
-            cp_async_elem(ring + (int)(kf % kWeightRing) * nt + i, arena + t_woff[i] + (kf - t_L[i]));
+          if (t_wb[i]) cp_async_elem(ring + (int)(kf % kWeightRing) * nt + i, t_wb[i] + kf);
       cp_async_commit();
       // ... and, for windows without a stored copy, Algorithm 2's recurrence
       // P_k = P_{k-1} x / k (the tail is added at k = K).
-      if (jump)
+      if (jump && any_rec)
         for (int i = clo + lane; i <= chi; i += 32) {
           if (t_woff[i] >= 0) continue;
           const double P = (k == t_L[i]) ? t_PL[i] : __dmul_rn(rprev[i], __ddiv_rn(t_x[i], (double)k));

@@ -237,3 +237,28 @@ def test_weight_store_fallback(prec, cap):
     r, ri = ora_expv(cfg["kind"], cfg["dims"], cfg["theta"], cfg["rho0"], times)
     assert list(gi["K"]) == list(ri["K"])
     assert np.abs(g - r).max() <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_loglik_groups_of_many_states(prec):
+    # Groups of 1, 3 and 5 states (the generic member list) across a cluster.
+    mjp = _mjp()
+    dims, theta = [30, 40], [6.0, 1.0, 1.5, 0.3]
+    n = 1200
+    times = np.array([0.4, 1.5])
+    gen = np.random.default_rng(21)
+    obs = []
+    for _ in times:
+        mem, cnt = [], []
+        for size in (1, 3, 5, 3, 1):
+            mem.append(gen.choice(n // 4, size=size, replace=False))
+            cnt.append(float(gen.integers(1, 9)))
+        obs.append((mem, np.array(cnt)))
+    rho0 = synth.delta(n, 0)
+    m = mjp.Model(synth.MRNA_PROT2D, dims, theta, prec)
+    m.set_option(mjp.OPT_CLUSTER, 2)
+    o = mjp.Obs(n, times, obs, rho0)
+    ll = mjp.loglik(m, o, np.array([theta]))
+    ref = oracle.loglik(oracle.build_model(synth.MRNA_PROT2D, dims, theta), rho0, times, obs)
+    nobs = sum(c.sum() for _, c in obs)
+    assert abs(ll[0] - ref) <= PER_OBS[prec] * nobs
