@@ -1,0 +1,182 @@
+"""Pins of the sampler oracle (oracle/mcmc.py) against things other than itself:
+NumPy's Philox4x64-10, exact stationarity of the (delayed-acceptance) transition
+kernel on a discrete target, the AR(1) autocorrelation time, an FFT
+autocovariance, NumPy's covariance and Cholesky, and sampling a known Gaussian."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import mcmc
+
+
+@pytest.mark.parametrize("key", [(0, 0), (123456789, 987654321), (2**64 - 1, 2**63 + 5)])
+@pytest.mark.parametrize("ctr", [0, 7, 2**40 + 3])
+def test_philox_round_structure_matches_numpy_philox4x64(key, ctr):
+    # numpy.random.Philox emits block counter+1 first; the same round function
+    # with the 64-bit constants must reproduce it word for word.
+    bg = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=np.array([ctr, 0, 0, 0], dtype=np.uint64))
+    want = [int(x) for x in bg.random_raw(4)]
+    got = mcmc.philox([ctr + 1, 0, 0, 0], key, spec=mcmc.PHILOX64)
+    assert got == want
+
+
+def test_philox32_bits_are_balanced_and_keyed():
+    key = mcmc.seed_key(20231205)
+    words = np.array([mcmc.philox((i, 0, 5, 0), key) for i in range(2048)], dtype=np.uint64).ravel()
+    bits = np.array([(words >> b) & 1 for b in range(32)]).mean(axis=1)
+    n = len(words)
+    assert np.all(np.abs(bits - 0.5) < 5 * 0.5 / math.sqrt(n))
+    byte_counts = np.bincount((words & 0xFF).astype(np.int64), minlength=256)
+    assert stats.chisquare(byte_counts).pvalue > 1e-4
+    assert mcmc.philox((0, 0, 0, 0), (1, 0)) != mcmc.philox((0, 0, 0, 0), (0, 0))
+    assert mcmc.philox((1, 0, 0, 0), (0, 0)) != mcmc.philox((0, 0, 0, 0), (0, 0))
+
+
+def test_u52_is_open_unit_interval():
+    assert mcmc.u52(0, 0) == 0.5 / 2**52
+    assert 0.0 < mcmc.u52(0, 0) < mcmc.u52(0xFFFFFFFF, 0xFFFFFFFF) < 1.0
+    assert mcmc.u52(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 0.5 / 2**52
+    assert mcmc.u52(0x80000000, 0) == 0.5 + 0.5 / 2**52
+
+
+def test_normals_are_standard_normal():
+    z = np.concatenate([mcmc.normals4(11, c, h) for c in range(8) for h in range(600)])
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    assert abs(z.mean()) < 5 / math.sqrt(len(z))
+    assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / len(z))
+
+
+def _discrete_kernel(logpi, s, accept):
+    """Transition matrix of a +-1 random-walk proposal (probability 1/2 each,
+    out-of-range proposals rejected) with acceptance probability accept(i, j)."""
+    K = len(logpi)
+    T = np.zeros((K, K))
+    for i in range(K):
+        for j in (i - 1, i + 1):
+            if 0 <= j < K:
+                T[i, j] = 0.5 * accept(i, j)
+        T[i, i] = 1.0 - T[i].sum()
+    return T
+
+
+def test_delayed_acceptance_kernel_is_exactly_stationary():
+    gen = np.random.default_rng(3)
+    K = 14
+    logpi = gen.normal(0, 2, K)
+    pi = np.exp(logpi - logpi.max())
+    pi /= pi.sum()
+    s = logpi + gen.normal(0, 1.5, K)   # a poor surrogate: the kernel stays exact anyway
+
+    def da(i, j):
+        return mcmc.da_alpha1(s[j], s[i], 0.0, 0.0) * mcmc.da_alpha2(logpi[j], logpi[i], s[j], s[i])
+
+    T = _discrete_kernel(logpi, s, da)
+    assert np.all(T >= 0) and np.allclose(T.sum(axis=1), 1.0, atol=1e-15)
+    assert np.max(np.abs(pi @ T - pi)) < 1e-15
+    F = pi[:, None] * T
+    assert np.max(np.abs(F - F.T)) < 1e-15
+    # The plain kernel is exact too; a second stage that forgets to divide by
+    # the surrogate ratio is not (the pin can tell them apart).
+    Tp = _discrete_kernel(logpi, s, lambda i, j: mcmc.mh_alpha(logpi[j], logpi[i]))
+    assert np.max(np.abs(pi @ Tp - pi)) < 1e-15
+
+    def wrong(i, j):
+        return mcmc.da_alpha1(s[j], s[i], 0.0, 0.0) * mcmc.mh_alpha(logpi[j], logpi[i])
+
+    Tw = _discrete_kernel(logpi, s, wrong)
+    assert np.max(np.abs(pi @ Tw - pi)) > 1e-4
+
+
+def test_acceptance_edge_cases():
+    assert mcmc.mh_alpha(-math.inf, -5.0) == 0.0
+    assert mcmc.mh_alpha(math.nan, -5.0) == 0.0
+    assert mcmc.mh_alpha(1.0, 0.0) == 1.0
+    assert mcmc.da_alpha2(-math.inf, -1.0, 0.0, 0.0) == 0.0
+    assert mcmc.da_alpha1(math.nan, 0.0, 0.0, 0.0) == 0.0
+    assert mcmc.da_alpha1(0.0, 0.0, -1.0, 0.0) == pytest.approx(math.exp(-1.0), rel=1e-15)
+
+
+def test_log_prior_matches_scipy_normal():
+    psi = np.array([0.3, -2.0, 4.6, 1.0])
+    want = stats.norm(loc=1.0, scale=1e5).logpdf(psi).sum()
+    assert mcmc.log_prior(psi) == pytest.approx(want, rel=1e-14)
+
+
+def test_cholesky_matches_numpy():
+    gen = np.random.default_rng(5)
+    A = gen.normal(size=(4, 4))
+    Z = A @ A.T + 0.1 * np.eye(4)
+    assert np.max(np.abs(mcmc.cholesky_lower(Z) - np.linalg.cholesky(Z))) < 1e-13
+    with pytest.raises(ValueError):
+        mcmc.cholesky_lower(-np.eye(4))
+
+
+def test_adapt_Z_is_scaled_biased_covariance():
+    gen = np.random.default_rng(9)
+    X = gen.multivariate_normal(np.zeros(4), np.diag([1.0, 2.0, 0.5, 3.0]), size=100)
+    want = (2.38 / 4) ** 2 * (np.cov(X.T, bias=True) + mcmc.EPS_COV * np.eye(4))
+    assert np.max(np.abs(mcmc.adapt_Z(X) - want)) < 1e-14
+
+
+def test_autocovariance_matches_fft():
+    x = np.random.default_rng(1).normal(size=3000).cumsum()
+    n = len(x)
+    d = x - x.mean()
+    f = np.fft.rfft(d, 2 * n)
+    acov = np.fft.irfft(f * np.conj(f))[:n] / n
+    g = mcmc.autocovariance(x, 200)
+    assert np.max(np.abs(g - acov[:201])) < 1e-10 * acov[0]
+
+
+@pytest.mark.parametrize("phi", [0.0, 0.6, 0.9])
+def test_ess_of_ar1_matches_closed_form(phi):
+    # AR(1) x_t = phi x_{t-1} + e_t: integrated autocorrelation time (1+phi)/(1-phi).
+    n = 200_000
+    gen = np.random.default_rng(17)
+    e = gen.normal(size=n)
+    x = np.empty(n)
+    x[0] = e[0] / math.sqrt(1 - phi * phi)
+    for t in range(1, n):
+        x[t] = phi * x[t - 1] + e[t]
+    ess = mcmc.ess_geyer(x)
+    want = n * (1 - phi) / (1 + phi)
+    assert abs(ess / want - 1.0) < 0.08
+
+
+def test_ess_of_chains_adds_up_and_mcse():
+    gen = np.random.default_rng(4)
+    tr = gen.normal(size=(6, 5000, 2))
+    ess = mcmc.ess_chains(tr)
+    assert np.all(np.abs(ess / 30000 - 1.0) < 0.1)
+    mo = mcmc.moments_mcse(tr)
+    assert np.all(np.abs(mo["mean"]) < 4 * mo["mcse_mean"])
+    assert np.all(np.abs(mo["var"] - 1.0) < 4 * mo["mcse_var"])
+    # iid normal: sd of the sample variance is sqrt(2/n).
+    assert np.all(np.abs(mo["mcse_var"] / math.sqrt(2 / 30000) - 1) < 0.15)
+
+
+def test_plain_and_delayed_acceptance_sample_a_known_gaussian():
+    sd = np.array([0.5, 1.0, 2.0, 0.25])
+    target = lambda p: float(-0.5 * np.sum((p / sd) ** 2))
+    surrogate = lambda p: 0.8 * target(p) + 0.3 * p[0]   # biased on purpose
+    L = mcmc.cholesky_lower(np.diag((1.2 * sd) ** 2))
+    psi0 = np.zeros((6, 4))
+    out = {}
+    for mode in ("plain", "da"):
+        st = mcmc.MHState(psi0, target, surrogate if mode == "da" else None, seed=77)
+        if mode == "plain":
+            for _ in range(2500):
+                st.plain_step(L)
+        else:
+            while min(len(t) for t in st.trace) < 2500:
+                st.da_round(L, 8, 2500)
+        tr = np.array([t[:2500] for t in st.trace])[:, 250:]
+        mo = mcmc.moments_mcse(tr)
+        assert np.all(np.abs(mo["mean"]) < 4.5 * mo["mcse_mean"]), (mode, mo)
+        assert np.all(np.abs(mo["var"] - sd**2) < 4.5 * mo["mcse_var"]), (mode, mo)
+        out[mode] = st
+    # DA screened every iteration but evaluated the exact target only on stage-1 survivors.
+    assert out["da"].n_exact < 0.8 * 6 * 2500
+    assert out["da"].n_exact == out["da"].n_stage1
