@@ -156,18 +156,23 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
+CHAIN_SOURCES = ("stencil.cu", "internal.cuh")
+
+
 def kernel_source_sha() -> str:
+    """Hash of the sources that define the chain kernel (the roofline kernel)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2312_05647_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in CHAIN_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def traffic_from_profiles():
-    """DRAM bytes per chain launch from the committed ncu summary, if it was
-    taken on the current kernel sources (else null)."""
+def traffic_from_profiles(thetas: int):
+    """DRAM bytes of one chain launch over `thetas` parameter vectors, scaled
+    from the committed ncu summary (per-theta bytes: each theta reads its own
+    weight windows, the observations are shared), if that summary was taken on
+    the current chain sources (else null)."""
     p = os.path.join(ROOT, "profiles", "chain_mrna_protein_traffic.json")
     try:
         d = json.load(open(p))
@@ -175,7 +180,8 @@ def traffic_from_profiles():
         return None
     if d.get("kernel_source_sha") != kernel_source_sha():
         return None
-    return d.get("dram_bytes_per_launch")
+    per_theta = d.get("dram_bytes_per_theta")
+    return None if per_theta is None else per_theta * thetas
 
 
 def run_reference(args, world, rank):
@@ -304,7 +310,7 @@ def main():
     peak = sms * ALU_FP32_FMA_PER_CLK_PER_SM * 2 * max_mhz * 1e6 / 1e12
     achieved = flops / chain_avg_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic_from_profiles(), "kernel": "chain_kernel<float, MRNA_PROT2D, loglik>",
+            "traffic": traffic_from_profiles(B), "kernel": "chain_kernel<float, MRNA_PROT2D, loglik>",
             "peak_basis": f"{sms} SMs x 128 FP32 FMA/clk x 2 x {max_mhz:.0f} MHz (derived, no measured ALU peak)",
             "flops_per_launch": flops, "chain_ms_avg": statistics.mean(chain_ms),
             "plan_ms_avg": statistics.mean(plan_ms)}
