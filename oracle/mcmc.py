@@ -179,6 +179,10 @@ class MHState:
         self.n_accept = 0
         self.n_stage1 = 0
         self.n_exact = 0
+        # (chain, iteration, |u - alpha|) of every accept decision: how close
+        # each was to going the other way.
+        self.margins = []
+        self.evals = []  # (Psi', exact log-likelihood) of every exact evaluation, in order
 
     def plain_step(self, L):
         """One MH iteration of every chain (SI A.1)."""
@@ -187,8 +191,11 @@ class MHState:
             prop = propose(self.psi[c], L, self.seed, c, h)
             lp = self.loglik_fn(prop)
             self.n_exact += 1
+            self.evals.append((prop.copy(), lp))
             ua, _ = uniforms2(self.seed, c, h)
-            if ua < mh_alpha(lp + log_prior(prop), self.ll[c] + log_prior(self.psi[c])):
+            alpha = mh_alpha(lp + log_prior(prop), self.ll[c] + log_prior(self.psi[c]))
+            self.margins.append((c, h, abs(ua - alpha)))
+            if ua < alpha:
                 self.psi[c] = prop
                 self.ll[c] = lp
                 self.n_accept += 1
@@ -210,6 +217,7 @@ class MHState:
                 sp = self.surrogate_fn(prop)
                 ua, ub = uniforms2(self.seed, c, h)
                 a1 = da_alpha1(sp, self.s[c], log_prior(prop), log_prior(self.psi[c]))
+                self.margins.append((c, h, abs(ua - a1)))
                 self.it[c] = h + 1
                 if not ua < a1:
                     self.trace[c].append(self.psi[c].copy())
@@ -217,7 +225,10 @@ class MHState:
                 self.n_stage1 += 1
                 lp = self.loglik_fn(prop)
                 self.n_exact += 1
-                if ub < da_alpha2(lp, self.ll[c], sp, self.s[c]):
+                self.evals.append((prop.copy(), lp))
+                a2 = da_alpha2(lp, self.ll[c], sp, self.s[c])
+                self.margins.append((c, h, abs(ub - a2)))
+                if ub < a2:
                     self.psi[c] = prop
                     self.ll[c] = lp
                     self.s[c] = sp
@@ -237,26 +248,31 @@ def autocovariance(x, maxlag: int):
 def ess_geyer(x) -> float:
     """Effective sample size n / tau with Geyer's initial monotone sequence:
     Gamma_m = gamma(2m) + gamma(2m+1) summed while positive, each clipped to the
-    previous one, tau = (-gamma(0) + 2 sum_m Gamma_m) / gamma(0)."""
+    previous one, tau = (-gamma(0) + 2 sum_m Gamma_m) / gamma(0), floored at
+    1 / log10(n)."""
     x = np.asarray(x, dtype=np.float64)
     n = len(x)
     if n < 4:
         return float(n)
-    g = autocovariance(x, n - 1)
-    if g[0] <= 0.0:
+    d = x - x.mean()
+    gamma = lambda k: float(np.dot(d[:n - k], d[k:]) / n)
+    g0 = gamma(0)
+    if g0 <= 0.0:
         return float(n)
-    total = -g[0]
+    total = -g0
     prev = np.inf
     m = 0
     while 2 * m + 1 < n:
-        G = g[2 * m] + g[2 * m + 1]
+        G = gamma(2 * m) + gamma(2 * m + 1)
         if G <= 0.0:
             break
         G = min(G, prev)
         total += 2.0 * G
         prev = G
         m += 1
-    tau = total / g[0]
+    # Antithetic or very short series can drive the estimate to zero or below;
+    # tau is floored at 1/log10(n), so ESS stays in (0, n log10 n].
+    tau = max(total / g0, 1.0 / math.log10(n))
     return float(n / tau)
 
 

@@ -1,4 +1,5 @@
-"""ctypes binding of libmjp.so (include/mjp.h): argument marshalling only.
+"""ctypes binding of libmjp.so (include/mjp.h, include/mjp_surrogate.h): argument
+marshalling only.
 
 Every numerical step runs in the library's CUDA kernels.  PyTorch supplies
 device memory and the current stream; there is no CPU fallback, and loading
@@ -34,6 +35,31 @@ class SeriesInfo(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("K", _i64p), ("eps", _f64p)]
 
 
+class TrainCfg(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("batch", ctypes.c_int64), ("lr", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("fit_norm", ctypes.c_int)]
+
+
+class SamplerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("iterations", "accepted", "stage1", "exact_evals", "rounds", "kept",
+                                              "evals_kept")]
+
+
+class AdaptCfg(ctypes.Structure):
+    _fields_ = [("every", ctypes.c_int64), ("window", ctypes.c_int64), ("cycle", ctypes.c_int64),
+                ("good_cycles", ctypes.c_int64), ("z0", ctypes.c_double), ("eps", ctypes.c_double),
+                ("acc_lo", ctypes.c_double), ("acc_hi", ctypes.c_double), ("restart_at_best", ctypes.c_int),
+                ("max_iters", ctypes.c_int64)]
+
+
+class AdaptReport(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64 * 2), ("good", ctypes.c_int64 * 2), ("converged", ctypes.c_int),
+                ("acc_last", ctypes.c_double)]
+
+
+MLP_NPAR, MLP_NNORM = 17281, 10
+
 SIGNATURES = {
     "mjp_last_error": (ctypes.c_char_p, []),
     "mjp_version": (ctypes.c_char_p, []),
@@ -63,6 +89,33 @@ SIGNATURES = {
     "expv_batch_destroy": (None, [_vp]),
     "expv_series_static": (ctypes.c_int, [ctypes.c_int, _i64p, ctypes.c_int, _f64p, ctypes.c_int, _vp, _f64p,
                                           ctypes.c_int, _vp, _vp]),
+    # include/mjp_surrogate.h
+    "mjp_mlp_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint64]),
+    "mjp_mlp_destroy": (None, [_vp]),
+    "mjp_mlp_set_params": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    "mjp_mlp_get_params": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    "mjp_mlp_fit_norm": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, _vp]),
+    "mjp_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int, _vp]),
+    "mjp_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp, ctypes.c_int, _vp]),
+    "mjp_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(TrainCfg), _vp, ctypes.c_int,
+                                     _vp]),
+    "mjp_sampler_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, _vp, ctypes.c_int, ctypes.c_int64,
+                                          ctypes.c_int64, ctypes.c_uint64]),
+    "mjp_sampler_destroy": (None, [_vp]),
+    "mjp_sampler_set_state": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
+    "mjp_sampler_get_state": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    "mjp_sampler_set_cov": (ctypes.c_int, [_vp, _f64p, _vp]),
+    "mjp_sampler_get_cov": (ctypes.c_int, [_vp, _f64p, _vp]),
+    "mjp_sampler_adapt_cov": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, _vp]),
+    "mjp_sampler_run_plain": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int, _vp]),
+    "mjp_sampler_run_da": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _vp]),
+    "mjp_sampler_clear": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "mjp_sampler_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(SamplerStats), _vp]),
+    "mjp_sampler_trace": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
+    "mjp_sampler_evals": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64p]),
+    "mjp_sampler_adapt": (ctypes.c_int, [_vp, ctypes.POINTER(AdaptCfg), ctypes.POINTER(AdaptReport), _vp]),
+    "mjp_ess": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
+                               ctypes.c_int, _vp]),
 }
 
 _LIB = None

@@ -778,3 +778,28 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
 }
 
 }  // extern "C"
+
+// ---- internal accessors for the sampler (not part of the C ABI) -----------
+namespace mjp {
+
+int model_kind(const mjp_model* m) { return m->kind; }
+
+// Wait for `s`, grow the weight arena if a window overflowed it, then return
+// and clear the device status word (MJP_OK when nothing was flagged).  A
+// sampler keeps going after a flagged evaluation: its result is NaN and the
+// proposal is rejected.
+int model_take_status(mjp_model* m, cudaStream_t s, int* status) {
+  *status = 0;
+  MJP_CUDA(cudaStreamSynchronize(s));
+  if (m->d_arena_ctl.p) {
+    int over = 0;
+    MJP_CUDA(cudaMemcpy(&over, m->d_arena_ctl.as<char>() + 8, sizeof(int), cudaMemcpyDeviceToHost));
+    if (over) m->arena_grow = true;
+  }
+  if (!m->d_status.p) return MJP_OK;
+  MJP_CUDA(cudaMemcpy(status, m->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  MJP_CUDA(cudaMemset(m->d_status.p, 0, sizeof(int)));
+  return MJP_OK;
+}
+
+}  // namespace mjp

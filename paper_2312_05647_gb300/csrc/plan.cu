@@ -103,7 +103,9 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
   if (!(kstar + 1.0 <= (double)p.kcap)) {  // also catches inf/NaN; nothing loops
     if (lane == 0) {
       set_status(p.status, kStatusKcap);
-      r.L = 0; r.K = 0; r.PL = 1.0; r.tail = 0.0; r.woff = -1;
+      // A NaN weight makes this time's result (and a log-likelihood using it)
+      // NaN, so a caller that keeps going (a sampler) rejects the parameters.
+      r.L = 0; r.K = 0; r.PL = __longlong_as_double(0x7ff8000000000000LL); r.tail = 0.0; r.woff = -1;
       *dst = r;
     }
     return;

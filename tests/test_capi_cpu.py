@@ -144,3 +144,32 @@ def test_batch_validation(L):
     rc = L.expv_batch_create(ctypes.byref(h), capi.TWOSTATE, 2, N.ctypes.data_as(capi._i64p),
                              th.ctypes.data_as(capi._f64p), t.ctypes.data_as(capi._f64p), None, capi.FP32)
     assert rc == -8
+
+
+def test_surrogate_and_sampler_host_validation(L):
+    vp = ctypes.c_void_p
+    out = vp()
+    assert L.mjp_mlp_create(None, 0) == -1
+    assert L.mjp_mlp_forward(None, vp(8), 1, vp(8), capi.PTR_HOST, None) == -1
+    assert L.mjp_mlp_train(None, vp(8), vp(8), 1, None, None, capi.PTR_HOST, None) == -1
+    assert L.mjp_mlp_set_params(None, None, None, capi.PTR_HOST, None) == -1
+    assert L.mjp_sampler_create(ctypes.byref(out), None, None, 4, 10, 0, 0) == -1
+    assert L.mjp_sampler_set_cov(None, None, None) == -1
+    assert L.mjp_sampler_run_plain(None, 1, 1, None) == -1
+    assert L.mjp_sampler_run_da(None, None, 1, 4, 1, None) == -1
+    st = capi.SamplerStats()
+    assert L.mjp_sampler_stats_get(None, ctypes.byref(st), None) == -1
+    assert L.mjp_sampler_adapt(None, None, None, None) == -1
+    # ESS: shape checks come before any device work.
+    assert L.mjp_ess(vp(8), 2, 3, 1, None, None, None, None, None, capi.PTR_HOST, None) == -1
+    assert L.mjp_ess(vp(8), 0, 10, 1, None, None, None, None, None, capi.PTR_HOST, None) == -1
+    assert L.mjp_ess(None, 2, 10, 1, None, None, None, None, None, capi.PTR_HOST, None) == -1
+
+
+def test_binding_struct_layouts_match_header():
+    # Sizes of the C structs of include/mjp_surrogate.h on an LP64 target.
+    assert ctypes.sizeof(capi.TrainCfg) == 64
+    assert ctypes.sizeof(capi.SamplerStats) == 56
+    assert ctypes.sizeof(capi.AdaptCfg) == 80
+    assert ctypes.sizeof(capi.AdaptReport) == 48
+    assert capi.AdaptCfg.max_iters.offset == 72 and capi.AdaptReport.acc_last.offset == 40

@@ -180,3 +180,11 @@ def test_plain_and_delayed_acceptance_sample_a_known_gaussian():
     # DA screened every iteration but evaluated the exact target only on stage-1 survivors.
     assert out["da"].n_exact < 0.8 * 6 * 2500
     assert out["da"].n_exact == out["da"].n_stage1
+
+
+def test_ess_floor_on_degenerate_series():
+    # Alternating series: gamma(1) = -gamma(0) makes the first pair sum zero;
+    # the floor keeps ESS finite and positive (n log10 n at most).
+    x = np.tile([1.0, -1.0], 50)
+    assert mcmc.ess_geyer(x) == pytest.approx(100 * math.log10(100))
+    assert 0 < mcmc.ess_geyer(np.array([0.3, -1.0, 2.0, 0.1])) <= 4 * math.log10(4) + 1e-12
