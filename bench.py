@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=152, help="thetas per step and GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mcmc", action="store_true", help="skip the ESS/s comparison")
+    ap.add_argument("--mcmc-iters", type=int, default=400, help="iterations of each timed sampler run")
+    ap.add_argument("--mcmc-adapt-iters", type=int, default=1500, help="iteration cap of each adaptive phase")
     return ap.parse_args()
 
 
@@ -210,6 +213,48 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+MCMC_WORKLOAD = "two_state_promoter_NR300_50times_100cells_256chains"
+
+
+def mcmc_comparison(args):
+    """ESS/s of delayed acceptance (trained surrogate) against plain MH on the
+    two-state promoter data: SI adaptive protocol (capped), surrogate trained
+    on the adaptation's exact evaluations, then equal-length runs from the
+    adapted state with the same frozen covariance."""
+    import numpy as np
+    import synth
+    import paper_2312_05647_gb300 as mjp
+    from paper_2312_05647_gb300 import surrogate as S
+    cfg = synth.twostate_promoter()
+    snaps = synth.gillespie_snapshots(cfg["kind"], cfg["dims"], cfg["theta"], cfg["times"], 100, synth.rng(5, 0))
+    obs = synth.snapshot_obs(cfg["kind"], cfg["dims"], snaps)
+    model = mjp.Model(cfg["kind"], cfg["dims"], cfg["theta"], mjp.FP32)
+    ob = mjp.Obs(600, cfg["times"], obs, cfg["rho0"])
+    C = 256
+    r = S.da_vs_plain(model, ob, S.promoter_initial_psi(obs, C), C, iters=args.mcmc_iters,
+                      adapt=dict(max_iters=args.mcmc_adapt_iters))
+
+    def arm(d, da):
+        st = d["stats"]
+        out = {"ess_per_s": d["ess_per_s"], "min_ess": d["min_ess"], "seconds": d["seconds"],
+               "iterations": st["iterations"], "exact_evals": st["exact_evals"], "exact_launches": st["rounds"],
+               "accept_rate": st["accepted"] / st["iterations"], "ess": [float(v) for v in d["ess"]],
+               "mean_psi": [float(v) for v in d["mean"]]}
+        if da:
+            out["stage1_rate"] = st["stage1"] / st["iterations"]
+        return out
+
+    return {"workload": MCMC_WORKLOAD, "chains": C, "iters": args.mcmc_iters,
+            "adapt": {"iters_per_phase": r["adapt"]["iters"], "good_cycles": r["adapt"]["good"],
+                      "converged": r["adapt"]["converged"], "seconds": r["adapt_s"]},
+            "surrogate": {"train_pairs": r["train_pairs"], "train_s": r["train_s"],
+                          "loss_first_last": r["train_loss_first_last"]},
+            "plain": arm(r["plain"], False), "da": arm(r["da"], True),
+            "ess_per_s_ratio": r["ess_per_s_ratio"], "max_z_mean": max(r["z_mean"]), "max_z_var": max(r["z_var"]),
+            "moments_within_2mcse": bool(max(r["z_mean"]) < 2.0 and max(r["z_var"]) < 2.0),
+            "timing": "CUDA events around each sampler run (device-resident chains)"}
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -324,6 +369,10 @@ def main():
                "sample": f"{workers} of the {B} thetas, one full 20-time loglik per process",
                "max_abs_loglik_diff_vs_gpu": err}
 
+    mcmc = None
+    if not args.no_mcmc and world == 1:
+        mcmc = mcmc_comparison(args)
+
     line = {
         "metric": METRIC, "value": value, "unit": "loglik evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
@@ -338,6 +387,7 @@ def main():
                 "d2h_bytes_per_step": int(B * 8)},
         "gpu_launches": launches,
         "clocks": clk,
+        "mcmc": mcmc,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
