@@ -355,7 +355,7 @@ def main():
     peak = sms * ALU_FP32_FMA_PER_CLK_PER_SM * 2 * max_mhz * 1e6 / 1e12
     achieved = flops / chain_avg_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic_from_profiles(B), "kernel": "chain_kernel<float, MRNA_PROT2D, loglik>",
+            "traffic": traffic_from_profiles(B), "kernel": "chain_reg2d_kernel<5> (register-resident, FP32 mRNA/protein loglik)",
             "peak_basis": f"{sms} SMs x 128 FP32 FMA/clk x 2 x {max_mhz:.0f} MHz (derived, no measured ALU peak)",
             "flops_per_launch": flops, "chain_ms_avg": statistics.mean(chain_ms),
             "plan_ms_avg": statistics.mean(plan_ms)}

@@ -85,6 +85,10 @@ extern "C" {
 #define MJP_OPT_PROFILE 5       /* 1: record CUDA events around each kernel of a call (see rate_model_last_timing) */
 #define MJP_OPT_ARENA 6         /* capacity (elements) of the planner's Poisson-weight store; 0 = automatic.  Windows
                                    that do not fit are generated in the chain by Algorithm 2's recurrence instead. */
+#define MJP_OPT_CHAIN 7         /* loglik chain kernel for stencil models: 0 = automatic (the register-resident kernel for
+                                   FP32 mRNA/protein boxes without renormalisation, forced cluster or thread counts,
+                                   else the shared-memory kernel), 1 = shared-memory kernel, 2 = register-resident
+                                   kernel (MJP_ERR_UNSUPPORTED where it does not apply) */
 
 typedef struct mjp_model mjp_model;
 typedef struct mjp_obs mjp_obs;

@@ -13,7 +13,7 @@ import ctypes
 import numpy as np
 
 from . import capi
-from .capi import (BD1D, CSR, FP32, FP64, MRNA_PROT2D, OPT_ARENA, OPT_CLUSTER, OPT_K_CAP, OPT_PROFILE,
+from .capi import (BD1D, CSR, FP32, FP64, MRNA_PROT2D, OPT_ARENA, OPT_CHAIN, OPT_CLUSTER, OPT_K_CAP, OPT_PROFILE,
                    OPT_RENORM_PERIOD, OPT_THREADS, PTR_DEVICE, PTR_HOST, TRUNC_PAPER, TRUNC_TOL, TWOSTATE,
                    MJPError)
 

@@ -21,7 +21,7 @@ BD1D, TWOSTATE, MRNA_PROT2D, CSR = 1, 2, 3, 4
 FP32, FP64 = 1, 2
 TRUNC_PAPER, TRUNC_TOL = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
-OPT_RENORM_PERIOD, OPT_K_CAP, OPT_THREADS, OPT_CLUSTER, OPT_PROFILE, OPT_ARENA = 1, 2, 3, 4, 5, 6
+OPT_RENORM_PERIOD, OPT_K_CAP, OPT_THREADS, OPT_CLUSTER, OPT_PROFILE, OPT_ARENA, OPT_CHAIN = 1, 2, 3, 4, 5, 6, 7
 
 # Every entry point of include/mjp.h: name -> (restype, argtypes).
 _vp = ctypes.c_void_p

@@ -49,6 +49,7 @@ struct mjp_model {
   int renorm = 0;
   int64_t kcap = (int64_t)1 << 26;
   int threads = 0;
+  int chain = 0;  // MJP_OPT_CHAIN
   int cluster = 0;
   int profile = 0;
   bool timed = false;
@@ -465,6 +466,10 @@ int rate_model_set_option(mjp_model* m, int option, int64_t value) {
       if (value != 0 && (value % 32 != 0 || value < 64 || value > 1024)) return fail(MJP_ERR_ARG, "threads must be 0 or a multiple of 32 in [64, 1024]");
       m->threads = (int)value;
       return MJP_OK;
+    case MJP_OPT_CHAIN:
+      if (value < 0 || value > 2) return fail(MJP_ERR_ARG, "chain must be 0, 1 or 2");
+      m->chain = (int)value;
+      return MJP_OK;
     case MJP_OPT_ARENA:
       if (value < 0) return fail(MJP_ERR_ARG, "arena capacity must be >= 0");
       m->d_arena.release();
@@ -727,12 +732,22 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
       if (!finite_nonneg(theta + (int64_t)b * ntheta, ntheta)) return fail(MJP_ERR_ARG, "rates must be finite and >= 0");
   cudaStream_t s = (cudaStream_t)stream;
   const int nt = obs->ntimes;
-  int C, T;
-  int64_t slab;
+  int C = 0, T = 0;
+  int64_t slab = 0;
   // The chain keeps a generic member list only for groups of > 2 members.
   const int nmem_list = obs->maxmem > 2 ? obs->nmem : 0;
-  int rc = stencil_config(m, 1, nt, obs->G, nmem_list, &C, &T, &slab);
-  if (rc) return rc;
+  // Register-resident chain: FP32 mRNA/protein boxes, no renormalisation, no
+  // forced launch shape.
+  RegPlan rp = {};
+  bool use_reg = false;
+  if (m->chain != 1 && m->kind == MJP_MRNA_PROT2D && m->precision == MJP_FP32 && m->renorm == 0 &&
+      (m->chain == 2 || (m->cluster == 0 && m->threads == 0)))
+    use_reg = chain_reg2d_plan(m->M, m->P, nt, obs->nmem, 8, &rp);
+  if (m->chain == 2 && !use_reg)
+    return fail(MJP_ERR_UNSUPPORTED, "the register-resident chain needs an FP32 mRNA/protein box without "
+                                     "renormalisation that fits 8 CTAs");
+  int rc = 0;
+  if (!use_reg && (rc = stencil_config(m, 1, nt, obs->G, nmem_list, &C, &T, &slab))) return rc;
   if ((rc = ensure_status(m))) return rc;
   if ((rc = m->d_win.ensure(sizeof(Win) * (size_t)nt * B))) return rc;
   if ((rc = m->d_info.ensure(sizeof(JobInfo) * (size_t)B))) return rc;
@@ -768,7 +783,8 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   cp.G = obs->G; cp.nmem = nmem_list; cp.ll = d_out;
   cp.renorm = (m->precision == MJP_FP32) ? m->renorm : 0;
   cp.slab = slab; cp.status = pp.status;
-  MJP_CUDA(launch_chain_stencil(m->kind, m->precision, 1, cp, C, T, s));
+  if (use_reg) MJP_CUDA(launch_chain_reg2d(cp, rp, s));
+  else MJP_CUDA(launch_chain_stencil(m->kind, m->precision, 1, cp, C, T, s));
   if ((rc = mark(m, 2, s))) return rc;
   if (where == MJP_PTR_HOST) {
     MJP_CUDA(cudaMemcpyAsync(out, d_out, sizeof(double) * B, cudaMemcpyDeviceToHost, s));

@@ -1,0 +1,90 @@
+// chain_common.cuh -- device helpers shared by the jump-chain kernels
+// (stencil.cu, stencil_reg.cu): status word, split cluster barrier, cp.async
+// copies, scaled rate coefficients and fixed-order (uncontracted) arithmetic.
+#pragma once
+
+#include "internal.cuh"
+
+namespace mjp {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void set_status(int* st, int code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Asynchronous global -> shared copy of one float or double (cp.async).
+__device__ __forceinline__ void cp_async_elem(float* sdst, const float* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double* sdst, const double* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Scaled rates (rate / Omega) of one instance in the chain type.
+template <typename T>
+struct Coef {
+  T a, b, c, d;
+};
+
+template <typename T, int KIND>
+__device__ __forceinline__ Coef<T> make_coef(const double* th, double omega) {
+  Coef<T> k;
+  double inv = omega > 0.0 ? 1.0 / omega : 0.0;
+  k.a = (T)(th[0] * inv);
+  k.b = (T)(th[1] * inv);
+  k.c = (KIND == MJP_BD1D) ? (T)0 : (T)(th[2] * inv);
+  k.d = (KIND == MJP_BD1D) ? (T)0 : (T)(th[3] * inv);
+  return k;
+}
+
+// Fixed-order arithmetic (no contraction): every thread layout and cluster
+// shape produces bit-identical chains.
+__device__ __forceinline__ float f_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double f_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float f_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double f_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float f_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double f_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float f_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double f_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Pairs of chain values (two rows of one column).  FP32 pairs use the packed
+// sm_100+ FP32x2 instructions; FP64 pairs are two scalar operations.
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+__device__ __forceinline__ float2 v_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 v_mul(double2 a, double2 b) {
+  return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 v_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 v_add(double2 a, double2 b) {
+  return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 v_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 v_fma(double2 a, double2 b, double2 c) {
+  return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 v_make(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 v_make(double a, double b) { return make_double2(a, b); }
+
+}  // namespace
+}  // namespace mjp

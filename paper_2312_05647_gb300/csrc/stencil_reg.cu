@@ -1,0 +1,556 @@
+// stencil_reg.cu -- register-resident jump chain for the mRNA/protein stencil
+// (FP32, log-likelihood mode), Algorithm 2 with one chain shared by all times.
+//
+// Each thread keeps a 4-column x 8- or 10-row block of rho (32 or 40 states,
+// as row pairs) in registers for all K jumps; shared memory carries only the
+// block edges (its left and right columns, first and last rows),
+// double-buffered by jump parity, and the observation accumulators.  Per jump
+// a thread reads its four neighbours' edges, updates its states in place (row
+// pair by row pair, keeping the old values the next ones still need), writes
+// its own edges and meets the rest of the cluster at one split barrier.
+// Compared with a shared-memory ping-pong of the whole slab (every state read
+// three times and written once per jump), shared-memory traffic drops from
+// 16 B to ~1.5 B per state and the FP32 pipe becomes the limit.
+//
+// Arithmetic per state is the same operation sequence, in the same order, as
+// the shared-memory kernel in stencil.cu (gather form of rho B with the
+// coefficients built from theta), so both kernels produce bit-identical
+// chains; observations with one member per group give bit-identical
+// log-likelihoods.  A cluster of C CTAs splits the rows; block edges that
+// cross a CTA boundary are written into the neighbour CTA's halo slots
+// through distributed shared memory.
+//
+// Every neighbour read and edge write uses a per-thread base plus a
+// compile-time offset (the edge arrays have fixed strides), and the jump
+// counter is 32-bit, so the jump loop carries almost no integer work besides
+// the arithmetic of the states.
+#include <cooperative_groups.h>
+
+#include <type_traits>
+
+#include "chain_common.cuh"
+#include "internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace mjp {
+
+namespace {
+
+constexpr int kQC = 4;            // columns per thread block of states
+constexpr int kRegThreads = 512;  // threads per CTA at most (16 warps, <= 128 registers each); warp 0
+                                  // also streams the Poisson weights into the ring
+constexpr int kMaxNQ = 512;       // column quads (M <= 2048)
+// Fixed strides of the edge arrays (per parity):
+//  - columns [2 sides][QR][kCStr] float2: the left (side 0) and right (side 1)
+//    column of block t, row pair r; entry kZero is a zero slot;
+//  - rows [2][kRStr] float4: the first (0) and last (1) row of block t (its
+//    4 columns); entries kZero + 1 + q hold the row just outside the CTA for
+//    column quad q (the next CTA's first row in array 0, the previous CTA's
+//    last row in array 1), written by those CTAs; entry kZero is zero.
+// Every neighbour read goes through a fixed per-thread slot, so threads at
+// the box edge read a zero slot instead of branching.
+constexpr int kZero = kRegThreads;
+constexpr int kCStr = kRegThreads + 1;
+constexpr int kRStr = kRegThreads + 1 + kMaxNQ;
+
+template <int QR>
+struct EdgeGeo {
+  static constexpr size_t col_bytes = ((size_t)8 * 2 * QR * kCStr + 15) / 16 * 16;
+  static constexpr size_t par_bytes = col_bytes + (size_t)16 * 2 * kRStr;
+  static constexpr size_t col(int side, int r) { return (size_t)8 * (side * QR + r) * kCStr; }
+  static constexpr size_t row(int which) { return col_bytes + (size_t)16 * which * kRStr; }
+};
+
+struct RegLayout {
+  size_t edge, tx, tPL, ttail, twb, pw, tL, tK, trec, ring, gptr, ent, acc_s, acc_c, total;
+};
+
+__host__ __device__ inline RegLayout reg_layout(size_t edge_bytes, int nt, int nmem) {
+  RegLayout s;
+  size_t o = 0;
+  s.edge = o; o += edge_bytes;
+  s.tx = o; o += 8 * (size_t)nt;
+  s.tPL = o; o += 8 * (size_t)nt;
+  s.ttail = o; o += 8 * (size_t)nt;
+  s.twb = o; o += 8 * (size_t)nt;
+  s.pw = o; o += 16 * (size_t)nt;
+  s.tL = o; o += align_up(4 * (size_t)nt, 8);
+  s.tK = o; o += align_up(4 * (size_t)nt, 8);
+  s.trec = o; o += align_up(4 * (size_t)nt, 8);
+  s.ring = o; o += align_up(4 * kWeightRing * (size_t)nt, 8);
+  s.gptr = o; o += align_up(4 * (size_t)(nt + 1), 8);
+  s.ent = o; o += 8 * (size_t)nmem;
+  s.acc_s = o; o += align_up(4 * (size_t)nmem, 8);
+  s.acc_c = o; o += align_up(4 * (size_t)nmem, 16);
+  s.total = align_up(o, 16);
+  return s;
+}
+
+// Register value of slot (row pair r, column c, half h) = ((r * 4 + c) * 2 + h)
+// with a runtime slot, by selection (no local-memory array).
+template <int QR>
+__device__ __forceinline__ float pick(const float2 (&S)[QR][kQC], int slot) {
+  float v = 0.0f;
+#pragma unroll
+  for (int i = 0; i < QR * kQC; ++i) {
+    v = (slot == 2 * i) ? S[i / kQC][i % kQC].x : v;
+    v = (slot == 2 * i + 1) ? S[i / kQC][i % kQC].y : v;
+  }
+  return v;
+}
+
+// The value of v, hidden from the optimiser: quantities derived from it inside
+// the jump loop are recomputed each jump instead of being hoisted out of the
+// loop and held in registers for all states.
+__device__ __forceinline__ int opaque(int v) {
+  asm volatile("" : "+r"(v));
+  return v;
+}
+
+// Exclusive prefix sum of v over the block (blockDim <= 1024).
+__device__ int block_exclusive_scan(int v, int* wsum) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  int off = 0;
+  for (int w = 0; w < warp; ++w) off += wsum[w];
+  __syncthreads();
+  return off + x - v;
+}
+
+template <int kQR>
+__global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const ChainParams p, const int NQ,
+                                                                      const int RS) {
+  using G = EdgeGeo<kQR>;
+  constexpr int kRows = 2 * kQR;  // rows of a thread's block
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int wsum[32];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int job = blockIdx.x / C;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int nt = p.ntimes;
+  const int M = p.M, P = p.P;
+  const int p0 = rank * RS;
+  const int p1 = min(P, p0 + RS);
+  const int nrb = p1 > p0 ? (p1 - p0 + kRows - 1) / kRows : 0;  // row blocks of this CTA
+  const bool wwarp = warp == 0;  // streams the weights (and holds states like every warp)
+  const int qx = tid % NQ, rb = tid / NQ;
+  const bool owner = rb < nrb;   // this thread holds a block of states
+  const int m0 = kQC * qx, pb = p0 + kRows * rb;  // first column and first row of the block
+  const int nmem = (int)p.mptr[p.G];
+
+  const RegLayout L = reg_layout(2 * G::par_bytes, nt, nmem);
+  double* t_x = reinterpret_cast<double*>(smem + L.tx);
+  double* t_PL = reinterpret_cast<double*>(smem + L.tPL);
+  double* t_tail = reinterpret_cast<double*>(smem + L.ttail);
+  int* t_L = reinterpret_cast<int*>(smem + L.tL);
+  int* t_K = reinterpret_cast<int*>(smem + L.tK);
+  int* t_rec = reinterpret_cast<int*>(smem + L.trec);  // 1: no stored copy, run the recurrence
+  const float** t_wb = reinterpret_cast<const float**>(smem + L.twb);
+  double* pw = reinterpret_cast<double*>(smem + L.pw);
+  float* ring = reinterpret_cast<float*>(smem + L.ring);
+  int* s_gptr = reinterpret_cast<int*>(smem + L.gptr);
+  int2* ent = reinterpret_cast<int2*>(smem + L.ent);
+  float* acc_s = reinterpret_cast<float*>(smem + L.acc_s);
+  float* acc_c = reinterpret_cast<float*>(smem + L.acc_c);
+  const float* arena = reinterpret_cast<const float*>(p.arena);
+
+  // ---- prologue: windows, weights, observations ---------------------------
+  const int64_t Kmax64 = p.info[job].Kmax;
+  const Win* wj = p.win + (int64_t)job * nt;
+  for (int i = tid; i < nt; i += blockDim.x) {
+    const Win w = wj[i];
+    t_x[i] = w.x;
+    t_PL[i] = w.PL;
+    t_tail[i] = w.tail;
+    t_L[i] = (int)w.L;
+    t_K[i] = (int)w.K;
+    t_rec[i] = (w.woff < 0 || !arena) ? 1 : 0;
+    t_wb[i] = (w.woff >= 0 && arena) ? arena + (w.woff - w.L) : nullptr;
+    pw[i] = (w.L == 0) ? w.PL : 0.0;
+    if (w.L == 0) ring[i] = (w.woff >= 0 && arena) ? arena[w.woff] : (float)(w.PL + (w.K == 0 ? w.tail : 0.0));
+  }
+  for (int i = tid; i <= nt; i += blockDim.x) s_gptr[i] = (int)p.gptr[i];
+  const double omega = p.info[job].omega;
+  const Coef<float> co = make_coef<float, MJP_MRNA_PROT2D>(p.theta + (int64_t)job * p.ntheta, omega);
+  // The planner caps K (MJP_OPT_K_CAP, default 2^26); the loop counts in 32 bits.
+  const int Kmax = Kmax64 < (1LL << 30) ? (int)Kmax64 : 0;
+  if (Kmax64 >= (1LL << 30) && tid == 0 && rank == 0) set_status(p.status, kStatusKcap);
+  __syncthreads();
+
+  // Observation entries: (member q, register slot, time) of the states this
+  // thread holds, in member order (= time order).  Two passes: count, then
+  // fill after a block-wide prefix sum.
+  auto owns = [&](int s, int& slot) -> bool {
+    const int ps = s / M, ms = s - ps * M;
+    if (!owner || ps < pb || ps >= pb + kRows || ms < m0 || ms >= m0 + kQC) return false;
+    const int pr = ps - pb;
+    slot = (((pr >> 1) * kQC) + (ms - m0)) * 2 + (pr & 1);
+    return true;
+  };
+  auto scan_members = [&](bool fill, int base) -> int {
+    int n = 0, i = 0;
+    for (int g = 0; g < p.G; ++g) {
+      while (i < nt && g >= s_gptr[i + 1]) ++i;
+      const int q0 = (int)p.mptr[g], q1 = (int)p.mptr[g + 1];
+      for (int q = q0; q < q1; ++q) {
+        int slot;
+        if (owns(p.members[q], slot)) {
+          if (fill) ent[base + n] = make_int2(q, slot | (i << 6));
+          ++n;
+        }
+      }
+    }
+    return n;
+  };
+  const int ecount = owner ? scan_members(false, 0) : 0;
+  const int ebeg = block_exclusive_scan(ecount, wsum);
+  if (owner) scan_members(true, ebeg);
+  const int eend = ebeg + ecount;
+  for (int q = tid; q < nmem; q += blockDim.x) {
+    acc_s[q] = 0.0f;
+    acc_c[q] = 0.0f;
+  }
+  {
+    float4* e = reinterpret_cast<float4*>(smem + L.edge);
+    for (int q = tid; q < (int)(2 * G::par_bytes / 16); q += blockDim.x) e[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  // Every CTA's edge arrays are zeroed before any neighbour writes into them.
+  if (C > 1) cluster.sync();
+  else __syncthreads();
+
+  // Column coefficients (rates into column m, scaled by 1/Omega): gamma_m
+  // (m+1) from m+1, k_p m from p-1, and 1 - e without the gamma_p p part;
+  // the first and the last as pairs (both rows of a row pair).
+  const float one = 1.0f;
+  float2 crp[kQC], d0p[kQC];
+  float cdv[kQC];
+  int colmask = 0;  // bit c: column m0 + c lies in the box
+#pragma unroll
+  for (int c = 0; c < kQC; ++c) {
+    const int m = m0 + c;
+    if (m < M) colmask |= 1 << c;
+    const float fm = (float)m;
+    const float cr = f_mul(co.b, (float)(m + 1));
+    cdv[c] = f_mul(co.c, fm);
+    const float d0 = f_sub(one, f_add(f_add(f_mul(co.b, fm), m + 1 < M ? co.a : 0.0f), cdv[c]));
+    crp[c] = v_make(cr, cr);
+    d0p[c] = v_make(d0, d0);
+  }
+  const float2 c_l = v_make(co.a, co.a), c_gp = v_make(co.d, co.d), c_ngp = v_make(-co.d, -co.d);
+  // Row pair of this block that holds row P-1 (-1 if none); blocks with it or
+  // with padding columns take the checked update.
+  const int rtop = (P - 1 >= pb && P - 1 < pb + kRows) ? (P - 1 - pb) / 2 : -1;
+  const bool special = rtop >= 0 || colmask != (1 << kQC) - 1;
+
+  // Fixed neighbour slots: left block's right column, right block's left
+  // column, the row below (a last row) and the row above (a first row).
+  const int iL = qx > 0 ? tid - 1 : kZero;
+  const int iR = qx + 1 < NQ ? tid + 1 : kZero;
+  const int iB = rb > 0 ? tid - NQ : (rank > 0 ? kZero + 1 + qx : kZero);
+  const int iA = rb + 1 < nrb ? tid + NQ : (rank + 1 < C ? kZero + 1 + qx : kZero);
+  const unsigned oL = 8u * iL, oR = 8u * iR, oB = 16u * iB, oA = 16u * iA, oT8 = 8u * tid, oT16 = 16u * tid;
+  unsigned char* const E0 = smem + L.edge;
+
+  // rho0 into registers, its edges into parity 0.
+  float2 S[kQR][kQC];
+  const float* rho0 = reinterpret_cast<const float*>(p.rho0);
+#pragma unroll
+  for (int r = 0; r < kQR; ++r)
+#pragma unroll
+    for (int c = 0; c < kQC; ++c) {
+      const int m = m0 + c, pa = pb + 2 * r;
+      float a = 0.0f, b = 0.0f;
+      if (owner && m < M) {
+        if (pa < p1) a = rho0[(int64_t)pa * M + m];
+        if (pa + 1 < p1) b = rho0[(int64_t)(pa + 1) * M + m];
+      }
+      S[r][c] = v_make(a, b);
+    }
+  // The row arrays of the neighbouring CTAs: our first row is the row above
+  // CTA rank-1 (its array 0), our last row the row below CTA rank+1 (array 1).
+  unsigned char* nb_dn = nullptr;
+  unsigned char* nb_up = nullptr;
+  if (C > 1) {
+    if (rank > 0 && rb == 0) nb_dn = cluster.map_shared_rank(E0, rank - 1) + G::row(0) + 16u * (kZero + 1 + qx);
+    if (rank + 1 < C && rb == nrb - 1)
+      nb_up = cluster.map_shared_rank(E0, rank + 1) + G::row(1) + 16u * (kZero + 1 + qx);
+  }
+  auto publish = [&](int par) {
+    unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
+#pragma unroll
+    for (int r = 0; r < kQR; ++r) {
+      *reinterpret_cast<float2*>(Ep + G::col(0, r) + oT8) = S[r][0];
+      *reinterpret_cast<float2*>(Ep + G::col(1, r) + oT8) = S[r][kQC - 1];
+    }
+    const float4 first = make_float4(S[0][0].x, S[0][1].x, S[0][2].x, S[0][3].x);
+    const float4 last = make_float4(S[kQR - 1][0].y, S[kQR - 1][1].y, S[kQR - 1][2].y, S[kQR - 1][3].y);
+    *reinterpret_cast<float4*>(Ep + G::row(0) + oT16) = first;
+    *reinterpret_cast<float4*>(Ep + G::row(1) + oT16) = last;
+    const size_t po = par ? G::par_bytes : 0;
+    if (nb_dn) *reinterpret_cast<float4*>(nb_dn + po) = first;
+    if (nb_up) *reinterpret_cast<float4*>(nb_up + po) = last;
+  };
+  if (owner) publish(0);
+  if (C > 1) cluster.sync();
+  else __syncthreads();
+
+  bool mine_rec = false;
+  for (int i = tid; i < nt; i += blockDim.x) mine_rec |= t_rec[i] != 0;
+  const bool any_rec = __syncthreads_or(mine_rec) != 0;
+
+  int lo = 0, hi = -1;
+  auto advance = [&](int k, int& l, int& h) {
+    while (l < nt && t_K[l] < k) ++l;
+    while (h + 1 < nt && t_L[h + 1] <= k) ++h;
+  };
+  advance(0, lo, hi);
+  int flo = 0, fhi = -1;
+  if (wwarp) {
+    for (int kf = 1; kf <= kWeightLead; ++kf) {
+      advance(kf, flo, fhi);
+      if (kf <= Kmax)
+        for (int i = flo + lane; i <= fhi; i += 32)
+          if (t_wb[i]) cp_async_elem(ring + (kf % kWeightRing) * nt + i, t_wb[i] + kf);
+      cp_async_commit();
+    }
+  }
+  int ecur = ebeg;
+  int slot_prev = 0, slot_cur = 1;                 // ring slots of jumps k-1 and k
+  int slot_pre = (1 + kWeightLead) % kWeightRing;  // ring slot of jump k + lead
+
+  // One row pair r of the update, in place.  TOP: the row pair holding row
+  // P-1 (no protein birth out of it, row P absent).
+  auto row_pair = [&](const unsigned char* Ep, int r, int pbk, float (&prevY)[kQC], auto top) {
+    constexpr bool TOP = decltype(top)::value;
+    const float2 lpair = *reinterpret_cast<const float2*>(Ep + G::col(1, r) + oL);  // left block's right column
+    const float2 rpair = *reinterpret_cast<const float2*>(Ep + G::col(0, r) + oR);  // right block's left column
+    float4 above;  // row pb + kRows, for the last row pair
+    if (r + 1 == kQR) above = *reinterpret_cast<const float4*>(Ep + G::row(0) + oA);
+    const int pp = pbk + 2 * r;
+    const float2 fpp = v_make((float)pp, (float)(pp + 1));
+    const float2 cup = v_fma(c_gp, fpp, c_gp);  // gamma_p (p+1) from p+1
+    float2 oldl = lpair;                         // old value of the column to the left
+#pragma unroll
+    for (int c = 0; c < kQC; ++c) {
+      const float2 cur = S[r][c];
+      const float2 right = c + 1 < kQC ? S[r][c + 1] : rpair;
+      const float nx = r + 1 < kQR ? S[r + 1][c].x
+                                   : (c == 0 ? above.x : c == 1 ? above.y : c == 2 ? above.z : above.w);
+      float2 dg = v_fma(c_ngp, fpp, d0p[c]);  // 1 - e_{m,p}
+      if (TOP) {
+        if (pp == P - 1) dg.x = f_add(dg.x, cdv[c]);
+        else dg.y = f_add(dg.y, cdv[c]);
+      }
+      float2 y = v_fma(crp[c], right, v_fma(c_l, oldl, v_mul(dg, cur)));
+      y.x = f_fma(cup.x, cur.y, f_fma(cdv[c], prevY[c], y.x));
+      y.y = f_fma(cup.y, nx, f_fma(cdv[c], cur.x, y.y));
+      if (TOP && pp + 1 >= P) y.y = 0.0f;
+      oldl = cur;
+      prevY[c] = cur.y;
+      S[r][c] = y;
+    }
+  };
+
+  // ---- the jump chain -------------------------------------------------------
+  for (int k = 1; k <= Kmax + 1; ++k) {
+    const int par = (k - 1) & 1;
+    const double* rprev = pw + par * nt;
+    double* rcur = pw + (par ^ 1) * nt;
+    const float* wprev = ring + slot_prev * nt;
+    float* wcur = ring + slot_cur * nt;
+    const int plo = lo, phi = hi;
+    int clo = lo, chi = hi;
+    advance(k, clo, chi);
+    const bool jump = k <= Kmax;
+    if (wwarp) {
+      const int kf = k + kWeightLead;
+      advance(kf, flo, fhi);
+      if (kf <= Kmax)
+        for (int i = flo + lane; i <= fhi; i += 32)
+          if (t_wb[i]) cp_async_elem(ring + slot_pre * nt + i, t_wb[i] + kf);
+      cp_async_commit();
+      if (jump && any_rec)
+        for (int i = clo + lane; i <= chi; i += 32) {
+          if (!t_rec[i]) continue;
+          const double Pk = (k == t_L[i]) ? t_PL[i] : __dmul_rn(rprev[i], __ddiv_rn(t_x[i], (double)k));
+          rcur[i] = Pk;
+          wcur[i] = (float)(Pk + (k == t_K[i] ? t_tail[i] : 0.0));
+        }
+      cp_async_wait<kWeightLead>();
+    }
+    if (owner) {
+      // Observations of rho_{k-1} for the active times (Kahan, FP32).
+      if (plo <= phi) {
+        while (ecur < eend && (ent[ecur].y >> 6) < plo) ++ecur;
+        for (int e = ecur; e < eend; ++e) {
+          const int2 en = ent[e];
+          const int ti = en.y >> 6;
+          if (ti > phi) break;
+          const float v = pick<kQR>(S, en.y & 63);
+          const float w = wprev[ti];
+          const float y = __fsub_rn(__fmul_rn(w, v), acc_c[en.x]);
+          const float s0 = acc_s[en.x];
+          const float t = __fadd_rn(s0, y);
+          acc_c[en.x] = __fsub_rn(__fsub_rn(t, s0), y);
+          acc_s[en.x] = t;
+        }
+      }
+      if (jump) {
+        // Edges of rho_{k-1} around the block (zero slots outside the box).
+        const unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
+        const float4 below = *reinterpret_cast<const float4*>(Ep + G::row(1) + oB);  // row pb - 1
+        float prevY[kQC] = {below.x, below.y, below.z, below.w};
+        const int pbk = opaque(pb);
+        if (!special) {
+#pragma unroll
+          for (int r = 0; r < kQR; ++r) row_pair(Ep, r, pbk, prevY, std::false_type{});
+        } else {
+#pragma unroll
+          for (int r = 0; r < kQR; ++r) {
+            if (r == rtop) row_pair(Ep, r, pbk, prevY, std::true_type{});
+            else if (rtop >= 0 && r > rtop) {  // row pairs beyond the box stay zero
+#pragma unroll
+              for (int c = 0; c < kQC; ++c) S[r][c] = v_make(0.0f, 0.0f);
+            } else {
+              row_pair(Ep, r, pbk, prevY, std::false_type{});
+            }
+#pragma unroll
+            for (int c = 0; c < kQC; ++c)  // padding columns of the last quad stay zero
+              if (!((colmask >> c) & 1)) S[r][c] = v_make(0.0f, 0.0f);
+          }
+        }
+        publish(par ^ 1);
+      }
+    }
+    if (C > 1) {
+      cluster_arrive();
+      cluster_wait();
+    } else {
+      __syncthreads();
+    }
+    lo = clo;
+    hi = chi;
+    slot_prev = slot_cur;
+    slot_cur = slot_cur + 1 == kWeightRing ? 0 : slot_cur + 1;
+    slot_pre = slot_pre + 1 == kWeightRing ? 0 : slot_pre + 1;
+  }
+  if (wwarp) cp_async_wait<0>();
+
+  // ---- epilogue: sum_g c_g log(a_g) over the cluster's accumulators ---------
+  if (C > 1) cluster.sync();
+  else __syncthreads();
+  if (rank == 0) {
+    double ll = 0.0;
+    bool bad = false;
+    for (int g = tid; g < p.G; g += blockDim.x) {
+      double a = 0.0;
+      const int q0 = (int)p.mptr[g], q1 = (int)p.mptr[g + 1];
+      for (int q = q0; q < q1; ++q)
+        for (int r = 0; r < C; ++r) {
+          const float* rs = (C == 1) ? acc_s : cluster.map_shared_rank(acc_s, r);
+          const float* rc = (C == 1) ? acc_c : cluster.map_shared_rank(acc_c, r);
+          double v = (double)rs[q];
+          v -= (double)rc[q];
+          a += v;
+        }
+      const double c = p.counts[g];
+      if (c == 0.0) continue;
+      if (a > 0.0) ll += c * log(a);
+      else if (a > -1e-30) ll = -INFINITY;
+      else bad = true;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(kFull, ll, o);
+    double* red = reinterpret_cast<double*>(smem + L.edge);  // the edge arrays are no longer needed
+    __syncthreads();
+    if (lane == 0) red[warp] = ll;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < nwarps; ++w) tot += red[w];
+      if (isnan(tot)) set_status(p.status, kStatusNumeric);
+      p.ll[job] = tot;
+    }
+    if (bad) set_status(p.status, kStatusNumeric);
+  }
+  if (C > 1) cluster.sync();  // keep every CTA's accumulators alive until rank 0 is done
+}
+
+}  // namespace
+
+// Cluster size, rows per CTA and threads for an M x P box, or false when the
+// box does not fit this kernel (then the shared-memory kernel runs).
+bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluster, RegPlan* out) {
+  if (M < 1 || P < 1 || ntimes < 1) return false;
+  const int NQ = (int)((M + kQC - 1) / kQC);
+  if (NQ > kMaxNQ) return false;
+  // Fewest CTAs per instance first; for each, 8 rows per thread before 10.
+  for (int C = 1; C <= max_cluster; ++C)
+    for (int QR = 4; QR <= 5; ++QR) {
+      const int rows_blk = 2 * QR;
+      const int64_t rows = (P + C - 1) / C;
+      const int RS = (int)((rows + rows_blk - 1) / rows_blk) * rows_blk;
+      if ((int64_t)(C - 1) * RS >= P) continue;  // the last CTA would be empty
+      const int Tc = NQ * (RS / rows_blk);
+      if (Tc > kRegThreads) continue;
+      const size_t edge = 2 * (QR == 5 ? EdgeGeo<5>::par_bytes : EdgeGeo<4>::par_bytes);
+      const RegLayout L = reg_layout(edge, ntimes, nmem);
+      if (L.total + 1024 > 227 * 1024) continue;  // leave room for static shared memory
+      out->cluster = C;
+      out->rows = RS;
+      out->nq = NQ;
+      out->qr = QR;
+      out->threads = ((Tc + 31) / 32) * 32;
+      out->smem = L.total;
+      return true;
+    }
+  return false;
+}
+
+template <int QR>
+cudaError_t launch_reg(const ChainParams& p, const RegPlan& rp, cudaStream_t s) {
+  static int smem_set = 0;
+  static bool nonportable = false;
+  auto kern = chain_reg2d_kernel<QR>;
+  cudaError_t e;
+  if ((int)rp.smem > smem_set) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rp.smem);
+    if (e != cudaSuccess) return e;
+    smem_set = (int)rp.smem;
+  }
+  if (rp.cluster > 8 && !nonportable) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    nonportable = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(p.B * rp.cluster));
+  cfg.blockDim = dim3((unsigned)rp.threads);
+  cfg.dynamicSmemBytes = rp.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)rp.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, p, rp.nq, rp.rows);
+}
+
+cudaError_t launch_chain_reg2d(const ChainParams& p, const RegPlan& rp, cudaStream_t s) {
+  if (p.B <= 0) return cudaSuccess;
+  return rp.qr == 5 ? launch_reg<5>(p, rp, s) : launch_reg<4>(p, rp, s);
+}
+
+}  // namespace mjp

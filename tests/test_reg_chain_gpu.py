@@ -1,0 +1,101 @@
+"""The register-resident chain kernel (FP32 mRNA/protein log-likelihood):
+bit-identical to the shared-memory chain kernel on single-member observation
+groups (same operation order per state), and within the FP32 tolerance of the
+oracle, over box shapes that exercise ragged column quads, odd row counts and
+clusters of 1, 2 and 3 CTAs."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+PER_OBS_FP32 = 5e-5  # per observation, derived in test_parity_gpu.py
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_05647_gb300 import build as lib_build
+    lib_build.build()
+    torch.cuda.set_device(0)
+
+
+def _case(dims, theta, times, cells, seed):
+    snaps = synth.gillespie_snapshots(synth.MRNA_PROT2D, dims, theta, times, cells, synth.rng(2, seed))
+    obs = synth.snapshot_obs(synth.MRNA_PROT2D, dims, snaps)
+    n = dims[0] * dims[1]
+    return obs, synth.delta(n, 0)
+
+
+def _loglik(dims, theta, thetas, times, obs, rho0, chain):
+    import paper_2312_05647_gb300 as mjp
+    m = mjp.Model(synth.MRNA_PROT2D, dims, theta, mjp.FP32)
+    m.set_option(mjp.OPT_CHAIN, chain)
+    o = mjp.Obs(dims[0] * dims[1], times, obs, rho0)
+    ll = mjp.loglik(m, o, thetas)
+    m.check()
+    return ll
+
+
+@pytest.mark.parametrize("dims,theta", [
+    ((30, 40), (8.0, 1.0, 1.0, 0.3)),        # 1 CTA, two padding columns in the last quad
+    ((37, 53), (10.0, 1.0, 1.5, 0.4)),       # odd rows, three padding columns
+    ((200, 200), (20.0, 1.0, 5.0, 0.1)),     # the benchmark box: 2 CTAs, 10 rows per thread
+    ((120, 330), (15.0, 1.0, 2.0, 0.2)),     # 2 CTAs, uneven split
+    ((136, 401), (12.0, 1.0, 2.0, 0.15)),    # 3 CTAs, odd rows, short last CTA
+])
+def test_register_chain_is_bitwise_equal_to_shared_memory_chain(dims, theta):
+    times = np.array([0.05, 0.2, 0.6, 1.5])
+    obs, rho0 = _case(dims, theta, times, 30, seed=sum(dims))
+    thetas = synth.jitter(theta, 3, 0.2, synth.rng(2, 7))
+    a = _loglik(dims, theta, thetas, times, obs, rho0, 1)
+    b = _loglik(dims, theta, thetas, times, obs, rho0, 2)
+    assert np.all(np.isfinite(a))
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("dims,theta", [((37, 53), (10.0, 1.0, 1.5, 0.4)), ((200, 200), (20.0, 1.0, 5.0, 0.1))])
+def test_register_chain_matches_oracle(dims, theta):
+    times = np.array([0.1, 0.5, 1.2])
+    obs, rho0 = _case(dims, theta, times, 40, seed=3)
+    thetas = synth.jitter(theta, 2, 0.2, synth.rng(2, 8))
+    ll = _loglik(dims, theta, thetas, times, obs, rho0, 2)
+    nobs = sum(c.sum() for _, c in obs)
+    for b in range(len(thetas)):
+        ref = oracle.loglik(oracle.build_model(synth.MRNA_PROT2D, list(dims), thetas[b]), rho0, times, obs)
+        assert abs(ll[b] - ref) <= PER_OBS_FP32 * nobs
+
+
+def test_register_chain_groups_of_many_states():
+    # Groups of 1, 3 and 5 states: each member accumulates in its owner thread.
+    import paper_2312_05647_gb300 as mjp
+    dims, theta = (30, 40), [6.0, 1.0, 1.5, 0.3]
+    n = 1200
+    times = np.array([0.4, 1.5])
+    gen = np.random.default_rng(21)
+    obs = []
+    for _ in times:
+        mem, cnt = [], []
+        for size in (1, 3, 5, 3, 1):
+            mem.append(gen.choice(n // 4, size=size, replace=False))
+            cnt.append(float(gen.integers(1, 9)))
+        obs.append((mem, np.array(cnt)))
+    rho0 = synth.delta(n, 0)
+    ll = _loglik(dims, theta, np.array([theta]), times, obs, rho0, 2)
+    ref = oracle.loglik(oracle.build_model(synth.MRNA_PROT2D, list(dims), theta), rho0, times, obs)
+    nobs = sum(c.sum() for _, c in obs)
+    assert abs(ll[0] - ref) <= PER_OBS_FP32 * nobs
+
+
+def test_register_chain_option_rejects_other_models():
+    import paper_2312_05647_gb300 as mjp
+    from paper_2312_05647_gb300.capi import MJPError
+    m = mjp.Model(synth.MRNA_PROT2D, [20, 20], [5.0, 1.0, 1.0, 0.2], mjp.FP64)
+    m.set_option(mjp.OPT_CHAIN, 2)
+    o = mjp.Obs(400, [0.5], [([np.array([0])], np.array([1.0]))], synth.delta(400, 0))
+    with pytest.raises(MJPError):
+        mjp.loglik(m, o, np.array([[5.0, 1.0, 1.0, 0.2]]))
