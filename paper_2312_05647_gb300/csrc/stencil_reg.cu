@@ -38,8 +38,7 @@ namespace mjp {
 namespace {
 
 constexpr int kQC = 4;            // columns per thread block of states
-constexpr int kRegThreads = 512;  // threads per CTA at most (16 warps, <= 128 registers each); warp 0
-                                  // also streams the Poisson weights into the ring
+constexpr int kRegThreads = 512;  // threads per CTA at most (16 warps, <= 128 registers each)
 constexpr int kMaxNQ = 512;       // column quads (M <= 2048)
 // Fixed strides of the edge arrays (per parity):
 //  - columns [2 sides][QR][kCStr] float2: the left (side 0) and right (side 1)
@@ -51,6 +50,10 @@ constexpr int kMaxNQ = 512;       // column quads (M <= 2048)
 // Every neighbour read goes through a fixed per-thread slot, so threads at
 // the box edge read a zero slot instead of branching.
 constexpr int kZero = kRegThreads;
+// Poisson weights are staged per time in a ring of kStage jumps, filled
+// kChunk jumps at a time, one chunk ahead, by every thread of the CTA.
+constexpr int kChunk = 32;
+constexpr int kStage = 2 * kChunk;
 constexpr int kCStr = kRegThreads + 1;
 constexpr int kRStr = kRegThreads + 1 + kMaxNQ;
 
@@ -78,7 +81,7 @@ __host__ __device__ inline RegLayout reg_layout(size_t edge_bytes, int nt, int n
   s.tL = o; o += align_up(4 * (size_t)nt, 8);
   s.tK = o; o += align_up(4 * (size_t)nt, 8);
   s.trec = o; o += align_up(4 * (size_t)nt, 8);
-  s.ring = o; o += align_up(4 * kWeightRing * (size_t)nt, 8);
+  s.ring = o; o += align_up(4 * kStage * (size_t)nt, 16);
   s.gptr = o; o += align_up(4 * (size_t)(nt + 1), 8);
   s.ent = o; o += 8 * (size_t)nmem;
   s.acc_s = o; o += align_up(4 * (size_t)nmem, 8);
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
   const int p0 = rank * RS;
   const int p1 = min(P, p0 + RS);
   const int nrb = p1 > p0 ? (p1 - p0 + kRows - 1) / kRows : 0;  // row blocks of this CTA
-  const bool wwarp = warp == 0;  // streams the weights (and holds states like every warp)
+  const bool wwarp = warp == 0;  // runs the weight recurrence of windows without a stored copy
   const int qx = tid % NQ, rb = tid / NQ;
   const bool owner = rb < nrb;   // this thread holds a block of states
   const int m0 = kQC * qx, pb = p0 + kRows * rb;  // first column and first row of the block
@@ -177,7 +180,8 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
     t_rec[i] = (w.woff < 0 || !arena) ? 1 : 0;
     t_wb[i] = (w.woff >= 0 && arena) ? arena + (w.woff - w.L) : nullptr;
     pw[i] = (w.L == 0) ? w.PL : 0.0;
-    if (w.L == 0) ring[i] = (w.woff >= 0 && arena) ? arena[w.woff] : (float)(w.PL + (w.K == 0 ? w.tail : 0.0));
+    if (w.L == 0 && (w.woff < 0 || !arena))  // jump 0 of a window without a stored copy
+      ring[i * kStage] = (float)(w.PL + (w.K == 0 ? w.tail : 0.0));
   }
   for (int i = tid; i <= nt; i += blockDim.x) s_gptr[i] = (int)p.gptr[i];
   const double omega = p.info[job].omega;
@@ -247,10 +251,8 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
     d0p[c] = v_make(d0, d0);
   }
   const float2 c_l = v_make(co.a, co.a), c_gp = v_make(co.d, co.d), c_ngp = v_make(-co.d, -co.d);
-  // Row pair of this block that holds row P-1 (-1 if none); blocks with it or
-  // with padding columns take the checked update.
+  // Row pair of this block that holds row P-1 (-1 if none).
   const int rtop = (P - 1 >= pb && P - 1 < pb + kRows) ? (P - 1 - pb) / 2 : -1;
-  const bool special = rtop >= 0 || colmask != (1 << kQC) - 1;
 
   // Fixed neighbour slots: left block's right column, right block's left
   // column, the row below (a last row) and the row above (a first row).
@@ -314,19 +316,22 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
     while (h + 1 < nt && t_L[h + 1] <= k) ++h;
   };
   advance(0, lo, hi);
-  int flo = 0, fhi = -1;
-  if (wwarp) {
-    for (int kf = 1; kf <= kWeightLead; ++kf) {
-      advance(kf, flo, fhi);
-      if (kf <= Kmax)
-        for (int i = flo + lane; i <= fhi; i += 32)
-          if (t_wb[i]) cp_async_elem(ring + (kf % kWeightRing) * nt + i, t_wb[i] + kf);
-      cp_async_commit();
+  // Stage the stored weights of jumps [k0, k0 + kChunk) of every window into
+  // the ring (slot j % kStage), spread over all threads.
+  auto stage_chunk = [&](int k0) {
+    const int k1 = min(k0 + kChunk, Kmax + 1);
+    for (int e = tid; e < nt * kChunk; e += blockDim.x) {
+      const int i = e / kChunk, j = k0 + (e - i * kChunk);
+      if (j < k1 && t_wb[i] && j >= t_L[i] && j <= t_K[i])
+        cp_async_elem(ring + i * kStage + (j & (kStage - 1)), t_wb[i] + j);
     }
-  }
+    cp_async_commit();
+  };
+  stage_chunk(0);
+  stage_chunk(kChunk);
+  cp_async_wait<1>();  // chunk 0 has landed
+  __syncthreads();
   int ecur = ebeg;
-  int slot_prev = 0, slot_cur = 1;                 // ring slots of jumps k-1 and k
-  int slot_pre = (1 + kWeightLead) % kWeightRing;  // ring slot of jump k + lead
 
   // One row pair r of the update, in place.  TOP: the row pair holding row
   // P-1 (no protein birth out of it, row P absent).
@@ -366,28 +371,24 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
     const int par = (k - 1) & 1;
     const double* rprev = pw + par * nt;
     double* rcur = pw + (par ^ 1) * nt;
-    const float* wprev = ring + slot_prev * nt;
-    float* wcur = ring + slot_cur * nt;
+    const int sprev = (k - 1) & (kStage - 1);  // ring slot of jump k-1
     const int plo = lo, phi = hi;
     int clo = lo, chi = hi;
     advance(k, clo, chi);
     const bool jump = k <= Kmax;
-    if (wwarp) {
-      const int kf = k + kWeightLead;
-      advance(kf, flo, fhi);
-      if (kf <= Kmax)
-        for (int i = flo + lane; i <= fhi; i += 32)
-          if (t_wb[i]) cp_async_elem(ring + slot_pre * nt + i, t_wb[i] + kf);
-      cp_async_commit();
-      if (jump && any_rec)
-        for (int i = clo + lane; i <= chi; i += 32) {
-          if (!t_rec[i]) continue;
-          const double Pk = (k == t_L[i]) ? t_PL[i] : __dmul_rn(rprev[i], __ddiv_rn(t_x[i], (double)k));
-          rcur[i] = Pk;
-          wcur[i] = (float)(Pk + (k == t_K[i] ? t_tail[i] : 0.0));
-        }
-      cp_async_wait<kWeightLead>();
-    }
+    // Chunk c (jumps [c kChunk, (c+1) kChunk)) is staged at jump (c-1) kChunk + 1,
+    // after the last read of the slots it reuses (chunk c-2's, read up to jump
+    // (c-1) kChunk), and waited for at jump c kChunk, before the barrier that
+    // precedes its first read.
+    if ((k & (kChunk - 1)) == 0) cp_async_wait<0>();
+    if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
+    if (wwarp && jump && any_rec)  // windows without a stored copy: P_k = P_{k-1} x / k
+      for (int i = clo + lane; i <= chi; i += 32) {
+        if (!t_rec[i]) continue;
+        const double Pk = (k == t_L[i]) ? t_PL[i] : __dmul_rn(rprev[i], __ddiv_rn(t_x[i], (double)k));
+        rcur[i] = Pk;
+        ring[i * kStage + (k & (kStage - 1))] = (float)(Pk + (k == t_K[i] ? t_tail[i] : 0.0));
+      }
     if (owner) {
       // Observations of rho_{k-1} for the active times (Kahan, FP32).
       if (plo <= phi) {
@@ -397,7 +398,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
           const int ti = en.y >> 6;
           if (ti > phi) break;
           const float v = pick<kQR>(S, en.y & 63);
-          const float w = wprev[ti];
+          const float w = ring[ti * kStage + sprev];
           const float y = __fsub_rn(__fmul_rn(w, v), acc_c[en.x]);
           const float s0 = acc_s[en.x];
           const float t = __fadd_rn(s0, y);
@@ -411,23 +412,23 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
         const float4 below = *reinterpret_cast<const float4*>(Ep + G::row(1) + oB);  // row pb - 1
         float prevY[kQC] = {below.x, below.y, below.z, below.w};
         const int pbk = opaque(pb);
-        if (!special) {
+        const int rtk = opaque(rtop);
 #pragma unroll
-          for (int r = 0; r < kQR; ++r) row_pair(Ep, r, pbk, prevY, std::false_type{});
-        } else {
+        for (int r = 0; r < kQR; ++r) {
+          if (r == rtk) row_pair(Ep, r, pbk, prevY, std::true_type{});  // the row pair holding row P-1
+          else if (rtk >= 0 && r > rtk) {                               // row pairs beyond the box stay zero
 #pragma unroll
-          for (int r = 0; r < kQR; ++r) {
-            if (r == rtop) row_pair(Ep, r, pbk, prevY, std::true_type{});
-            else if (rtop >= 0 && r > rtop) {  // row pairs beyond the box stay zero
-#pragma unroll
-              for (int c = 0; c < kQC; ++c) S[r][c] = v_make(0.0f, 0.0f);
-            } else {
-              row_pair(Ep, r, pbk, prevY, std::false_type{});
-            }
-#pragma unroll
-            for (int c = 0; c < kQC; ++c)  // padding columns of the last quad stay zero
-              if (!((colmask >> c) & 1)) S[r][c] = v_make(0.0f, 0.0f);
+            for (int c = 0; c < kQC; ++c) S[r][c] = v_make(0.0f, 0.0f);
+          } else {
+            row_pair(Ep, r, pbk, prevY, std::false_type{});
           }
+        }
+        if (colmask != (1 << kQC) - 1) {  // padding columns of the last quad stay zero
+#pragma unroll
+          for (int r = 0; r < kQR; ++r)
+#pragma unroll
+            for (int c = 0; c < kQC; ++c)
+              if (!((colmask >> c) & 1)) S[r][c] = v_make(0.0f, 0.0f);
         }
         publish(par ^ 1);
       }
@@ -440,11 +441,8 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
     }
     lo = clo;
     hi = chi;
-    slot_prev = slot_cur;
-    slot_cur = slot_cur + 1 == kWeightRing ? 0 : slot_cur + 1;
-    slot_pre = slot_pre + 1 == kWeightRing ? 0 : slot_pre + 1;
   }
-  if (wwarp) cp_async_wait<0>();
+  cp_async_wait<0>();
 
   // ---- epilogue: sum_g c_g log(a_g) over the cluster's accumulators ---------
   if (C > 1) cluster.sync();
