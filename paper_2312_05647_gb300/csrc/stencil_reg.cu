@@ -434,7 +434,11 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
       }
     }
     if (C > 1) {
-      cluster_arrive();
+      // Edges written into this CTA need CTA-scope ordering; only the threads
+      // that wrote into a neighbour CTA pay a cluster-scope fence.
+      if (nb_dn || nb_up) fence_cluster();
+      else fence_cta();
+      cluster_arrive_relaxed();
       cluster_wait();
     } else {
       __syncthreads();
