@@ -91,14 +91,19 @@ __host__ __device__ inline RegLayout reg_layout(size_t edge_bytes, int nt, int n
 }
 
 // Register value of slot (row pair r, column c, half h) = ((r * 4 + c) * 2 + h)
-// with a runtime slot, by selection (no local-memory array).
+// with a runtime slot, by a tree of selections (no local-memory array): the
+// half, the two column bits, then the row pair.
 template <int QR>
 __device__ __forceinline__ float pick(const float2 (&S)[QR][kQC], int slot) {
+  const bool h = slot & 1, c0 = slot & 2, c1 = slot & 4;
+  const int r = slot >> 3;
   float v = 0.0f;
 #pragma unroll
-  for (int i = 0; i < QR * kQC; ++i) {
-    v = (slot == 2 * i) ? S[i / kQC][i % kQC].x : v;
-    v = (slot == 2 * i + 1) ? S[i / kQC][i % kQC].y : v;
+  for (int q = 0; q < QR; ++q) {
+    const float x0 = h ? S[q][0].y : S[q][0].x, x1 = h ? S[q][1].y : S[q][1].x;
+    const float x2 = h ? S[q][2].y : S[q][2].x, x3 = h ? S[q][3].y : S[q][3].x;
+    const float lo = c0 ? x1 : x0, hi = c0 ? x3 : x2;
+    v = (r == q) ? (c1 ? hi : lo) : v;
   }
   return v;
 }
