@@ -335,8 +335,44 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
   stage_chunk(0);
   stage_chunk(kChunk);
   cp_async_wait<1>();  // chunk 0 has landed
-  __syncthreads();
+
+  // Observations of rho_k for the active times [l, h] of jump k (Kahan, FP32).
   int ecur = ebeg;
+  auto accumulate = [&](int k, int l, int h) {
+    if (!owner || l > h) return;
+    const int sk = k & (kStage - 1);
+    while (ecur < eend && (ent[ecur].y >> 6) < l) ++ecur;
+    for (int e = ecur; e < eend; ++e) {
+      const int2 en = ent[e];
+      const int ti = en.y >> 6;
+      if (ti > h) break;
+      const float v = pick<kQR>(S, en.y & 63);
+      const float w = ring[ti * kStage + sk];
+      const float y = __fsub_rn(__fmul_rn(w, v), acc_c[en.x]);
+      const float s0 = acc_s[en.x];
+      const float t = __fadd_rn(s0, y);
+      acc_c[en.x] = __fsub_rn(__fsub_rn(t, s0), y);
+      acc_s[en.x] = t;
+    }
+  };
+  // Weights of jump kn for windows without a stored copy (Algorithm 2's
+  // recurrence P_kn = P_{kn-1} x / kn from P_L, tail added at K), one jump
+  // ahead of their use; warp 0.
+  int rlo = lo, rhi = hi;
+  auto rec_step = [&](int kn) {
+    advance(kn, rlo, rhi);
+    const double* rprev = pw + ((kn - 1) & 1) * nt;
+    double* rcur = pw + (kn & 1) * nt;
+    for (int i = rlo + lane; i <= rhi; i += 32) {
+      if (!t_rec[i]) continue;
+      const double Pk = (kn == t_L[i]) ? t_PL[i] : __dmul_rn(rprev[i], __ddiv_rn(t_x[i], (double)kn));
+      rcur[i] = Pk;
+      ring[i * kStage + (kn & (kStage - 1))] = (float)(Pk + (kn == t_K[i] ? t_tail[i] : 0.0));
+    }
+  };
+  if (wwarp && any_rec && Kmax >= 1) rec_step(1);
+  __syncthreads();
+  accumulate(0, lo, hi);  // rho_0 with the weights of jump 0
 
   // One row pair r of the update, in place.  TOP: the row pair holding row
   // P-1 (no protein birth out of it, row P absent).
@@ -372,46 +408,10 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
   };
 
   // ---- the jump chain -------------------------------------------------------
-  for (int k = 1; k <= Kmax + 1; ++k) {
+  for (int k = 1; k <= Kmax; ++k) {
     const int par = (k - 1) & 1;
-    const double* rprev = pw + par * nt;
-    double* rcur = pw + (par ^ 1) * nt;
-    const int sprev = (k - 1) & (kStage - 1);  // ring slot of jump k-1
-    const int plo = lo, phi = hi;
-    int clo = lo, chi = hi;
-    advance(k, clo, chi);
-    const bool jump = k <= Kmax;
-    // Chunk c (jumps [c kChunk, (c+1) kChunk)) is staged at jump (c-1) kChunk + 1,
-    // after the last read of the slots it reuses (chunk c-2's, read up to jump
-    // (c-1) kChunk), and waited for at jump c kChunk, before the barrier that
-    // precedes its first read.
-    if ((k & (kChunk - 1)) == 0) cp_async_wait<0>();
-    if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
-    if (wwarp && jump && any_rec)  // windows without a stored copy: P_k = P_{k-1} x / k
-      for (int i = clo + lane; i <= chi; i += 32) {
-        if (!t_rec[i]) continue;
-        const double Pk = (k == t_L[i]) ? t_PL[i] : __dmul_rn(rprev[i], __ddiv_rn(t_x[i], (double)k));
-        rcur[i] = Pk;
-        ring[i * kStage + (k & (kStage - 1))] = (float)(Pk + (k == t_K[i] ? t_tail[i] : 0.0));
-      }
     if (owner) {
-      // Observations of rho_{k-1} for the active times (Kahan, FP32).
-      if (plo <= phi) {
-        while (ecur < eend && (ent[ecur].y >> 6) < plo) ++ecur;
-        for (int e = ecur; e < eend; ++e) {
-          const int2 en = ent[e];
-          const int ti = en.y >> 6;
-          if (ti > phi) break;
-          const float v = pick<kQR>(S, en.y & 63);
-          const float w = ring[ti * kStage + sprev];
-          const float y = __fsub_rn(__fmul_rn(w, v), acc_c[en.x]);
-          const float s0 = acc_s[en.x];
-          const float t = __fadd_rn(s0, y);
-          acc_c[en.x] = __fsub_rn(__fsub_rn(t, s0), y);
-          acc_s[en.x] = t;
-        }
-      }
-      if (jump) {
+      {
         // Edges of rho_{k-1} around the block (zero slots outside the box).
         const unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
         const float4 below = *reinterpret_cast<const float4*>(Ep + G::row(1) + oB);  // row pb - 1
@@ -438,18 +438,23 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
         publish(par ^ 1);
       }
     }
-    if (C > 1) {
-      // Edges written into this CTA need CTA-scope ordering; only the threads
-      // that wrote into a neighbour CTA pay a cluster-scope fence.
-      if (nb_dn || nb_up) fence_cluster();
-      else fence_cta();
-      cluster_arrive_relaxed();
-      cluster_wait();
-    } else {
-      __syncthreads();
-    }
-    lo = clo;
-    hi = chi;
+    // Chunk c (jumps [c kChunk, (c+1) kChunk)) is staged at jump (c-1) kChunk + 1,
+    // after the last read of the slots it reuses (chunk c-2's, read up to jump
+    // (c-1) kChunk - 1), and waited for at jump c kChunk - 1, before the barrier
+    // that precedes its first read.
+    if ((k & (kChunk - 1)) == kChunk - 1) cp_async_wait<0>();
+    // Edges written into this CTA need CTA-scope ordering; only the threads
+    // that wrote into a neighbour CTA pay a cluster-scope fence.
+    if (nb_dn || nb_up) fence_cluster();
+    else fence_cta();
+    cluster_arrive_relaxed();
+    // Work that touches no edge overlaps the barrier: observations of rho_k,
+    // the next chunk of weights, the recurrence one jump ahead.
+    advance(k, lo, hi);
+    accumulate(k, lo, hi);
+    if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
+    if (wwarp && any_rec && k + 1 <= Kmax) rec_step(k + 1);
+    cluster_wait();
   }
   cp_async_wait<0>();
 
