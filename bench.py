@@ -159,7 +159,7 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-CHAIN_SOURCES = ("stencil.cu", "internal.cuh")
+CHAIN_SOURCES = ("stencil_reg.cu", "chain_common.cuh", "internal.cuh")
 
 
 def kernel_source_sha() -> str:
