@@ -742,7 +742,7 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   bool use_reg = false;
   if (m->chain != 1 && m->kind == MJP_MRNA_PROT2D && m->precision == MJP_FP32 && m->renorm == 0 &&
       (m->chain == 2 || (m->cluster == 0 && m->threads == 0)))
-    use_reg = chain_reg2d_plan(m->M, m->P, nt, obs->nmem, 8, &rp);
+    use_reg = chain_reg2d_plan(m->M, m->P, nt, obs->nmem, 8, m->threads, &rp);
   if (m->chain == 2 && !use_reg)
     return fail(MJP_ERR_UNSUPPORTED, "the register-resident chain needs an FP32 mRNA/protein box without "
                                      "renormalisation that fits 8 CTAs");

@@ -152,10 +152,11 @@ struct RegPlan {
   int rows;      // rows per CTA (a multiple of 2 qr)
   int nq;        // column quads (ceil(M / 4))
   int qr;        // row pairs per thread (4 or 5)
+  int tmax;      // threads per CTA at most: 512 (one CTA per SM) or 256 (two)
   int threads;   // per CTA, including the weights warp
   size_t smem;   // dynamic shared memory per CTA
 };
-bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluster, RegPlan* out);
+bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluster, int threads, RegPlan* out);
 cudaError_t launch_chain_reg2d(const ChainParams& p, const RegPlan& rp, cudaStream_t s);
 cudaError_t launch_fill_weights(const Win* win, int ntimes, const int64_t* woff, double* table, cudaStream_t s);
 cudaError_t launch_permute_in(int precision, const void* src, const int32_t* perm, void* dst, int64_t n,

@@ -38,27 +38,29 @@ namespace mjp {
 namespace {
 
 constexpr int kQC = 4;            // columns per thread block of states
-constexpr int kRegThreads = 512;  // threads per CTA at most (16 warps, <= 128 registers each)
+// Threads per CTA at most, T = 512 (one CTA per SM) or 256 (two CTAs of
+// different instances per SM, so that one computes while the other waits at
+// its barrier); <= 128 registers per thread either way.
 constexpr int kMaxNQ = 512;       // column quads (M <= 2048)
 // Fixed strides of the edge arrays (per parity):
-//  - columns [2 sides][QR][kCStr] float2: the left (side 0) and right (side 1)
-//    column of block t, row pair r; entry kZero is a zero slot;
-//  - rows [2][kRStr] float4: the first (0) and last (1) row of block t (its
+//  - columns [2 sides][QR][T + 1] float2: the left (side 0) and right (side 1)
+//    column of block t, row pair r; entry T (kZero) is a zero slot;
+//  - rows [2][2 T + 1] float4: the first (0) and last (1) row of block t (its
 //    4 columns); entries kZero + 1 + q hold the row just outside the CTA for
 //    column quad q (the next CTA's first row in array 0, the previous CTA's
 //    last row in array 1), written by those CTAs; entry kZero is zero.
 // Every neighbour read goes through a fixed per-thread slot, so threads at
 // the box edge read a zero slot instead of branching.
-constexpr int kZero = kRegThreads;
 // Poisson weights are staged per time in a ring of kStage jumps, filled
 // kChunk jumps at a time, one chunk ahead, by every thread of the CTA.
 constexpr int kChunk = 32;
 constexpr int kStage = 2 * kChunk;
-constexpr int kCStr = kRegThreads + 1;
-constexpr int kRStr = kRegThreads + 1 + kMaxNQ;
 
-template <int QR>
+template <int QR, int T>
 struct EdgeGeo {
+  static constexpr int kZero = T;
+  static constexpr int kCStr = T + 1;
+  static constexpr int kRStr = 2 * T + 1;  // column quads <= blocks <= T
   static constexpr size_t col_bytes = ((size_t)8 * 2 * QR * kCStr + 15) / 16 * 16;
   static constexpr size_t par_bytes = col_bytes + (size_t)16 * 2 * kRStr;
   static constexpr size_t col(int side, int r) { return (size_t)8 * (side * QR + r) * kCStr; }
@@ -133,10 +135,11 @@ __device__ int block_exclusive_scan(int v, int* wsum) {
   return off + x - v;
 }
 
-template <int kQR>
-__global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const ChainParams p, const int NQ,
-                                                                      const int RS) {
-  using G = EdgeGeo<kQR>;
+template <int kQR, int kT>
+__global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainParams p, const int NQ,
+                                                                   const int RS) {
+  using G = EdgeGeo<kQR, kT>;
+  constexpr int kZero = G::kZero;
   constexpr int kRows = 2 * kQR;  // rows of a thread's block
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int wsum[32];
@@ -502,11 +505,15 @@ __global__ void __launch_bounds__(kRegThreads, 1) chain_reg2d_kernel(const Chain
 
 // Cluster size, rows per CTA and threads for an M x P box, or false when the
 // box does not fit this kernel (then the shared-memory kernel runs).
-bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluster, RegPlan* out) {
+bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluster, int threads, RegPlan* out) {
   if (M < 1 || P < 1 || ntimes < 1) return false;
   const int NQ = (int)((M + kQC - 1) / kQC);
   if (NQ > kMaxNQ) return false;
   // Fewest CTAs per instance first; for each, 8 rows per thread before 10.
+  // threads = 256 asks for two CTAs per SM (then the edge arrays are half as
+  // large and a CTA must fit half the shared memory).
+  const int T = threads == 256 ? 256 : 512;
+  const size_t smem_cap = T == 256 ? 113 * 1024 : 227 * 1024;
   for (int C = 1; C <= max_cluster; ++C)
     for (int QR = 4; QR <= 5; ++QR) {
       const int rows_blk = 2 * QR;
@@ -514,14 +521,17 @@ bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluste
       const int RS = (int)((rows + rows_blk - 1) / rows_blk) * rows_blk;
       if ((int64_t)(C - 1) * RS >= P) continue;  // the last CTA would be empty
       const int Tc = NQ * (RS / rows_blk);
-      if (Tc > kRegThreads) continue;
-      const size_t edge = 2 * (QR == 5 ? EdgeGeo<5>::par_bytes : EdgeGeo<4>::par_bytes);
+      if (Tc > T) continue;
+      size_t edge;
+      if (T == 256) edge = 2 * (QR == 5 ? EdgeGeo<5, 256>::par_bytes : EdgeGeo<4, 256>::par_bytes);
+      else edge = 2 * (QR == 5 ? EdgeGeo<5, 512>::par_bytes : EdgeGeo<4, 512>::par_bytes);
       const RegLayout L = reg_layout(edge, ntimes, nmem);
-      if (L.total + 1024 > 227 * 1024) continue;  // leave room for static shared memory
+      if (L.total + 1024 > smem_cap) continue;  // leave room for static shared memory
       out->cluster = C;
       out->rows = RS;
       out->nq = NQ;
       out->qr = QR;
+      out->tmax = T;
       out->threads = ((Tc + 31) / 32) * 32;
       out->smem = L.total;
       return true;
@@ -529,11 +539,11 @@ bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluste
   return false;
 }
 
-template <int QR>
+template <int QR, int T>
 cudaError_t launch_reg(const ChainParams& p, const RegPlan& rp, cudaStream_t s) {
   static int smem_set = 0;
   static bool nonportable = false;
-  auto kern = chain_reg2d_kernel<QR>;
+  auto kern = chain_reg2d_kernel<QR, T>;
   cudaError_t e;
   if ((int)rp.smem > smem_set) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rp.smem);
@@ -562,7 +572,8 @@ cudaError_t launch_reg(const ChainParams& p, const RegPlan& rp, cudaStream_t s) 
 
 cudaError_t launch_chain_reg2d(const ChainParams& p, const RegPlan& rp, cudaStream_t s) {
   if (p.B <= 0) return cudaSuccess;
-  return rp.qr == 5 ? launch_reg<5>(p, rp, s) : launch_reg<4>(p, rp, s);
+  if (rp.tmax == 256) return rp.qr == 5 ? launch_reg<5, 256>(p, rp, s) : launch_reg<4, 256>(p, rp, s);
+  return rp.qr == 5 ? launch_reg<5, 512>(p, rp, s) : launch_reg<4, 512>(p, rp, s);
 }
 
 }  // namespace mjp

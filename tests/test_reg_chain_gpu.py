@@ -31,10 +31,12 @@ def _case(dims, theta, times, cells, seed):
     return obs, synth.delta(n, 0)
 
 
-def _loglik(dims, theta, thetas, times, obs, rho0, chain):
+def _loglik(dims, theta, thetas, times, obs, rho0, chain, threads=0):
     import paper_2312_05647_gb300 as mjp
     m = mjp.Model(synth.MRNA_PROT2D, dims, theta, mjp.FP32)
     m.set_option(mjp.OPT_CHAIN, chain)
+    if threads:
+        m.set_option(mjp.OPT_THREADS, threads)
     o = mjp.Obs(dims[0] * dims[1], times, obs, rho0)
     ll = mjp.loglik(m, o, thetas)
     m.check()
@@ -55,6 +57,17 @@ def test_register_chain_is_bitwise_equal_to_shared_memory_chain(dims, theta):
     a = _loglik(dims, theta, thetas, times, obs, rho0, 1)
     b = _loglik(dims, theta, thetas, times, obs, rho0, 2)
     assert np.all(np.isfinite(a))
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("dims,theta", [((200, 200), (20.0, 1.0, 5.0, 0.1)), ((136, 401), (12.0, 1.0, 2.0, 0.15))])
+def test_register_chain_two_ctas_per_sm_variant_is_bitwise_equal(dims, theta):
+    # OPT_THREADS = 256 selects 256-thread CTAs (two per SM, more CTAs per cluster).
+    times = np.array([0.05, 0.2, 0.6])
+    obs, rho0 = _case(dims, theta, times, 30, seed=sum(dims) + 1)
+    thetas = synth.jitter(theta, 2, 0.2, synth.rng(2, 17))
+    a = _loglik(dims, theta, thetas, times, obs, rho0, 1)
+    b = _loglik(dims, theta, thetas, times, obs, rho0, 2, threads=256)
     np.testing.assert_array_equal(a, b)
 
 
