@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-mcmc", action="store_true", help="skip the ESS/s comparison")
     ap.add_argument("--mcmc-iters", type=int, default=400, help="iterations of each timed sampler run")
     ap.add_argument("--mcmc-adapt-iters", type=int, default=1500, help="iteration cap of each adaptive phase")
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the bench line, measure the other configurations (immigration-death latency, "
+                         "uneven batch, general CSR) and an L2-resident copy; prints one JSON object")
     return ap.parse_args()
 
 
@@ -213,6 +216,95 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def _events_ms(fn, reps: int = 1):
+    """Device time of fn() (CUDA events on the current stream), best of reps."""
+    import torch
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def _bd_K(N, lam, mu, t):
+    """Algorithm 2's K for birth-death instances (birth lam below N-1, death mu n)."""
+    import numpy as np
+    e = np.maximum(lam + mu * np.maximum(N - 2, 0), mu * (N - 1))
+    x = 1.1 * e * t
+    return np.floor(x + 6.0 * np.sqrt(x)).astype(np.int64) + 1
+
+
+def other_configs():
+    """Measurements of the configurations that are not the bench line."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2312_05647_gb300 as mjp
+    res = {}
+    # L2-resident copy (read + write bytes): the denominator for kernels whose
+    # working set fits the L2.
+    a = torch.empty(8 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    a.fill_(1.0)
+    ms = _events_ms(lambda: [b.copy_(a) for _ in range(50)], reps=5)
+    res["l2_copy_gbs"] = {"value": 2 * a.numel() * 4 * 50 / (ms / 1e3) / 1e9,
+                          "how": "torch copy of a 32 MB FP32 tensor, 50 back to back, best of 5 (read+write bytes)"}
+    # Immigration-death N = 64, 5 times, FP64: latency of one expv_series, and
+    # log-likelihoods of 10^4 random thetas.
+    cfg = synth.bd_small()
+    m = mjp.Model(cfg["kind"], cfg["dims"], cfg["theta"], mjp.FP64)
+    r0 = torch.tensor(cfg["rho0"], dtype=torch.float64, device="cuda")
+    out = torch.empty((5, 64), dtype=torch.float64, device="cuda")
+    for _ in range(5):
+        m.expv(r0, cfg["times"], out=out)
+    ms = _events_ms(lambda: [m.expv(r0, cfg["times"], out=out) for _ in range(200)], reps=3)
+    gen = synth.rng(1, 7)
+    th = np.stack([gen.uniform(5, 15, 10000), gen.uniform(0.5, 2.0, 10000)], axis=1)
+    snaps = synth.gillespie_snapshots(cfg["kind"], cfg["dims"], cfg["theta"], cfg["times"], 100, synth.rng(1, 8))
+    ob = mjp.Obs(64, cfg["times"], synth.snapshot_obs(cfg["kind"], cfg["dims"], snaps), cfg["rho0"])
+    thd = torch.tensor(th, dtype=torch.float64, device="cuda")
+    lo = torch.empty(10000, dtype=torch.float64, device="cuda")
+    mjp.loglik(m, ob, thd, out=lo)
+    ms_ll = _events_ms(lambda: mjp.loglik(m, ob, thd, out=lo), reps=3)
+    res["immigration_death_N64"] = {"expv_us_per_call": 1e3 * ms / 200, "loglik_evals_s_10k_thetas": 1e4 / (ms_ll / 1e3),
+                                    "dtype": "f64", "note": "expv: 200 back-to-back calls (planner + chain kernel)"}
+    # Uneven batch of 4096 birth-death instances, autotuned, replayed as a CUDA graph.
+    bc = synth.bd_batch()
+    K = _bd_K(bc["N"], bc["theta"][:, 0], bc["theta"][:, 1], bc["t"])
+    updates = float(np.sum(K * bc["N"]))
+    res["uneven_batch_4096"] = {"state_updates": updates}
+    for prec, name in ((mjp.FP32, "f32"), (mjp.FP64, "f64")):
+        bt = mjp.Batch(bc["N"], bc["theta"], bc["t"], precision=prec)
+        o = bt.empty_out()
+        tuned = bt.tune(o)
+        bt.run(o, use_graph=True)
+        ms = _events_ms(lambda: bt.run(o, use_graph=True), reps=3)
+        res["uneven_batch_4096"][name] = {"ms": ms, "state_updates_per_s": updates / (ms / 1e3), "tuned": tuned}
+    # General CSR, N = 2^20, 8 nonzeros per row, Omega = 220, t = 1 (K = 309).
+    cc = synth.csr_large()
+    n = len(cc["rho0"])
+    nnz = len(cc["col"])
+    res["csr_2p20"] = {}
+    for prec, name, vb in ((mjp.FP32, "f32", 4), (mjp.FP64, "f64", 8)):
+        mc = mjp.Model.from_csr(n, cc["row_ptr"], cc["col"], cc["val"], prec)
+        mc.set_option(mjp.OPT_PROFILE, 1)
+        r = torch.tensor(cc["rho0"], dtype=mc.torch_dtype, device="cuda")
+        o, info = mc.expv(r, cc["times"], info=True)
+        ms = _events_ms(lambda: mc.expv(r, cc["times"], out=o), reps=3)
+        Kc = int(info["K"][0])
+        # Per jump: nnz (value, column index, gathered rho) + n (diagonal, rho
+        # read, rho written); the window's accumulation is counted separately.
+        per_jump = nnz * (vb + 4 + vb) + n * 3 * vb
+        res["csr_2p20"][name] = {"ms": ms, "K": Kc, "bytes_per_jump": per_jump,
+                                 "achieved_gbs": per_jump * Kc / (ms / 1e3) / 1e9}
+    return res
+
+
 MCMC_WORKLOAD = "two_state_promoter_NR300_50times_100cells_256chains"
 
 
@@ -267,6 +359,11 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build() if rank == 0 or world == 1 else None
+    if args.configs:
+        torch.cuda.set_device(local)
+        if rank == 0:
+            print(json.dumps(other_configs()), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
