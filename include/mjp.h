@@ -85,10 +85,17 @@ extern "C" {
 #define MJP_OPT_PROFILE 5       /* 1: record CUDA events around each kernel of a call (see rate_model_last_timing) */
 #define MJP_OPT_ARENA 6         /* capacity (elements) of the planner's Poisson-weight store; 0 = automatic.  Windows
                                    that do not fit are generated in the chain by Algorithm 2's recurrence instead. */
-#define MJP_OPT_CHAIN 7         /* loglik chain kernel for stencil models: 0 = automatic (the register-resident kernel for
-                                   FP32 mRNA/protein boxes without renormalisation, forced cluster or thread counts,
-                                   else the shared-memory kernel), 1 = shared-memory kernel, 2 = register-resident
-                                   kernel (MJP_ERR_UNSUPPORTED where it does not apply) */
+#define MJP_OPT_CHAIN 7         /* chain kernel for stencil models: 0 = automatic (the register-resident kernels for
+                                   the log-likelihood of FP32 mRNA/protein boxes and for expv_series of birth-death
+                                   models, both without renormalisation or forced thread counts (and for the
+                                   former forced cluster sizes), else the shared-memory kernel), 1 = shared-memory
+                                   kernel, 2 = register-resident kernel (MJP_ERR_UNSUPPORTED where it does not
+                                   apply; other models' expv_series always runs the shared-memory kernel).  Also a batch option
+                                   (expv_batch_set_option): 0 = the register-resident birth-death kernel wherever every
+                                   instance fits it (N_j <= 8 x 8,192 states FP32, 8 x 4,096 FP64), 1 = shared-memory
+                                   kernel, 2 = register-resident kernel */
+#define MJP_OPT_HALO 8          /* batches, register-resident kernel: halo width h of an instance split over a cluster,
+                                   i.e. jumps between two halo exchanges (default 32; 1 .. 1024) */
 
 typedef struct mjp_model mjp_model;
 typedef struct mjp_obs mjp_obs;
@@ -234,6 +241,15 @@ int expv_batch_tune(mjp_batch* b, void* out, void* stream, char* cfg, int cfg_le
 
 /* Device-side error check of the last run (synchronises `stream`). */
 int expv_batch_check(mjp_batch* b, void* stream);
+
+/* Batch options: MJP_OPT_CHAIN (0 automatic, 1 shared-memory kernel, 2
+ * register-resident kernel; see beside MJP_OPT_CHAIN), MJP_OPT_CLUSTER (CTAs
+ * per heavy instance, 0 = automatic, else 1 .. 8; instances that need more
+ * CTAs to fit still get them), MJP_OPT_HALO (halo width of the
+ * register-resident kernel's clusters).  Takes effect at the next run or tune
+ * (a captured graph is rebuilt).  Every setting gives the same results up to
+ * the bit (the kernels share their arithmetic).  Errors: MJP_ERR_ARG. */
+int expv_batch_set_option(mjp_batch* b, int option, int64_t value);
 
 void expv_batch_destroy(mjp_batch* b);
 

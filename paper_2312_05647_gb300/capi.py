@@ -21,7 +21,7 @@ BD1D, TWOSTATE, MRNA_PROT2D, CSR = 1, 2, 3, 4
 FP32, FP64 = 1, 2
 TRUNC_PAPER, TRUNC_TOL = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
-OPT_RENORM_PERIOD, OPT_K_CAP, OPT_THREADS, OPT_CLUSTER, OPT_PROFILE, OPT_ARENA, OPT_CHAIN = 1, 2, 3, 4, 5, 6, 7
+OPT_RENORM_PERIOD, OPT_K_CAP, OPT_THREADS, OPT_CLUSTER, OPT_PROFILE, OPT_ARENA, OPT_CHAIN, OPT_HALO = 1, 2, 3, 4, 5, 6, 7, 8
 
 # Every entry point of include/mjp.h: name -> (restype, argtypes).
 _vp = ctypes.c_void_p
@@ -86,6 +86,7 @@ SIGNATURES = {
     "expv_batch_run": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
     "expv_batch_tune": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_char_p, ctypes.c_int]),
     "expv_batch_check": (ctypes.c_int, [_vp, _vp]),
+    "expv_batch_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64]),
     "expv_batch_destroy": (None, [_vp]),
     "expv_series_static": (ctypes.c_int, [ctypes.c_int, _i64p, ctypes.c_int, _f64p, ctypes.c_int, _vp, _f64p,
                                           ctypes.c_int, _vp, _vp]),

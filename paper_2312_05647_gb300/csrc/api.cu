@@ -562,17 +562,29 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
     return MJP_OK;
   }
 
-  int C, T;
-  int64_t slab;
-  int rc = stencil_config(m, 0, nt, 0, 0, &C, &T, &slab);
-  if (rc) return rc;
+  // Birth-death chains: the register-resident kernel (one CTA, or the fewest
+  // CTAs of a cluster that hold the chain, halo 32) unless renormalisation or
+  // a thread count is asked for.
+  Reg1dPlan rp1 = {};
+  bool use_reg1 = false;
+  if (m->kind == MJP_BD1D && m->chain != 1 && m->threads == 0 && !(m->precision == MJP_FP32 && m->renorm > 0)) {
+    const int c0 = m->cluster > 0 ? m->cluster : 1, c1 = m->cluster > 0 ? m->cluster : 8;
+    for (int c = c0; c <= c1 && !use_reg1; ++c) use_reg1 = chain_reg1d_plan(m->precision, m->N, nt, c, 32, &rp1, true);
+  }
+  if (m->chain == 2 && m->kind == MJP_BD1D && !use_reg1)
+    return fail(MJP_ERR_UNSUPPORTED, "the register-resident expv chain needs a birth-death model without "
+                                     "renormalisation or a forced thread count that fits 8 CTAs");
+  int C = 0, T = 0;
+  int64_t slab = 0;
+  int rc = 0;
+  if (!use_reg1 && (rc = stencil_config(m, 0, nt, 0, 0, &C, &T, &slab))) return rc;
   if ((rc = ensure_status(m))) return rc;
   if ((rc = m->d_times.ensure(sizeof(double) * nt))) return rc;
   if ((rc = m->d_orig.ensure(sizeof(int32_t) * nt))) return rc;
   if ((rc = m->d_win.ensure(sizeof(Win) * nt))) return rc;
   if ((rc = m->d_info.ensure(sizeof(JobInfo)))) return rc;
   if ((rc = m->d_theta.ensure(sizeof(double) * m->theta.size()))) return rc;
-  if (m->precision == MJP_FP32 && (rc = m->d_comp.ensure(sizeof(float) * (size_t)nt * m->N))) return rc;
+  if (!use_reg1 && m->precision == MJP_FP32 && (rc = m->d_comp.ensure(sizeof(float) * (size_t)nt * m->N))) return rc;
   MJP_CUDA(cudaMemcpyAsync(m->d_times.p, st.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, s));
   MJP_CUDA(cudaMemcpyAsync(m->d_orig.p, order.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
   MJP_CUDA(cudaMemcpyAsync(m->d_theta.p, m->theta.data(), sizeof(double) * m->theta.size(), cudaMemcpyHostToDevice, s));
@@ -597,7 +609,8 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
   cp.out = out; cp.out_stride = 0; cp.comp = m->d_comp.as<float>(); cp.comp_stride = 0;
   cp.renorm = (m->precision == MJP_FP32) ? m->renorm : 0;
   cp.slab = slab; cp.status = pp.status;
-  MJP_CUDA(launch_chain_stencil(m->kind, m->precision, 0, cp, C, T, s));
+  if (use_reg1) MJP_CUDA(launch_chain_reg1d(m->precision, cp, rp1, s));
+  else MJP_CUDA(launch_chain_stencil(m->kind, m->precision, 0, cp, C, T, s));
   if ((rc = mark(m, 2, s))) return rc;
 
   if (info) {

@@ -7,10 +7,15 @@
 // the hardware block scheduler hands the longest remaining instance to the
 // next free SM (list scheduling, longest processing time first).  Instances
 // whose work alone would exceed a fair share of the makespan ("heavy") are
-// split over a thread-block cluster (DSMEM halos), so the largest instance
-// does not set the makespan; the light ones run one CTA each, grouped by size
-// so each group gets a fitting CTA width.  The groups run concurrently on
-// separate streams; the whole sequence can be captured as one CUDA graph.
+// split over a thread-block cluster, so the largest instance does not set the
+// makespan; the light ones run one CTA each, grouped by size so each group
+// gets a fitting CTA width.  The groups run concurrently on separate streams;
+// the whole sequence can be captured as one CUDA graph.
+//
+// Two chain kernels serve the groups: the register-resident one
+// (stencil_reg1d.cu; clusters exchange halos every h jumps), the default
+// wherever every instance fits it, and the shared-memory one (stencil.cu;
+// clusters exchange boundary values every jump), which takes any size.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -25,13 +30,17 @@ using namespace mjp;
 
 namespace {
 
-constexpr int kGroups = 4;  // heavy + three light size classes
+constexpr int kGroups = 16;        // groups of either kernel at most
+constexpr int kClassicGroups = 4;  // shared-memory kernel: heavy + three light size classes
+constexpr int kMaxRegCluster = 8;  // register kernel: CTAs per instance at most
 constexpr size_t kSmemMax = 227 * 1024;
 
 struct Group {
   std::vector<int32_t> jobs;  // longest first
   int cluster = 1, threads = 128, tile = 0;
   size_t smem = 0;
+  bool reg = false;  // register-resident kernel (plan in rp)
+  Reg1dPlan rp = {};
   DevBuf d_map;
 };
 
@@ -54,6 +63,11 @@ struct mjp_batch {
   int light_threads[3] = {96, 288, 608};
   int heavy_cluster = 8, heavy_threads = 288;
   double heavy_factor = 1.0;
+  // register-resident kernel: 0 = automatic, 1 = shared-memory kernel only,
+  // 2 = register kernel only (MJP_OPT_CHAIN)
+  int chain = 0;
+  int reg_heavy_cluster = 4, reg_halo = 32;
+  double reg_heavy_factor = 1.0;
   int sms = 152;
   Group groups[kGroups];
   bool uploaded = false, grouped = false;
@@ -87,12 +101,15 @@ int tile_of(int64_t N, int cluster) {
   return chain_stencil_tile(MJP_BD1D, N, 1, slab);
 }
 
-// Split the instances into the heavy group and three light size classes.
-int regroup(mjp_batch* b) {
+// Shared-memory kernel: the heavy group and three light size classes.
+int regroup_classic(mjp_batch* b) {
   double total = 0.0;
   for (double w : b->work) total += w;
   const double fair = total / std::max(1, b->sms);
-  for (auto& g : b->groups) g.jobs.clear();
+  for (auto& g : b->groups) {
+    g.jobs.clear();
+    g.reg = false;
+  }
   for (int j = 0; j < b->n; ++j) {
     int C1tile = tile_of(b->N[j], 1);
     size_t smem1 = chain_stencil_smem_tile(b->precision, 0, C1tile, 1, 0, 0);
@@ -100,7 +117,7 @@ int regroup(mjp_batch* b) {
     int gi = heavy ? 0 : (b->N[j] < 1024 ? 1 : (b->N[j] < 4096 ? 2 : 3));
     b->groups[gi].jobs.push_back(j);
   }
-  for (int gi = 0; gi < kGroups; ++gi) {
+  for (int gi = 0; gi < kClassicGroups; ++gi) {
     Group& g = b->groups[gi];
     std::stable_sort(g.jobs.begin(), g.jobs.end(), [&](int32_t a, int32_t c) { return b->work[a] > b->work[c]; });
     g.cluster = gi == 0 ? b->heavy_cluster : 1;
@@ -128,6 +145,74 @@ int regroup(mjp_batch* b) {
     if (!g.jobs.empty())
       MJP_CUDA(cudaMemcpy(g.d_map.p, g.jobs.data(), sizeof(int32_t) * g.jobs.size(), cudaMemcpyHostToDevice));
   }
+  return MJP_OK;
+}
+
+
+// Register kernel: every instance takes the fewest CTAs that hold it (at
+// most kMaxRegCluster), heavy ones at least reg_heavy_cluster; one group per
+// cluster size, and six size classes of single-CTA instances (a CTA is as wide
+// as its group's largest instance needs, so classes keep idle threads few).
+// Returns MJP_ERR_UNSUPPORTED when some instance fits no cluster.
+int regroup_reg(mjp_batch* b) {
+  double total = 0.0;
+  for (double w : b->work) total += w;
+  const double fair = total / std::max(1, b->sms);
+  const int64_t per_cta = chain_reg1d_max_states(b->precision);
+  std::vector<int> gof(b->n);
+  Reg1dPlan rp;
+  for (int j = 0; j < b->n; ++j) {
+    int c = 1;
+    while (c <= kMaxRegCluster && !chain_reg1d_plan(b->precision, b->N[j], 1, c, b->reg_halo, &rp)) ++c;
+    if (c > kMaxRegCluster) return fail(MJP_ERR_UNSUPPORTED, "an instance does not fit the register-resident chain");
+    if (b->work[j] > b->reg_heavy_factor * fair)
+      for (int ch = std::min(b->reg_heavy_cluster, kMaxRegCluster); ch > c; --ch)
+        if (chain_reg1d_plan(b->precision, b->N[j], 1, ch, b->reg_halo, &rp)) {
+          c = ch;
+          break;
+        }
+    // groups 0..5: one CTA, up to 1/16, 1/8, 1/4, 1/2, 3/4 and all of a
+    // CTA's states; group 4 + c: clusters of c CTAs
+    int cls = 5;
+    if (c == 1) {
+      const int64_t n16 = b->N[j] * 16;
+      cls = n16 <= per_cta ? 0 : n16 <= 2 * per_cta ? 1 : n16 <= 4 * per_cta ? 2 : n16 <= 8 * per_cta ? 3
+                                                                                 : n16 <= 12 * per_cta ? 4 : 5;
+    }
+    gof[j] = c > 1 ? 4 + c : cls;
+  }
+  for (auto& g : b->groups) {
+    g.jobs.clear();
+    g.reg = true;
+  }
+  for (int j = 0; j < b->n; ++j) b->groups[gof[j]].jobs.push_back(j);
+  for (int gi = 0; gi < kGroups; ++gi) {
+    Group& g = b->groups[gi];
+    if (g.jobs.empty()) continue;
+    std::stable_sort(g.jobs.begin(), g.jobs.end(), [&](int32_t a, int32_t c) { return b->work[a] > b->work[c]; });
+    int64_t nmax = 0;
+    for (int32_t j : g.jobs) nmax = std::max(nmax, b->N[j]);
+    const int C = gi <= 5 ? 1 : gi - 4;
+    if (!chain_reg1d_plan(b->precision, nmax, 1, C, b->reg_halo, &g.rp))
+      return fail(MJP_ERR_UNSUPPORTED, "a batch group does not fit the register-resident chain");
+    g.cluster = C;
+    g.threads = g.rp.threads;
+    g.smem = g.rp.smem;
+    ChainParams prep = {};  // set kernel attributes now (never inside graph capture)
+    prep.B = 0;
+    MJP_CUDA(launch_chain_reg1d(b->precision, prep, g.rp, nullptr));
+    int rc = g.d_map.ensure(sizeof(int32_t) * g.jobs.size());
+    if (rc) return rc;
+    MJP_CUDA(cudaMemcpy(g.d_map.p, g.jobs.data(), sizeof(int32_t) * g.jobs.size(), cudaMemcpyHostToDevice));
+  }
+  return MJP_OK;
+}
+
+int regroup(mjp_batch* b) {
+  int rc = MJP_ERR_UNSUPPORTED;
+  if (b->chain != 1) rc = regroup_reg(b);
+  if (rc && b->chain != 2) rc = regroup_classic(b);
+  if (rc) return rc;
   b->grouped = true;
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
@@ -195,7 +280,8 @@ int enqueue(mjp_batch* b, void* out, cudaStream_t s) {
     cp.renorm = 0; cp.slab = 1; cp.status = pp.status;
     cp.jobN = pp.jobN; cp.job_off = b->d_off.as<int64_t>(); cp.job_map = g.d_map.as<int32_t>();
     cp.job_s0 = b->d_s0.as<int64_t>(); cp.tile_max = g.tile; cp.arena = b->d_arena.p;
-    MJP_CUDA(launch_chain_stencil(MJP_BD1D, b->precision, 0, cp, g.cluster, g.threads, b->side[gi]));
+    if (g.reg) MJP_CUDA(launch_chain_reg1d(b->precision, cp, g.rp, b->side[gi]));
+    else MJP_CUDA(launch_chain_stencil(MJP_BD1D, b->precision, 0, cp, g.cluster, g.threads, b->side[gi]));
     MJP_CUDA(cudaEventRecord(b->ev_join[gi], b->side[gi]));
     MJP_CUDA(cudaStreamWaitEvent(s, b->ev_join[gi], 0));
   }
@@ -314,33 +400,58 @@ int expv_batch_tune(mjp_batch* b, void* out, void* stream, char* cfg, int cfg_le
   int rc = prepare(b);
   if (rc) return rc;
   struct Cand {
+    int chain;  // 1 shared-memory kernel, 2 register kernel
     int lt[3];
     int hc, ht;
     double hf;
   };
+  const int user_chain = b->chain;
   std::vector<Cand> cands;
-  const int lts[2][3] = {{96, 288, 608}, {64, 160, 416}};
-  for (auto& lt : lts)
-    for (int hc : {4, 8, 16})
-      for (double hf : {0.5, 1.0, 2.0}) cands.push_back({{lt[0], lt[1], lt[2]}, hc, hc >= 8 ? 160 : 288, hf});
+  if (user_chain != 1) {
+    b->chain = 2;
+    if (regroup(b) == MJP_OK)
+      for (int hc : {2, 4, 8})
+        for (double hf : {0.5, 1.0, 2.0}) cands.push_back({2, {0, 0, 0}, hc, 0, hf});
+  }
+  if (user_chain == 1 || (user_chain == 0 && cands.empty())) {
+    const int lts[2][3] = {{96, 288, 608}, {64, 160, 416}};
+    for (auto& lt : lts)
+      for (int hc : {4, 8, 16})
+        for (double hf : {0.5, 1.0, 2.0}) cands.push_back({1, {lt[0], lt[1], lt[2]}, hc, hc >= 8 ? 160 : 288, hf});
+  } else if (user_chain == 0) {
+    cands.push_back({1, {96, 288, 608}, 4, 288, 0.5});  // the shared-memory kernel's usual best, for comparison
+  }
+  if (cands.empty()) {
+    b->chain = user_chain;
+    return fail(MJP_ERR_UNSUPPORTED, "no launch configuration fits this batch");
+  }
+  auto apply = [&](const Cand& c) {
+    b->chain = c.chain;
+    if (c.chain == 2) {
+      b->reg_heavy_cluster = c.hc;
+      b->reg_heavy_factor = c.hf;
+    } else {
+      std::copy(c.lt, c.lt + 3, b->light_threads);
+      b->heavy_cluster = c.hc;
+      b->heavy_threads = c.ht;
+      b->heavy_factor = c.hf;
+    }
+  };
   cudaEvent_t e0, e1;
   MJP_CUDA(cudaEventCreate(&e0));
   MJP_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   Cand bestc = cands[0];
+  rc = MJP_OK;
   for (const Cand& c : cands) {
-    std::copy(c.lt, c.lt + 3, b->light_threads);
-    b->heavy_cluster = c.hc;
-    b->heavy_threads = c.ht;
-    b->heavy_factor = c.hf;
-    if ((rc = regroup(b))) break;
+    apply(c);
+    if (regroup(b) != MJP_OK) continue;
+    cudaEventRecord(e0, s);
     if (enqueue(b, out, s) != MJP_OK) {  // shape not launchable here: skip it
       cudaStreamSynchronize(s);
       cudaGetLastError();
       continue;
     }
-    cudaEventRecord(e0, s);
-    if ((rc = enqueue(b, out, s))) break;
     cudaEventRecord(e1, s);
     if (cudaEventSynchronize(e1) != cudaSuccess) {
       rc = fail(MJP_ERR_CUDA, "tuning run failed");
@@ -355,19 +466,50 @@ int expv_batch_tune(mjp_batch* b, void* out, void* stream, char* cfg, int cfg_le
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  std::copy(bestc.lt, bestc.lt + 3, b->light_threads);
-  b->heavy_cluster = bestc.hc;
-  b->heavy_threads = bestc.ht;
-  b->heavy_factor = bestc.hf;
+  apply(bestc);
   int rc2 = regroup(b);
+  b->chain = user_chain == 0 ? bestc.chain : user_chain;
   if (rc) return rc;
   if (rc2) return rc2;
-  if (cfg && cfg_len > 0)
-    snprintf(cfg, (size_t)cfg_len,
-             "{\"light_threads\": [%d, %d, %d], \"heavy_cluster\": %d, \"heavy_threads\": %d, "
-             "\"heavy_factor\": %.2f, \"ms\": %.4f, \"heavy_jobs\": %zu}",
-             b->light_threads[0], b->light_threads[1], b->light_threads[2], b->heavy_cluster, b->heavy_threads,
-             b->heavy_factor, best, b->groups[0].jobs.size());
+  size_t heavy = 0;
+  for (int gi = 0; gi < kGroups; ++gi)
+    if (b->groups[gi].cluster > 1) heavy += b->groups[gi].jobs.size();
+  if (cfg && cfg_len > 0) {
+    if (bestc.chain == 2)
+      snprintf(cfg, (size_t)cfg_len,
+               "{\"chain\": \"register\", \"heavy_cluster\": %d, \"heavy_factor\": %.2f, \"halo\": %d, "
+               "\"ms\": %.4f, \"cluster_jobs\": %zu}",
+               b->reg_heavy_cluster, b->reg_heavy_factor, b->reg_halo, best, heavy);
+    else
+      snprintf(cfg, (size_t)cfg_len,
+               "{\"chain\": \"shared\", \"light_threads\": [%d, %d, %d], \"heavy_cluster\": %d, "
+               "\"heavy_threads\": %d, \"heavy_factor\": %.2f, \"ms\": %.4f, \"cluster_jobs\": %zu}",
+               b->light_threads[0], b->light_threads[1], b->light_threads[2], b->heavy_cluster, b->heavy_threads,
+               b->heavy_factor, best, heavy);
+  }
+  return MJP_OK;
+}
+
+int expv_batch_set_option(mjp_batch* b, int option, int64_t value) {
+  if (!b) return fail(MJP_ERR_ARG, "NULL batch");
+  switch (option) {
+    case MJP_OPT_CHAIN:
+      if (value < 0 || value > 2) return fail(MJP_ERR_ARG, "chain must be 0, 1 or 2");
+      b->chain = (int)value;
+      break;
+    case MJP_OPT_CLUSTER:
+      if (value < 0 || value > kMaxRegCluster) return fail(MJP_ERR_ARG, "cluster must be in [0, 8]");
+      b->reg_heavy_cluster = value == 0 ? 4 : (int)value;
+      b->heavy_cluster = value == 0 ? 8 : std::max(2, (int)value);
+      break;
+    case MJP_OPT_HALO:
+      if (value < 1 || value > 1024) return fail(MJP_ERR_ARG, "halo must be in [1, 1024]");
+      b->reg_halo = (int)value;
+      break;
+    default:
+      return fail(MJP_ERR_ARG, "option not supported by batches");
+  }
+  b->grouped = false;
   return MJP_OK;
 }
 

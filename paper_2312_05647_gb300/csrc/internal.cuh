@@ -158,6 +158,21 @@ struct RegPlan {
 };
 bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluster, int threads, RegPlan* out);
 cudaError_t launch_chain_reg2d(const ChainParams& p, const RegPlan& rp, cudaStream_t s);
+// Register-resident birth-death chain (stencil_reg1d.cu): expv mode, FP32 or
+// FP64, one CTA or a cluster with temporal blocking per instance.
+struct Reg1dPlan {
+  int cluster;   // CTAs per instance
+  int threads;   // per CTA
+  int qp;        // state pairs per thread
+  int halo;      // halo width h (jumps between cluster exchanges); 0 for one CTA
+  size_t smem;   // dynamic shared memory per CTA
+};
+// small: prefer one state pair per thread when the chain fits a CTA that way
+// (latency of single solves); batches keep the wider runs (throughput).
+bool chain_reg1d_plan(int precision, int64_t Nmax, int ntimes, int cluster, int halo, Reg1dPlan* out,
+                      bool small = false);
+int64_t chain_reg1d_max_states(int precision);
+cudaError_t launch_chain_reg1d(int precision, const ChainParams& p, const Reg1dPlan& rp, cudaStream_t s);
 cudaError_t launch_fill_weights(const Win* win, int ntimes, const int64_t* woff, double* table, cudaStream_t s);
 cudaError_t launch_permute_in(int precision, const void* src, const int32_t* perm, void* dst, int64_t n,
                               cudaStream_t s);

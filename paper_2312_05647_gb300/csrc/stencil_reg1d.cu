@@ -1,0 +1,523 @@
+// stencil_reg1d.cu -- register-resident jump chain for birth-death instances
+// (Eq. BD_def, reflecting top; expv mode, FP32 and FP64): Algorithm 2 with one
+// chain shared by all times of an instance.
+//
+// Layout.  Thread t of a CTA holds R = 2 QP consecutive states of the CTA's
+// segment in registers, as QP pairs: pair j = (state x0 + j, state x0 + QP + j)
+// with x0 = t R.  The stencil neighbours of pair j are then pairs j - 1 and
+// j + 1 component by component, so the update runs on whole pairs (packed
+// FP32x2 instructions) and only the two ends of a thread's run need another
+// thread's value.  Those come through shared memory (the first and last state
+// of every thread, double-buffered by jump parity, with a zero slot at the
+// segment's ends): one CTA barrier per jump.
+//
+// Clusters with temporal blocking.  An instance too large for one CTA's
+// registers, or long enough to set a batch's makespan, runs on a cluster of C
+// CTAs.  CTA r owns states [r S, r S + S) and also carries a halo of h states
+// on each side.  It advances h jumps without hearing from its neighbours: after
+// j jumps only the states within distance j of the halo's outer edge are
+// stale, which never reaches the owned states.  Then the CTAs copy their
+// outermost h owned states into each other's halos through distributed shared
+// memory and meet at one cluster barrier, so the cluster barrier (~550 cycles
+// on GB300) is paid once per h jumps instead of once per jump.
+//
+// Arithmetic per state is the shared-memory kernel's (stencil.cu) operation
+// sequence in the same order, and the weighted accumulation is the same
+// Kahan (FP32) or plain (FP64) sum in jump order, with the same weights, so
+// both kernels give bit-identical outputs for every cluster shape and halo.
+#include <cooperative_groups.h>
+
+#include <type_traits>
+
+#include "chain_common.cuh"
+#include "internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace mjp {
+
+namespace {
+
+constexpr int kChunk1 = 32;           // jumps of weights staged at a time
+constexpr int kStage1 = 2 * kChunk1;  // ring slots per time
+
+struct Reg1dLayout {
+  size_t edge, recv, tx, tPL, ttail, twb, pw, tL, tK, trec, torig, ring, acc_s, acc_c, total;
+};
+
+// Shared memory of one CTA: edges [parity][first, last][threads + 1] (entry
+// `threads` is a zero slot), halo receive buffers [exchange parity][left,
+// right][h], the windows, the weight ring [time][kStage1], the accumulators
+// [time][pair][thread] (pairs of T; FP32 adds the Kahan compensations).
+__host__ __device__ inline Reg1dLayout reg1d_layout(size_t elt, int threads, int qp, int halo, int nt) {
+  Reg1dLayout s;
+  size_t o = 0;
+  s.edge = o; o += align_up(elt * 4 * (size_t)(threads + 1), 16);
+  s.recv = o; o += align_up(elt * 4 * (size_t)(halo > 0 ? halo : 1), 16);
+  s.tx = o; o += 8 * (size_t)nt;
+  s.tPL = o; o += 8 * (size_t)nt;
+  s.ttail = o; o += 8 * (size_t)nt;
+  s.twb = o; o += 8 * (size_t)nt;
+  s.pw = o; o += 16 * (size_t)nt;
+  s.tL = o; o += align_up(4 * (size_t)nt, 8);
+  s.tK = o; o += align_up(4 * (size_t)nt, 8);
+  s.trec = o; o += align_up(4 * (size_t)nt, 8);
+  s.torig = o; o += align_up(4 * (size_t)nt, 8);
+  o = align_up(o, 16);  // pairs of doubles below are 16-byte accesses
+  s.ring = o; o += align_up(elt * kStage1 * (size_t)nt, 16);
+  s.acc_s = o; o += align_up(elt * 2 * (size_t)qp * threads * nt, 16);
+  s.acc_c = o;
+  if (elt == 4) o += align_up(4 * 2 * (size_t)qp * threads * nt, 16);
+  s.total = align_up(o, 16);
+  return s;
+}
+
+// Calls f(O) for N successive register rotations O, O - 1, ... (mod P1).
+template <int P1, int O, int N>
+struct RotSeq {
+  template <class F>
+  __device__ __forceinline__ static void run(F& f) {
+    f(std::integral_constant<int, O>{});
+    RotSeq<P1, (O + P1 - 1) % P1, N - 1>::run(f);
+  }
+};
+template <int P1, int O>
+struct RotSeq<P1, O, 0> {
+  template <class F>
+  __device__ __forceinline__ static void run(F&) {}
+};
+
+template <typename T, int QP, int kMaxT>
+__global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams p, const int halo) {
+  using T2 = typename Pair<T>::type;
+  constexpr int R = 2 * QP;
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int job = p.job_map ? p.job_map[blockIdx.x / C] : (int)(blockIdx.x / C);
+  const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const int nt = p.ntimes;
+  const int N = p.jobN ? p.jobN[job] : (int)p.N;
+  const int S = (N + C - 1) / C;                     // owned states per CTA
+  const int start = rank * S;
+  const int own = max(0, min(N, start + S) - start);
+  // Halo width: at most what the last CTA owns (its first h states fill the
+  // previous CTA's right halo); the host keeps that >= 1.
+  const int h = C > 1 ? max(1, min(halo, N - (C - 1) * S)) : 0;
+  const int xb = start - h;                          // state at segment coordinate 0
+  const int ext = own + 2 * h;                       // segment: halo, owned, halo
+  const int x0 = tid * R;
+  const int64_t out_base = p.job_off ? p.job_off[job] : (int64_t)job * p.out_stride;
+
+  const Reg1dLayout Ly = reg1d_layout(sizeof(T), nthr, QP, h, nt);
+  T* const E = reinterpret_cast<T*>(smem + Ly.edge);     // [2][2][nthr + 1]
+  T* const recv = reinterpret_cast<T*>(smem + Ly.recv);  // [2][2][h]
+  double* t_x = reinterpret_cast<double*>(smem + Ly.tx);
+  double* t_PL = reinterpret_cast<double*>(smem + Ly.tPL);
+  double* t_tail = reinterpret_cast<double*>(smem + Ly.ttail);
+  const T** t_wb = reinterpret_cast<const T**>(smem + Ly.twb);
+  double* pw = reinterpret_cast<double*>(smem + Ly.pw);
+  int* t_L = reinterpret_cast<int*>(smem + Ly.tL);
+  int* t_K = reinterpret_cast<int*>(smem + Ly.tK);
+  int* t_rec = reinterpret_cast<int*>(smem + Ly.trec);
+  int* t_orig = reinterpret_cast<int*>(smem + Ly.torig);
+  T* ring = reinterpret_cast<T*>(smem + Ly.ring);
+  T2* acc_s = reinterpret_cast<T2*>(smem + Ly.acc_s);
+  float2* acc_c = reinterpret_cast<float2*>(smem + Ly.acc_c);
+  const T* arena = reinterpret_cast<const T*>(p.arena);
+  const int ES = nthr + 1;  // edge array stride
+
+  // ---- prologue: windows, coefficients, rho0 --------------------------------
+  const int64_t Kmax64 = p.info[job].Kmax;
+  const Win* wj = p.win + (int64_t)job * nt;
+  for (int i = tid; i < nt; i += nthr) {
+    const Win w = wj[i];
+    t_x[i] = w.x;
+    t_PL[i] = w.PL;
+    t_tail[i] = w.tail;
+    t_L[i] = (int)w.L;
+    t_K[i] = (int)w.K;
+    t_orig[i] = p.orig ? p.orig[i] : i;
+    t_rec[i] = (w.woff < 0 || !arena) ? 1 : 0;
+    t_wb[i] = (w.woff >= 0 && arena) ? arena + (w.woff - w.L) : nullptr;
+    pw[i] = (w.L == 0) ? w.PL : 0.0;
+    if (w.L == 0 && (w.woff < 0 || !arena))  // jump 0 of a window without a stored copy
+      ring[i * kStage1] = (T)(w.PL + (w.K == 0 ? w.tail : 0.0));
+  }
+  if (tid < 4) E[tid * ES + nthr] = (T)0;  // the zero slots
+  const double omega = p.info[job].omega;
+  const Coef<T> co = make_coef<T, MJP_BD1D>(p.theta + (int64_t)job * p.ntheta, omega);
+  const int Kmax = Kmax64 < (1LL << 30) ? (int)Kmax64 : 0;
+  if (Kmax64 >= (1LL << 30) && tid == 0 && rank == 0) set_status(p.status, kStatusKcap);
+
+  // Coefficients of every held state n (rates into n, scaled by 1/Omega): the
+  // diagonal 1 - e_n and the death rate gamma (n+1) from n+1, both zero outside
+  // the segment or the box, and the latter zero at n = N - 1 too (the value
+  // held beyond the box is never zero-padded, so it must not be read).
+  const T one = (T)1;
+  const T* rho0 = reinterpret_cast<const T*>(p.rho0);
+  const int64_t s0 = p.job_s0 ? p.job_s0[job] : -1;
+  // r[QP] is a spare pair: part 1 of the jump chain rotates the pairs
+  // through all QP + 1 slots (below); elsewhere pair j is r[j].
+  T2 r[QP + 1], dg[QP], up[QP];
+  r[QP] = v_make((T)0, (T)0);
+#pragma unroll
+  for (int j = 0; j < QP; ++j) {
+    T dv[2], uv[2], rv[2];
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const int x = x0 + hh * QP + j;
+      const int n = xb + x;
+      const bool in = x < ext && n >= 0 && n < N;
+      const T fm = (T)n;
+      const T e = f_add(f_mul(co.b, fm), n + 1 < N ? co.a : (T)0);
+      dv[hh] = in ? f_sub(one, e) : (T)0;
+      uv[hh] = (in && n + 1 < N) ? f_mul(co.b, f_add(fm, one)) : (T)0;
+      rv[hh] = !in ? (T)0 : (s0 >= 0 ? (T)(n == s0 ? 1 : 0) : rho0[n]);
+    }
+    dg[j] = v_make(dv[0], dv[1]);
+    up[j] = v_make(uv[0], uv[1]);
+    r[j] = v_make(rv[0], rv[1]);
+  }
+  const T2 a2 = v_make(co.a, co.a);
+  // Fixed neighbour slots: the left thread's last state, the right thread's
+  // first state, the zero slot at the segment's ends.
+  const int iL = tid > 0 ? tid - 1 : nthr;
+  const int iR = tid + 1 < nthr ? tid + 1 : nthr;
+  auto publish = [&](int par) {
+    E[(par * 2 + 0) * ES + tid] = r[0].x;
+    E[(par * 2 + 1) * ES + tid] = r[QP - 1].y;
+  };
+  // Halo exchange (clusters): this thread's registers that are sent or received.
+  const bool sendL = C > 1 && rank > 0 && x0 < 2 * h && x0 + R > h;
+  const bool sendR = C > 1 && rank + 1 < C && x0 < own + h && x0 + R > own;
+  const bool recvL = C > 1 && rank > 0 && x0 < h;
+  const bool recvR = C > 1 && rank + 1 < C && x0 < own + 2 * h && x0 + R > own + h;
+  T* rmtL = nullptr;  // the left neighbour's receive buffers (its right halo)
+  T* rmtR = nullptr;  // the right neighbour's (its left halo)
+  if (C > 1) {
+    if (rank > 0) rmtL = cluster.map_shared_rank(recv, rank - 1);
+    if (rank + 1 < C) rmtR = cluster.map_shared_rank(recv, rank + 1);
+  }
+  // recv[ep][side][q]: side 0 = left halo (from rank - 1), 1 = right halo.
+  auto exchange = [&](int ep) {
+    if (sendL || sendR) {
+#pragma unroll
+      for (int j = 0; j < QP; ++j)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int x = x0 + hh * QP + j;
+          const T v = hh ? r[j].y : r[j].x;
+          if (sendL && x >= h && x < 2 * h) rmtL[(ep * 2 + 1) * h + (x - h)] = v;
+          if (sendR && x >= own && x < own + h) rmtR[(ep * 2 + 0) * h + (x - own)] = v;
+        }
+      fence_cluster();
+    }
+    cluster_arrive_relaxed();
+    cluster_wait();
+    if (recvL || recvR) {
+#pragma unroll
+      for (int j = 0; j < QP; ++j) {
+        T v0 = r[j].x, v1 = r[j].y;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int x = x0 + hh * QP + j;
+          T v = hh ? v1 : v0;
+          if (recvL && x < h) v = recv[(ep * 2 + 0) * h + x];
+          if (recvR && x >= own + h && x < own + 2 * h) v = recv[(ep * 2 + 1) * h + (x - own - h)];
+          if (hh) v1 = v;
+          else v0 = v;
+        }
+        r[j] = v_make(v0, v1);
+      }
+    }
+  };
+
+  publish(0);
+  publish(1);  // warps that hold no state never publish again: their slots stay zero
+  // A warp whose threads all lie beyond the segment skips the arithmetic
+  // (it still meets every barrier).
+  const bool wact = (warp * 32) * R < ext;
+  bool mine_rec = false;
+  for (int i = tid; i < nt; i += nthr) mine_rec |= t_rec[i] != 0;
+  // Every CTA of the cluster is running (and its tables are set) before any
+  // distributed-shared-memory write.
+  if (C > 1) cluster.sync();
+  const bool any_rec = __syncthreads_or(mine_rec) != 0;
+
+  int lo = 0, hi = -1;
+  auto advance = [&](int k, int& l, int& hgh) {
+    while (l < nt && t_K[l] < k) ++l;
+    while (hgh + 1 < nt && t_L[hgh + 1] <= k) ++hgh;
+  };
+  advance(0, lo, hi);
+  // Stored weights of jumps [k0, k0 + kChunk1) of every window into the ring
+  // (slot j % kStage1), spread over all threads.
+  auto stage_chunk = [&](int k0) {
+    const int k1 = min(k0 + kChunk1, Kmax + 1);
+    for (int e = tid; e < nt * kChunk1; e += nthr) {
+      const int i = e / kChunk1, j = k0 + (e - i * kChunk1);
+      if (j < k1 && t_wb[i] && j >= t_L[i] && j <= t_K[i])
+        cp_async_elem(ring + i * kStage1 + (j & (kStage1 - 1)), t_wb[i] + j);
+    }
+    cp_async_commit();
+  };
+  // Weights of jump kn for windows without a stored copy (Algorithm 2's
+  // recurrence P_kn = P_{kn-1} x / kn from P_L, tail added at K), one jump
+  // ahead of their use; warp 0.
+  int rlo = lo, rhi = hi;
+  auto rec_step = [&](int kn) {
+    advance(kn, rlo, rhi);
+    const double* rprev = pw + ((kn - 1) & 1) * nt;
+    double* rcur = pw + (kn & 1) * nt;
+    for (int i = rlo + lane; i <= rhi; i += 32) {
+      if (!t_rec[i]) continue;
+      const double Pk = (kn == t_L[i]) ? t_PL[i] : __dmul_rn(rprev[i], __ddiv_rn(t_x[i], (double)kn));
+      rcur[i] = Pk;
+      ring[i * kStage1 + (kn & (kStage1 - 1))] = (T)(Pk + (kn == t_K[i] ? t_tail[i] : 0.0));
+    }
+  };
+
+  // rho*_i += w_{i,k} rho_k for the active times [l, hgh] of jump k (Kahan in
+  // FP32), the result written out at k = K_i for the owned states.
+  auto accumulate = [&](int k, int l, int hgh) {
+    for (int i = l; i <= hgh; ++i) {
+      const T w = ring[i * kStage1 + (k & (kStage1 - 1))];
+      const bool first = k == t_L[i], last = k == t_K[i];
+      T* const o = reinterpret_cast<T*>(p.out) + out_base + (int64_t)t_orig[i] * N + xb;
+#pragma unroll
+      for (int j = 0; j < QP; ++j) {
+        const int slot = (i * QP + j) * nthr + tid;
+        const T2 v = r[j];
+        if (sizeof(T) == 4) {
+          float2 s, cc;
+          if (first) {
+            s = make_float2(__fmul_rn((float)w, (float)v.x), __fmul_rn((float)w, (float)v.y));
+            cc = make_float2(0.0f, 0.0f);
+          } else {
+            const T2 s0v = acc_s[slot];
+            s = make_float2((float)s0v.x, (float)s0v.y);
+            cc = acc_c[slot];
+            const float yx = __fsub_rn(__fmul_rn((float)w, (float)v.x), cc.x);
+            const float yy = __fsub_rn(__fmul_rn((float)w, (float)v.y), cc.y);
+            const float tx = __fadd_rn(s.x, yx), ty = __fadd_rn(s.y, yy);
+            cc = make_float2(__fsub_rn(__fsub_rn(tx, s.x), yx), __fsub_rn(__fsub_rn(ty, s.y), yy));
+            s = make_float2(tx, ty);
+          }
+          if (last) {
+            const int xa = x0 + j, xc = x0 + QP + j;
+            if (xa >= h && xa < h + own) o[xa] = (T)__fsub_rn(s.x, cc.x);
+            if (xc >= h && xc < h + own) o[xc] = (T)__fsub_rn(s.y, cc.y);
+          } else {
+            acc_s[slot] = v_make((T)s.x, (T)s.y);
+            acc_c[slot] = cc;
+          }
+        } else {
+          T2 s;
+          if (first) s = v_make(f_mul(w, v.x), f_mul(w, v.y));
+          else {
+            const T2 s0v = acc_s[slot];
+            s = v_make(f_fma(w, v.x, s0v.x), f_fma(w, v.y, s0v.y));
+          }
+          if (last) {
+            const int xa = x0 + j, xc = x0 + QP + j;
+            if (xa >= h && xa < h + own) o[xa] = s.x;
+            if (xc >= h && xc < h + own) o[xc] = s.y;
+          } else {
+            acc_s[slot] = s;
+          }
+        }
+      }
+    }
+  };
+
+  // One jump of the stencil in place: rho_{k-1} (registers, edges of parity
+  // par) -> rho_k (registers).
+  auto stencil = [&](int par) {
+    const T lin = E[(par * 2 + 1) * ES + iL];  // rho_{k-1} just left of the run
+    const T rin = E[(par * 2 + 0) * ES + iR];  // and just right of it
+    const T first_y = r[0].y;
+    T2 left = v_make(lin, r[QP - 1].x);
+#pragma unroll
+    for (int j = 0; j < QP; ++j) {
+      const T2 cur = r[j];
+      const T2 right = (j + 1 < QP) ? r[j + 1] : v_make(first_y, rin);
+      r[j] = v_fma(up[j], right, v_fma(a2, left, v_mul(dg[j], cur)));
+      left = cur;
+    }
+  };
+  // Halo exchange every h jumps (clusters), except after the last jump.
+  int xleft = h, ep = 0;
+  auto maybe_exchange = [&](int k) {
+    if (h > 0 && --xleft == 0) {
+      xleft = h;
+      ep ^= 1;
+      if (k < Kmax) exchange(ep);
+    }
+  };
+
+  // ---- the jump chain, part 1: jumps before the first window ---------------
+  // No time is active and no weight is needed before the earliest window
+  // start, so these jumps carry no bookkeeping.  They run in groups of
+  // P1 = QP + 1 jumps with the pairs rotating through the QP + 1 register
+  // slots: pair j of rho_{k-1} sits in slot (j + O) % P1 and pair j of rho_k
+  // is written over pair j-1 of rho_{k-1} (its last reader), pair 0 into the
+  // spare slot, so the update needs no register copies; after P1 jumps the
+  // rotation is back to 0.  Clusters exchange halos at group ends, every
+  // P1 floor(h / P1) <= h jumps (part 1 is skipped when h < P1).
+  constexpr int P1 = QP + 1;
+  int minL = Kmax;
+  for (int i = 0; i < nt; ++i) minL = min(minL, t_L[i]);
+  const int xper = h > 0 ? P1 * (h / P1) : 0;  // jumps between exchanges in part 1 (0: never)
+  const int ngroups = (h > 0 && xper == 0) ? 0 : max(0, minL - 1) / P1;
+  int k = 1;
+  int par = 0;
+  auto rot_jump = [&](auto OC) {
+    constexpr int O = decltype(OC)::value;
+    if (wact) {
+      const T lin = E[(par * 2 + 1) * ES + iL];
+      const T rin = E[(par * 2 + 0) * ES + iR];
+      const T first_y = r[O % P1].y;
+      const T2 left0 = v_make(lin, r[(QP - 1 + O) % P1].x);
+#pragma unroll
+      for (int j = 0; j < QP; ++j) {
+        const T2 cur = r[(j + O) % P1];
+        const T2 left = j == 0 ? left0 : r[(j - 1 + O) % P1];
+        const T2 right = (j + 1 < QP) ? r[(j + 1 + O) % P1] : v_make(first_y, rin);
+        const T2 y = v_fma(up[j], right, v_fma(a2, left, v_mul(dg[j], cur)));
+        r[j == 0 ? (O + QP) % P1 : (j - 1 + O) % P1] = y;
+      }
+      constexpr int O2 = (O + QP) % P1;  // rotation of rho_k
+      E[((par ^ 1) * 2 + 0) * ES + tid] = r[O2].x;
+      E[((par ^ 1) * 2 + 1) * ES + tid] = r[(QP - 1 + O2) % P1].y;
+    }
+    __syncthreads();
+    par ^= 1;
+    ++k;
+  };
+  for (int g = 0; g < ngroups; ++g) {
+    RotSeq<P1, 0, P1>::run(rot_jump);
+    if (h > 0 && (xleft -= P1) == h - xper) {  // a halo exchange every xper jumps
+      xleft = h;
+      ep ^= 1;
+      if (k - 1 < Kmax) {
+        exchange(ep);
+        if (wact) publish(par);
+        __syncthreads();
+      }
+    }
+  }
+
+  // ---- part 2: the remaining jumps, with weights and accumulation ---------
+  // Chunk c of the weights (jumps [c kChunk1, (c+1) kChunk1)) is staged at
+  // jump (c-1) kChunk1 + 1, after the last read of the slots it reuses, and
+  // waited for at jump c kChunk1 - 1, before the barrier that precedes its
+  // first read; on entry (after jump kE) the chunks of kE and the next one.
+  const int kE = k - 1;
+  stage_chunk(kChunk1 * (kE / kChunk1));
+  if (kChunk1 * (kE / kChunk1 + 1) <= Kmax) stage_chunk(kChunk1 * (kE / kChunk1 + 1));
+  cp_async_wait<0>();
+  if (warp == 0 && any_rec && kE + 1 <= Kmax) rec_step(kE + 1);
+  __syncthreads();
+  advance(kE, lo, hi);
+  if (wact) accumulate(kE, lo, hi);
+  for (; k <= Kmax; ++k) {
+    const int pk = (k - 1) & 1;
+    if (wact) stencil(pk);
+    maybe_exchange(k);
+    if (wact) publish(pk ^ 1);
+    advance(k, lo, hi);
+    if (wact) accumulate(k, lo, hi);
+    if ((k & (kChunk1 - 1)) == kChunk1 - 1) cp_async_wait<0>();
+    if ((k & (kChunk1 - 1)) == 1 && k - 1 + kChunk1 <= Kmax) stage_chunk(k - 1 + kChunk1);
+    if (warp == 0 && any_rec && k + 1 <= Kmax) rec_step(k + 1);
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+template <typename T, int QP, int kMaxT>
+cudaError_t launch_reg1d_typed(const ChainParams& p, const Reg1dPlan& rp, cudaStream_t s) {
+  static int smem_set = 0;
+  static bool nonportable = false;
+  auto kern = chain_reg1d_kernel<T, QP, kMaxT>;
+  cudaError_t e;
+  if ((int)rp.smem > smem_set) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rp.smem);
+    if (e != cudaSuccess) return e;
+    smem_set = (int)rp.smem;
+  }
+  if (rp.cluster > 8 && !nonportable) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    nonportable = true;
+  }
+  if (p.B <= 0) return cudaSuccess;  // attribute preparation only
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(p.B * rp.cluster));
+  cfg.blockDim = dim3((unsigned)rp.threads);
+  cfg.dynamicSmemBytes = rp.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)rp.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, p, rp.halo);
+}
+
+// States per thread (2 QP) and the largest CTA of each precision: the
+// registers hold 3 pairs (state, diagonal, death coefficient) per pair of
+// states, 48 registers at FP32 QP = 8 and at FP64 QP = 4; with 512 threads a
+// thread may use up to 128 registers, which the kernel fits without spills.
+constexpr int kQP32 = 8, kMaxT32 = 512;
+constexpr int kQP64 = 4, kMaxT64 = 512;
+// One pair per thread spreads a small chain over more warps: the latency of a
+// single solve drops (GB300's FP64 pipe issues a warp's FP64 instruction over
+// many cycles, so a chain held by one warp is limited by one sub-partition).
+constexpr int kQPSmall = 1, kMaxTSmall = 512;
+
+}  // namespace
+
+bool chain_reg1d_plan(int precision, int64_t Nmax, int ntimes, int cluster, int halo, Reg1dPlan* out,
+                      bool small) {
+  if (Nmax < 1 || ntimes < 1 || cluster < 1 || cluster > 16) return false;
+  const bool f64 = precision == MJP_FP64;
+  int qp = f64 ? kQP64 : kQP32, maxt = f64 ? kMaxT64 : kMaxT32;
+  if (small && (Nmax + cluster - 1) / cluster + (cluster > 1 ? 2 * (int64_t)halo : 0) <= 2 * kQPSmall * kMaxTSmall) {
+    qp = kQPSmall;
+    maxt = kMaxTSmall;
+  }
+  const int64_t S = (Nmax + cluster - 1) / cluster;
+  const int h = cluster > 1 ? halo : 0;
+  if (cluster > 1 && (h < 1 || Nmax - (int64_t)(cluster - 1) * S < 1)) return false;
+  const int64_t ext = S + 2 * (int64_t)h;
+  const int64_t thr = (ext + 2 * qp - 1) / (2 * qp);
+  if (thr > maxt) return false;
+  const int threads = (int)((thr + 31) / 32 * 32);
+  const Reg1dLayout L = reg1d_layout(f64 ? 8 : 4, threads, qp, h, ntimes);
+  if (L.total + 1024 > (size_t)227 * 1024) return false;
+  out->cluster = cluster;
+  out->threads = threads;
+  out->qp = qp;
+  out->halo = h;
+  out->smem = L.total;
+  return true;
+}
+
+int64_t chain_reg1d_max_states(int precision) {
+  return precision == MJP_FP64 ? (int64_t)2 * kQP64 * kMaxT64 : (int64_t)2 * kQP32 * kMaxT32;
+}
+
+cudaError_t launch_chain_reg1d(int precision, const ChainParams& p, const Reg1dPlan& rp, cudaStream_t s) {
+  if (rp.qp == kQPSmall)
+    return precision == MJP_FP64 ? launch_reg1d_typed<double, kQPSmall, kMaxTSmall>(p, rp, s)
+                                 : launch_reg1d_typed<float, kQPSmall, kMaxTSmall>(p, rp, s);
+  if (precision == MJP_FP64) return launch_reg1d_typed<double, kQP64, kMaxT64>(p, rp, s);
+  return launch_reg1d_typed<float, kQP32, kMaxT32>(p, rp, s);
+}
+
+}  // namespace mjp
