@@ -27,6 +27,8 @@
 // both kernels give bit-identical outputs for every cluster shape and halo.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include <type_traits>
 
 #include "chain_common.cuh"
@@ -42,17 +44,17 @@ constexpr int kChunk1 = 32;           // jumps of weights staged at a time
 constexpr int kStage1 = 2 * kChunk1;  // ring slots per time
 
 struct Reg1dLayout {
-  size_t edge, recv, tx, tPL, ttail, twb, pw, tL, tK, trec, torig, ring, acc_s, acc_c, total;
+  size_t wh, recv, tx, tPL, ttail, twb, pw, tL, tK, trec, torig, ring, acc_s, acc_c, total;
 };
 
-// Shared memory of one CTA: edges [parity][first, last][threads + 1] (entry
-// `threads` is a zero slot), halo receive buffers [exchange parity][left,
+// Shared memory of one CTA: the warps' halo runs [round parity][left, right]
+// [warp][pair], the cluster halo receive buffers [exchange parity][left,
 // right][h], the windows, the weight ring [time][kStage1], the accumulators
 // [time][pair][thread] (pairs of T; FP32 adds the Kahan compensations).
 __host__ __device__ inline Reg1dLayout reg1d_layout(size_t elt, int threads, int qp, int halo, int nt) {
   Reg1dLayout s;
   size_t o = 0;
-  s.edge = o; o += align_up(elt * 4 * (size_t)(threads + 1), 16);
+  s.wh = o; o += align_up(elt * 2 * 4 * (size_t)(threads / 32) * qp, 16);
   s.recv = o; o += align_up(elt * 4 * (size_t)(halo > 0 ? halo : 1), 16);
   s.tx = o; o += 8 * (size_t)nt;
   s.tPL = o; o += 8 * (size_t)nt;
@@ -70,6 +72,13 @@ __host__ __device__ inline Reg1dLayout reg1d_layout(size_t elt, int threads, int
   if (elt == 4) o += align_up(4 * 2 * (size_t)qp * threads * nt, 16);
   s.total = align_up(o, 16);
   return s;
+}
+
+// Warps of a CTA for a segment of ext states: one window of 64 qp states, or
+// windows that overlap by two lanes' runs (2 x 2 qp states).
+__host__ __device__ inline int reg1d_warps(int ext, int qp) {
+  const int win = 64 * qp, wo = 60 * qp;
+  return ext <= win ? 1 : (ext + wo - 1) / wo;
 }
 
 // Calls f(O) for N successive register rotations O, O - 1, ... (mod P1).
@@ -90,7 +99,10 @@ struct RotSeq<P1, O, 0> {
 template <typename T, int QP, int kMaxT>
 __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams p, const int halo) {
   using T2 = typename Pair<T>::type;
-  constexpr int R = 2 * QP;
+  constexpr int R = 2 * QP;       // states per lane
+  constexpr int P1 = QP + 1;      // register rotation period = jumps per round
+  constexpr int WIN = 32 * R;     // states of a warp's window
+  static_assert(kChunk1 % P1 == 0 && P1 <= R, "rounds must tile the weight chunks and fit a warp halo");
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
@@ -102,16 +114,26 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
   const int S = (N + C - 1) / C;                     // owned states per CTA
   const int start = rank * S;
   const int own = max(0, min(N, start + S) - start);
-  // Halo width: at most what the last CTA owns (its first h states fill the
-  // previous CTA's right halo); the host keeps that >= 1.
-  const int h = C > 1 ? max(1, min(halo, N - (C - 1) * S)) : 0;
+  // CTA halo width: at least one round, at most what the last CTA owns (its
+  // first h states fill the previous CTA's right halo); the host keeps the
+  // last CTA's share >= P1.
+  const int h = C > 1 ? min(max(halo, P1), N - (C - 1) * S) : 0;
   const int xb = start - h;                          // state at segment coordinate 0
   const int ext = own + 2 * h;                       // segment: halo, owned, halo
-  const int x0 = tid * R;
+  // Warps: warp w owns segment coordinates [w Wo, (w+1) Wo) and holds its
+  // window [w Wo - sw, w Wo - sw + WIN), sw = one lane's run when several
+  // warps share the segment; lane l holds window coordinates [l R, l R + R)
+  // as pairs (y0 + j, y0 + QP + j).
+  const int nwu = reg1d_warps(ext, QP);
+  const int sw = nwu > 1 ? R : 0;
+  const int Wo = WIN - 2 * sw;
+  const bool wact = warp < nwu;
+  const int y0 = lane * R;
+  const int xw = warp * Wo - sw;                     // segment coordinate of window coordinate 0
   const int64_t out_base = p.job_off ? p.job_off[job] : (int64_t)job * p.out_stride;
 
   const Reg1dLayout Ly = reg1d_layout(sizeof(T), nthr, QP, h, nt);
-  T* const E = reinterpret_cast<T*>(smem + Ly.edge);     // [2][2][nthr + 1]
+  T2* const wh = reinterpret_cast<T2*>(smem + Ly.wh);    // [2][2][nthr / 32][QP]
   T* const recv = reinterpret_cast<T*>(smem + Ly.recv);  // [2][2][h]
   double* t_x = reinterpret_cast<double*>(smem + Ly.tx);
   double* t_PL = reinterpret_cast<double*>(smem + Ly.tPL);
@@ -126,7 +148,7 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
   T2* acc_s = reinterpret_cast<T2*>(smem + Ly.acc_s);
   float2* acc_c = reinterpret_cast<float2*>(smem + Ly.acc_c);
   const T* arena = reinterpret_cast<const T*>(p.arena);
-  const int ES = nthr + 1;  // edge array stride
+  const int NW = nthr >> 5;
 
   // ---- prologue: windows, coefficients, rho0 --------------------------------
   const int64_t Kmax64 = p.info[job].Kmax;
@@ -145,7 +167,6 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
     if (w.L == 0 && (w.woff < 0 || !arena))  // jump 0 of a window without a stored copy
       ring[i * kStage1] = (T)(w.PL + (w.K == 0 ? w.tail : 0.0));
   }
-  if (tid < 4) E[tid * ES + nthr] = (T)0;  // the zero slots
   const double omega = p.info[job].omega;
   const Coef<T> co = make_coef<T, MJP_BD1D>(p.theta + (int64_t)job * p.ntheta, omega);
   const int Kmax = Kmax64 < (1LL << 30) ? (int)Kmax64 : 0;
@@ -153,13 +174,16 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
 
   // Coefficients of every held state n (rates into n, scaled by 1/Omega): the
   // diagonal 1 - e_n and the death rate gamma (n+1) from n+1, both zero outside
-  // the segment or the box, and the latter zero at n = N - 1 too (the value
-  // held beyond the box is never zero-padded, so it must not be read).
+  // the segment or the box, and the latter zero at n = N - 1 too (what is held
+  // beyond the box is not kept at zero, so it must not be read).  Values
+  // entering a lane's run from outside its warp's window are stale by design
+  // (halo) except at the segment's left end, where the inflow coefficient of
+  // the first state is zero instead (the state left of it is void).
   const T one = (T)1;
   const T* rho0 = reinterpret_cast<const T*>(p.rho0);
   const int64_t s0 = p.job_s0 ? p.job_s0[job] : -1;
-  // r[QP] is a spare pair: part 1 of the jump chain rotates the pairs
-  // through all QP + 1 slots (below); elsewhere pair j is r[j].
+  // r[QP] is a spare pair: the pairs rotate through all QP + 1 slots (below);
+  // at a round's end pair j is back in r[j].
   T2 r[QP + 1], dg[QP], up[QP];
   r[QP] = v_make((T)0, (T)0);
 #pragma unroll
@@ -167,9 +191,9 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
     T dv[2], uv[2], rv[2];
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
-      const int x = x0 + hh * QP + j;
+      const int x = xw + y0 + hh * QP + j;
       const int n = xb + x;
-      const bool in = x < ext && n >= 0 && n < N;
+      const bool in = wact && x >= 0 && x < ext && n >= 0 && n < N;
       const T fm = (T)n;
       const T e = f_add(f_mul(co.b, fm), n + 1 < N ? co.a : (T)0);
       dv[hh] = in ? f_sub(one, e) : (T)0;
@@ -181,51 +205,50 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
     r[j] = v_make(rv[0], rv[1]);
   }
   const T2 a2 = v_make(co.a, co.a);
-  // Fixed neighbour slots: the left thread's last state, the right thread's
-  // first state, the zero slot at the segment's ends.
-  const int iL = tid > 0 ? tid - 1 : nthr;
-  const int iR = tid + 1 < nthr ? tid + 1 : nthr;
-  auto publish = [&](int par) {
-    E[(par * 2 + 0) * ES + tid] = r[0].x;
-    E[(par * 2 + 1) * ES + tid] = r[QP - 1].y;
-  };
-  // Halo exchange (clusters): this thread's registers that are sent or received.
-  const bool sendL = C > 1 && rank > 0 && x0 < 2 * h && x0 + R > h;
-  const bool sendR = C > 1 && rank + 1 < C && x0 < own + h && x0 + R > own;
-  const bool recvL = C > 1 && rank > 0 && x0 < h;
-  const bool recvR = C > 1 && rank + 1 < C && x0 < own + 2 * h && x0 + R > own + h;
-  T* rmtL = nullptr;  // the left neighbour's receive buffers (its right halo)
-  T* rmtR = nullptr;  // the right neighbour's (its left halo)
+  const T2 a2first = v_make(warp == 0 && lane == 0 ? (T)0 : co.a, co.a);  // pair 0's inflow from the left
+
+  // ---- halo exchanges -------------------------------------------------------
+  // Cluster: every CTA copies its outermost h owned states into the
+  // neighbours' halos (distributed shared memory), by the lanes that own
+  // them; recv[ep][side][q], side 0 = left halo (from rank - 1), 1 = right.
+  T* rmtL = nullptr;
+  T* rmtR = nullptr;
   if (C > 1) {
     if (rank > 0) rmtL = cluster.map_shared_rank(recv, rank - 1);
     if (rank + 1 < C) rmtR = cluster.map_shared_rank(recv, rank + 1);
   }
-  // recv[ep][side][q]: side 0 = left halo (from rank - 1), 1 = right halo.
-  auto exchange = [&](int ep) {
-    if (sendL || sendR) {
+  const int xo0 = xw + max(sw, y0), xo1 = xw + min(sw + Wo, y0 + R);  // segment range this lane owns
+  const bool cl_send = C > 1 && wact && xo0 < xo1 &&
+                       ((rank > 0 && xo0 < 2 * h && xo1 > h) || (rank + 1 < C && xo0 < own + h && xo1 > own));
+  const bool cl_recv = C > 1 && wact && xo0 < xo1 &&
+                       ((rank > 0 && xo0 < h) || (rank + 1 < C && xo0 < own + 2 * h && xo1 > own + h));
+  auto owned_y = [&](int y) { return y >= sw && y < sw + Wo; };
+  auto cluster_exchange = [&](int ep) {
+    if (cl_send) {
 #pragma unroll
       for (int j = 0; j < QP; ++j)
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
-          const int x = x0 + hh * QP + j;
+          const int y = y0 + hh * QP + j, x = xw + y;
           const T v = hh ? r[j].y : r[j].x;
-          if (sendL && x >= h && x < 2 * h) rmtL[(ep * 2 + 1) * h + (x - h)] = v;
-          if (sendR && x >= own && x < own + h) rmtR[(ep * 2 + 0) * h + (x - own)] = v;
+          if (!owned_y(y)) continue;
+          if (rmtL && x >= h && x < 2 * h) rmtL[(ep * 2 + 1) * h + (x - h)] = v;
+          if (rmtR && x >= own && x < own + h) rmtR[(ep * 2 + 0) * h + (x - own)] = v;
         }
       fence_cluster();
     }
     cluster_arrive_relaxed();
     cluster_wait();
-    if (recvL || recvR) {
+    if (cl_recv) {
 #pragma unroll
       for (int j = 0; j < QP; ++j) {
         T v0 = r[j].x, v1 = r[j].y;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
-          const int x = x0 + hh * QP + j;
+          const int y = y0 + hh * QP + j, x = xw + y;
           T v = hh ? v1 : v0;
-          if (recvL && x < h) v = recv[(ep * 2 + 0) * h + x];
-          if (recvR && x >= own + h && x < own + 2 * h) v = recv[(ep * 2 + 1) * h + (x - own - h)];
+          if (owned_y(y) && rank > 0 && x < h) v = recv[(ep * 2 + 0) * h + x];
+          if (owned_y(y) && rank + 1 < C && x >= own + h && x < own + 2 * h) v = recv[(ep * 2 + 1) * h + (x - own - h)];
           if (hh) v1 = v;
           else v0 = v;
         }
@@ -233,12 +256,25 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
       }
     }
   };
+  // Warps: lane 1's run (the warp's first owned states) becomes lane 31's
+  // run (right halo) of the warp to the left, lane 30's run becomes lane 0's
+  // run (left halo) of the warp to the right; whole runs, pair by pair,
+  // through shared memory and one CTA barrier.  wh[rp][side][w][j], side 0 =
+  // left halo of warp w.
+  auto warp_exchange = [&](int rp) {
+    if (wact && ((lane == 1 && warp > 0) || (lane == 30 && warp + 1 < nwu))) {
+      T2* dst = wh + ((rp * 2 + (lane == 1 ? 1 : 0)) * NW + (lane == 1 ? warp - 1 : warp + 1)) * QP;
+#pragma unroll
+      for (int j = 0; j < QP; ++j) dst[j] = r[j];
+    }
+    __syncthreads();
+    if (wact && ((lane == 0 && warp > 0) || (lane == 31 && warp + 1 < nwu))) {
+      const T2* src = wh + ((rp * 2 + (lane == 0 ? 0 : 1)) * NW + warp) * QP;
+#pragma unroll
+      for (int j = 0; j < QP; ++j) r[j] = src[j];
+    }
+  };
 
-  publish(0);
-  publish(1);  // warps that hold no state never publish again: their slots stay zero
-  // A warp whose threads all lie beyond the segment skips the arithmetic
-  // (it still meets every barrier).
-  const bool wact = (warp * 32) * R < ext;
   bool mine_rec = false;
   for (int i = tid; i < nt; i += nthr) mine_rec |= t_rec[i] != 0;
   // Every CTA of the cluster is running (and its tables are set) before any
@@ -264,8 +300,7 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
     cp_async_commit();
   };
   // Weights of jump kn for windows without a stored copy (Algorithm 2's
-  // recurrence P_kn = P_{kn-1} x / kn from P_L, tail added at K), one jump
-  // ahead of their use; warp 0.
+  // recurrence P_kn = P_{kn-1} x / kn from P_L, tail added at K); warp 0.
   int rlo = lo, rhi = hi;
   auto rec_step = [&](int kn) {
     advance(kn, rlo, rhi);
@@ -278,18 +313,30 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
       ring[i * kStage1 + (kn & (kStage1 - 1))] = (T)(Pk + (kn == t_K[i] ? t_tail[i] : 0.0));
     }
   };
+  auto rec_round = [&](int k1, int k2) {  // jumps [k1, k2]
+    if (warp == 0 && any_rec)
+      for (int kn = k1; kn <= k2; ++kn) {
+        rec_step(kn);
+        __syncwarp();
+      }
+  };
 
   // rho*_i += w_{i,k} rho_k for the active times [l, hgh] of jump k (Kahan in
-  // FP32), the result written out at k = K_i for the owned states.
-  auto accumulate = [&](int k, int l, int hgh) {
+  // FP32), the result written out at k = K_i for the states this lane owns;
+  // rho_k's pairs at rotation O.
+  auto accumulate = [&](int k, int l, int hgh, auto OC) {
+    constexpr int O = decltype(OC)::value;
     for (int i = l; i <= hgh; ++i) {
       const T w = ring[i * kStage1 + (k & (kStage1 - 1))];
       const bool first = k == t_L[i], last = k == t_K[i];
-      T* const o = reinterpret_cast<T*>(p.out) + out_base + (int64_t)t_orig[i] * N + xb;
+      T* const o = reinterpret_cast<T*>(p.out) + out_base + (int64_t)t_orig[i] * N + xb + xw;
 #pragma unroll
       for (int j = 0; j < QP; ++j) {
         const int slot = (i * QP + j) * nthr + tid;
-        const T2 v = r[j];
+        const T2 v = r[(j + O) % P1];
+        const int ya = y0 + j, yc = y0 + QP + j;
+        const bool oa = owned_y(ya) && xw + ya >= h && xw + ya < h + own;
+        const bool oc = owned_y(yc) && xw + yc >= h && xw + yc < h + own;
         if (sizeof(T) == 4) {
           float2 s, cc;
           if (first) {
@@ -306,9 +353,8 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
             s = make_float2(tx, ty);
           }
           if (last) {
-            const int xa = x0 + j, xc = x0 + QP + j;
-            if (xa >= h && xa < h + own) o[xa] = (T)__fsub_rn(s.x, cc.x);
-            if (xc >= h && xc < h + own) o[xc] = (T)__fsub_rn(s.y, cc.y);
+            if (oa) o[ya] = (T)__fsub_rn(s.x, cc.x);
+            if (oc) o[yc] = (T)__fsub_rn(s.y, cc.y);
           } else {
             acc_s[slot] = v_make((T)s.x, (T)s.y);
             acc_c[slot] = cc;
@@ -321,9 +367,8 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
             s = v_make(f_fma(w, v.x, s0v.x), f_fma(w, v.y, s0v.y));
           }
           if (last) {
-            const int xa = x0 + j, xc = x0 + QP + j;
-            if (xa >= h && xa < h + own) o[xa] = s.x;
-            if (xc >= h && xc < h + own) o[xc] = s.y;
+            if (oa) o[ya] = s.x;
+            if (oc) o[yc] = s.y;
           } else {
             acc_s[slot] = s;
           }
@@ -332,107 +377,96 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
     }
   };
 
-  // One jump of the stencil in place: rho_{k-1} (registers, edges of parity
-  // par) -> rho_k (registers).
-  auto stencil = [&](int par) {
-    const T lin = E[(par * 2 + 1) * ES + iL];  // rho_{k-1} just left of the run
-    const T rin = E[(par * 2 + 0) * ES + iR];  // and just right of it
-    const T first_y = r[0].y;
-    T2 left = v_make(lin, r[QP - 1].x);
+  // One jump in place: rho_{k-1} -> rho_k with the pairs at rotation O (pair
+  // j in slot (j + O) % P1); pair j of rho_k is written over pair j-1 of
+  // rho_{k-1} (its last reader) and pair 0 into the free slot, so the new
+  // rotation is O - 1 (mod P1) and no register is copied.  The values just
+  // outside the lane's run come from the neighbour lanes (shuffles); at the
+  // window's ends they are the lane's own values, which only halo states or
+  // zero coefficients see.
+  int k = 1;
+  auto jump = [&](auto OC) {
+    constexpr int O = decltype(OC)::value;
+    const T lin = __shfl_up_sync(kFull, r[(QP - 1 + O) % P1].y, 1);
+    const T rin = __shfl_down_sync(kFull, r[O % P1].x, 1);
+    const T first_y = r[O % P1].y;
+    const T2 left0 = v_make(lin, r[(QP - 1 + O) % P1].x);
 #pragma unroll
     for (int j = 0; j < QP; ++j) {
-      const T2 cur = r[j];
-      const T2 right = (j + 1 < QP) ? r[j + 1] : v_make(first_y, rin);
-      r[j] = v_fma(up[j], right, v_fma(a2, left, v_mul(dg[j], cur)));
-      left = cur;
+      const T2 cur = r[(j + O) % P1];
+      const T2 left = j == 0 ? left0 : r[(j - 1 + O) % P1];
+      const T2 right = (j + 1 < QP) ? r[(j + 1 + O) % P1] : v_make(first_y, rin);
+      r[j == 0 ? (O + QP) % P1 : (j - 1 + O) % P1] =
+          v_fma(up[j], right, v_fma(j == 0 ? a2first : a2, left, v_mul(dg[j], cur)));
     }
   };
-  // Halo exchange every h jumps (clusters), except after the last jump.
-  int xleft = h, ep = 0;
-  auto maybe_exchange = [&](int k) {
-    if (h > 0 && --xleft == 0) {
-      xleft = h;
-      ep ^= 1;
-      if (k < Kmax) exchange(ep);
-    }
-  };
-
-  // ---- the jump chain, part 1: jumps before the first window ---------------
-  // No time is active and no weight is needed before the earliest window
-  // start, so these jumps carry no bookkeeping.  They run in groups of
-  // P1 = QP + 1 jumps with the pairs rotating through the QP + 1 register
-  // slots: pair j of rho_{k-1} sits in slot (j + O) % P1 and pair j of rho_k
-  // is written over pair j-1 of rho_{k-1} (its last reader), pair 0 into the
-  // spare slot, so the update needs no register copies; after P1 jumps the
-  // rotation is back to 0.  Clusters exchange halos at group ends, every
-  // P1 floor(h / P1) <= h jumps (part 1 is skipped when h < P1).
-  constexpr int P1 = QP + 1;
-  int minL = Kmax;
-  for (int i = 0; i < nt; ++i) minL = min(minL, t_L[i]);
-  const int xper = h > 0 ? P1 * (h / P1) : 0;  // jumps between exchanges in part 1 (0: never)
-  const int ngroups = (h > 0 && xper == 0) ? 0 : max(0, minL - 1) / P1;
-  int k = 1;
-  int par = 0;
-  auto rot_jump = [&](auto OC) {
-    constexpr int O = decltype(OC)::value;
-    if (wact) {
-      const T lin = E[(par * 2 + 1) * ES + iL];
-      const T rin = E[(par * 2 + 0) * ES + iR];
-      const T first_y = r[O % P1].y;
-      const T2 left0 = v_make(lin, r[(QP - 1 + O) % P1].x);
-#pragma unroll
-      for (int j = 0; j < QP; ++j) {
-        const T2 cur = r[(j + O) % P1];
-        const T2 left = j == 0 ? left0 : r[(j - 1 + O) % P1];
-        const T2 right = (j + 1 < QP) ? r[(j + 1 + O) % P1] : v_make(first_y, rin);
-        const T2 y = v_fma(up[j], right, v_fma(a2, left, v_mul(dg[j], cur)));
-        r[j == 0 ? (O + QP) % P1 : (j - 1 + O) % P1] = y;
-      }
-      constexpr int O2 = (O + QP) % P1;  // rotation of rho_k
-      E[((par ^ 1) * 2 + 0) * ES + tid] = r[O2].x;
-      E[((par ^ 1) * 2 + 1) * ES + tid] = r[(QP - 1 + O2) % P1].y;
-    }
-    __syncthreads();
-    par ^= 1;
+  auto jump_plain = [&](auto OC) {
+    jump(OC);
     ++k;
   };
-  for (int g = 0; g < ngroups; ++g) {
-    RotSeq<P1, 0, P1>::run(rot_jump);
-    if (h > 0 && (xleft -= P1) == h - xper) {  // a halo exchange every xper jumps
-      xleft = h;
-      ep ^= 1;
-      if (k - 1 < Kmax) {
-        exchange(ep);
-        if (wact) publish(par);
-        __syncthreads();
-      }
+  // With weights and accumulation; the round may end early at Kmax.
+  auto jump_acc = [&](auto OC) {
+    constexpr int O = decltype(OC)::value;
+    if (k > Kmax) return;
+    if (wact) jump(OC);
+    advance(k, lo, hi);
+    if (wact) accumulate(k, lo, hi, std::integral_constant<int, (O + QP) % P1>{});
+    ++k;
+  };
+
+  // ---- the jump chain -------------------------------------------------------
+  // Warps run rounds of P1 jumps without meeting: a warp window's halo (one
+  // lane's run, R >= P1 states) goes stale from its outer edge at one state
+  // per jump; at a round's end the pairs are back home, the warps refresh
+  // each other's halos (one CTA barrier) and, at most every h jumps, the CTAs
+  // refresh theirs.
+  int since = 0;  // jumps since the last cluster exchange
+  int cep = 0, wrp = 0;
+  auto round_end = [&](int k_e) {
+    since += P1;
+    if (C > 1 && since + P1 > h) {
+      cep ^= 1;
+      if (k_e < Kmax) cluster_exchange(cep);
+      since = 0;
     }
+    if (nwu > 1) {
+      wrp ^= 1;
+      warp_exchange(wrp);
+    }
+  };
+
+  // Part 1: jumps before the earliest window start carry no bookkeeping.
+  int minL = Kmax;
+  for (int i = 0; i < nt; ++i) minL = min(minL, t_L[i]);
+  const int ngroups = max(0, minL - 1) / P1;
+  const int kE = ngroups * P1;  // last jump of part 1
+  for (int g = 0; g < ngroups; ++g) {
+    if (wact) RotSeq<P1, 0, P1>::run(jump_plain);
+    else k += P1;
+    round_end(k - 1);
   }
 
-  // ---- part 2: the remaining jumps, with weights and accumulation ---------
-  // Chunk c of the weights (jumps [c kChunk1, (c+1) kChunk1)) is staged at
-  // jump (c-1) kChunk1 + 1, after the last read of the slots it reuses, and
-  // waited for at jump c kChunk1 - 1, before the barrier that precedes its
-  // first read; on entry (after jump kE) the chunks of kE and the next one.
-  const int kE = k - 1;
+  // Part 2: the same rounds with weights and accumulation.  Chunk c of the
+  // weights (jumps [c kChunk1, (c+1) kChunk1)) is staged after the barrier
+  // at jump (c-1) kChunk1 (no later round reads the slots it reuses) and
+  // waited for before the barrier that precedes the round holding jump
+  // c kChunk1; on entry (after jump kE) the chunks of kE and the next one.
   stage_chunk(kChunk1 * (kE / kChunk1));
   if (kChunk1 * (kE / kChunk1 + 1) <= Kmax) stage_chunk(kChunk1 * (kE / kChunk1 + 1));
   cp_async_wait<0>();
-  if (warp == 0 && any_rec && kE + 1 <= Kmax) rec_step(kE + 1);
+  rec_round(kE + 1, min(Kmax, kE + P1));
   __syncthreads();
   advance(kE, lo, hi);
-  if (wact) accumulate(kE, lo, hi);
-  for (; k <= Kmax; ++k) {
-    const int pk = (k - 1) & 1;
-    if (wact) stencil(pk);
-    maybe_exchange(k);
-    if (wact) publish(pk ^ 1);
-    advance(k, lo, hi);
-    if (wact) accumulate(k, lo, hi);
-    if ((k & (kChunk1 - 1)) == kChunk1 - 1) cp_async_wait<0>();
-    if ((k & (kChunk1 - 1)) == 1 && k - 1 + kChunk1 <= Kmax) stage_chunk(k - 1 + kChunk1);
-    if (warp == 0 && any_rec && k + 1 <= Kmax) rec_step(k + 1);
-    __syncthreads();
+  if (wact) accumulate(kE, lo, hi, std::integral_constant<int, 0>{});
+  while (k <= Kmax) {
+    RotSeq<P1, 0, P1>::run(jump_acc);
+    const int k_e = k - 1;
+    if (k_e >= Kmax) break;
+    if ((k_e + P1) % kChunk1 == 0) cp_async_wait<0>();
+    rec_round(k_e + 1, min(Kmax, k_e + P1));
+    round_end(k_e);
+    if (nwu <= 1) __syncthreads();
+    if (k_e % kChunk1 == 0 && k_e + kChunk1 <= Kmax) stage_chunk(k_e + kChunk1);
   }
   cp_async_wait<0>();
 }
@@ -473,8 +507,8 @@ cudaError_t launch_reg1d_typed(const ChainParams& p, const Reg1dPlan& rp, cudaSt
 // registers hold 3 pairs (state, diagonal, death coefficient) per pair of
 // states, 48 registers at FP32 QP = 8 and at FP64 QP = 4; with 512 threads a
 // thread may use up to 128 registers, which the kernel fits without spills.
-constexpr int kQP32 = 8, kMaxT32 = 512;
-constexpr int kQP64 = 4, kMaxT64 = 512;
+constexpr int kQP32 = 7, kMaxT32 = 512;
+constexpr int kQP64 = 3, kMaxT64 = 512;
 // One pair per thread spreads a small chain over more warps: the latency of a
 // single solve drops (GB300's FP64 pipe issues a warp's FP64 instruction over
 // many cycles, so a chain held by one warp is limited by one sub-partition).
@@ -487,17 +521,19 @@ bool chain_reg1d_plan(int precision, int64_t Nmax, int ntimes, int cluster, int 
   if (Nmax < 1 || ntimes < 1 || cluster < 1 || cluster > 16) return false;
   const bool f64 = precision == MJP_FP64;
   int qp = f64 ? kQP64 : kQP32, maxt = f64 ? kMaxT64 : kMaxT32;
-  if (small && (Nmax + cluster - 1) / cluster + (cluster > 1 ? 2 * (int64_t)halo : 0) <= 2 * kQPSmall * kMaxTSmall) {
+  const int64_t S = (Nmax + cluster - 1) / cluster;
+  if (S + 2 * (int64_t)halo + 64 > (int64_t)1 << 24) return false;
+  if (small && 32 * reg1d_warps((int)(S + (cluster > 1 ? 2 * std::max(halo, kQPSmall + 1) : 0)), kQPSmall) <= kMaxTSmall) {
     qp = kQPSmall;
     maxt = kMaxTSmall;
   }
-  const int64_t S = (Nmax + cluster - 1) / cluster;
-  const int h = cluster > 1 ? halo : 0;
-  if (cluster > 1 && (h < 1 || Nmax - (int64_t)(cluster - 1) * S < 1)) return false;
+  // The halo covers at least one round (qp + 1 jumps) and the last CTA owns
+  // at least that many states.
+  const int h = cluster > 1 ? std::max(halo, qp + 1) : 0;
+  if (cluster > 1 && Nmax - (int64_t)(cluster - 1) * S < qp + 1) return false;
   const int64_t ext = S + 2 * (int64_t)h;
-  const int64_t thr = (ext + 2 * qp - 1) / (2 * qp);
-  if (thr > maxt) return false;
-  const int threads = (int)((thr + 31) / 32 * 32);
+  const int threads = 32 * reg1d_warps((int)ext, qp);
+  if (threads > maxt) return false;
   const Reg1dLayout L = reg1d_layout(f64 ? 8 : 4, threads, qp, h, ntimes);
   if (L.total + 1024 > (size_t)227 * 1024) return false;
   out->cluster = cluster;
@@ -509,7 +545,8 @@ bool chain_reg1d_plan(int precision, int64_t Nmax, int ntimes, int cluster, int 
 }
 
 int64_t chain_reg1d_max_states(int precision) {
-  return precision == MJP_FP64 ? (int64_t)2 * kQP64 * kMaxT64 : (int64_t)2 * kQP32 * kMaxT32;
+  const int qp = precision == MJP_FP64 ? kQP64 : kQP32, maxt = precision == MJP_FP64 ? kMaxT64 : kMaxT32;
+  return (int64_t)(maxt / 32) * (60 * qp);  // warp windows overlap by two lanes' runs
 }
 
 cudaError_t launch_chain_reg1d(int precision, const ChainParams& p, const Reg1dPlan& rp, cudaStream_t s) {
