@@ -92,7 +92,7 @@ extern "C" {
                                    kernel, 2 = register-resident kernel (MJP_ERR_UNSUPPORTED where it does not
                                    apply; other models' expv_series always runs the shared-memory kernel).  Also a batch option
                                    (expv_batch_set_option): 0 = the register-resident birth-death kernel wherever every
-                                   instance fits it (N_j <= 8 x 8,192 states FP32, 8 x 4,096 FP64), 1 = shared-memory
+                                   instance fits it (N_j <= 8 x 6,720 states FP32, 8 x 3,360 FP64), 1 = shared-memory
                                    kernel, 2 = register-resident kernel */
 #define MJP_OPT_HALO 8          /* batches, register-resident kernel: halo width h of an instance split over a cluster,
                                    i.e. jumps between two halo exchanges (default 32; 1 .. 1024) */

@@ -503,12 +503,13 @@ cudaError_t launch_reg1d_typed(const ChainParams& p, const Reg1dPlan& rp, cudaSt
   return cudaLaunchKernelEx(&cfg, kern, p, rp.halo);
 }
 
-// States per thread (2 QP) and the largest CTA of each precision: the
-// registers hold 3 pairs (state, diagonal, death coefficient) per pair of
-// states, 48 registers at FP32 QP = 8 and at FP64 QP = 4; with 512 threads a
-// thread may use up to 128 registers, which the kernel fits without spills.
+// State pairs per lane (QP, QP + 1 = 8 jumps per round) and the largest CTA
+// of each precision: the registers hold 3 pairs (state, diagonal, death
+// coefficient) per pair of states, 42 registers at FP32 and 84 at FP64; 512
+// threads leave 128 registers per thread (FP32), 256 threads 255 (FP64,
+// whose slow FP64 pipe needs few warps but many independent operations).
 constexpr int kQP32 = 7, kMaxT32 = 512;
-constexpr int kQP64 = 3, kMaxT64 = 512;
+constexpr int kQP64 = 7, kMaxT64 = 256;
 // One pair per thread spreads a small chain over more warps: the latency of a
 // single solve drops (GB300's FP64 pipe issues a warp's FP64 instruction over
 // many cycles, so a chain held by one warp is limited by one sub-partition).

@@ -59,8 +59,9 @@ def _oracle_bd(N, th, t, s0):
 def test_batch_bitwise_over_clusters_and_halos(prec):
     N, th, t, s0 = _small_batch(96, 11)
     ref, _ = _run_batch(N, th, t, s0, prec, chain=1)
-    # Cluster 8 with 96 instances splits even 50-state instances into 8 CTAs
-    # (the last owning a single state, halo clamped to 1).
+    # Forced clusters split instances as far as the last CTA still owns one
+    # round of states (down to a few dozen states per CTA); halos below one
+    # round are raised to it.
     for cluster, halo in [(0, 0), (2, 1), (3, 7), (8, 32), (5, 100)]:
         got, _ = _run_batch(N, th, t, s0, prec, chain=2, cluster=cluster, halo=halo)
         np.testing.assert_array_equal(got, ref, err_msg=f"cluster {cluster} halo {halo}")
@@ -73,7 +74,7 @@ def test_batch_bitwise_over_clusters_and_halos(prec):
 
 @pytest.mark.parametrize("prec", [1, 2])
 def test_batch_instances_that_need_a_cluster(prec):
-    # FP32 CTAs hold 8,192 states, FP64 CTAs 4,096: these need 2..5 CTAs each.
+    # FP32 CTAs hold 6,720 states, FP64 CTAs 3,360: these need up to 3 and 6 CTAs.
     N = np.array([20000, 12000, 9000, 8193, 4097, 300], dtype=np.int64)
     th = np.stack([N / 5.0, np.full(len(N), 1.0)], 1)
     t = np.array([0.02, 0.03, 0.01, 0.02, 0.05, 0.5])
