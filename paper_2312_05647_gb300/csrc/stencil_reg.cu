@@ -92,20 +92,26 @@ __host__ __device__ inline RegLayout reg_layout(size_t edge_bytes, int nt, int n
   return s;
 }
 
-// Register value of slot (row pair r, column c, half h) = ((r * 4 + c) * 2 + h)
-// with a runtime slot, by a tree of selections (no local-memory array): the
-// half, the two column bits, then the row pair.
-template <int QR>
-__device__ __forceinline__ float pick(const float2 (&S)[QR][kQC], int slot) {
-  const bool h = slot & 1, c0 = slot & 2, c1 = slot & 4;
-  const int r = slot >> 3;
+// Register slot of row r of a block at rotation ROT: 0 = home (row r in slot
+// r), 1 = shifted (row r in slot r - 1, row 0 in the spare slot NR).
+template <int NR>
+__host__ __device__ constexpr int rslot(int r, int rot) {
+  return rot == 0 ? r : (r == 0 ? NR : r - 1);
+}
+
+// Register value of observation slot r * 4 + c (row r, column c; columns
+// c0, c2 in pair 0 and c1, c3 in pair 1 of the row) at rotation ROT, by a tree
+// of selections (no local-memory array).
+template <int NR, int ROT>
+__device__ __forceinline__ float pick(const float2 (&S)[NR + 1][2], int slot) {
+  const bool c1 = slot & 1, c2 = slot & 2;
+  const int r = slot >> 2;
   float v = 0.0f;
 #pragma unroll
-  for (int q = 0; q < QR; ++q) {
-    const float x0 = h ? S[q][0].y : S[q][0].x, x1 = h ? S[q][1].y : S[q][1].x;
-    const float x2 = h ? S[q][2].y : S[q][2].x, x3 = h ? S[q][3].y : S[q][3].x;
-    const float lo = c0 ? x1 : x0, hi = c0 ? x3 : x2;
-    v = (r == q) ? (c1 ? hi : lo) : v;
+  for (int q = 0; q < NR; ++q) {
+    const float2 a = S[rslot<NR>(q, ROT)][0], b = S[rslot<NR>(q, ROT)][1];
+    const float x = c2 ? (c1 ? b.y : a.y) : (c1 ? b.x : a.x);
+    v = (r == q) ? x : v;
   }
   return v;
 }
@@ -205,8 +211,7 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   auto owns = [&](int s, int& slot) -> bool {
     const int ps = s / M, ms = s - ps * M;
     if (!owner || ps < pb || ps >= pb + kRows || ms < m0 || ms >= m0 + kQC) return false;
-    const int pr = ps - pb;
-    slot = (((pr >> 1) * kQC) + (ms - m0)) * 2 + (pr & 1);
+    slot = (ps - pb) * kQC + (ms - m0);
     return true;
   };
   auto scan_members = [&](bool fill, int base) -> int {
@@ -241,26 +246,28 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   else __syncthreads();
 
   // Column coefficients (rates into column m, scaled by 1/Omega): gamma_m
-  // (m+1) from m+1, k_p m from p-1, and 1 - e without the gamma_p p part;
-  // the first and the last as pairs (both rows of a row pair).
+  // (m+1) from m+1, k_p m from p-1, and 1 - e without the gamma_p p part, as
+  // pairs of the columns (c0, c2) and (c1, c3) that share a register pair.
   const float one = 1.0f;
-  float2 crp[kQC], d0p[kQC];
-  float cdv[kQC];
+  float crc[kQC], cdc[kQC], d0c[kQC];
   int colmask = 0;  // bit c: column m0 + c lies in the box
 #pragma unroll
   for (int c = 0; c < kQC; ++c) {
     const int m = m0 + c;
     if (m < M) colmask |= 1 << c;
     const float fm = (float)m;
-    const float cr = f_mul(co.b, (float)(m + 1));
-    cdv[c] = f_mul(co.c, fm);
-    const float d0 = f_sub(one, f_add(f_add(f_mul(co.b, fm), m + 1 < M ? co.a : 0.0f), cdv[c]));
-    crp[c] = v_make(cr, cr);
-    d0p[c] = v_make(d0, d0);
+    crc[c] = f_mul(co.b, (float)(m + 1));
+    cdc[c] = f_mul(co.c, fm);
+    d0c[c] = f_sub(one, f_add(f_add(f_mul(co.b, fm), m + 1 < M ? co.a : 0.0f), cdc[c]));
   }
-  const float2 c_l = v_make(co.a, co.a), c_gp = v_make(co.d, co.d), c_ngp = v_make(-co.d, -co.d);
-  // Row pair of this block that holds row P-1 (-1 if none).
-  const int rtop = (P - 1 >= pb && P - 1 < pb + kRows) ? (P - 1 - pb) / 2 : -1;
+  const float2 d0A = v_make(d0c[0], d0c[2]), d0B = v_make(d0c[1], d0c[3]);
+  const float2 crA = v_make(crc[0], crc[2]), crB = v_make(crc[1], crc[3]);
+  const float2 cdA = v_make(cdc[0], cdc[2]), cdB = v_make(cdc[1], cdc[3]);
+  const float c_l = co.a;
+  const float2 c_l2 = v_make(co.a, co.a), c_gp = v_make(co.d, co.d), c_ngp = v_make(-co.d, -co.d);
+  const bool padcols = colmask != (1 << kQC) - 1;
+  // Row of this block that holds row P-1 (-1 if none).
+  const int rtop = (P - 1 >= pb && P - 1 < pb + kRows) ? P - 1 - pb : -1;
 
   // Fixed neighbour slots: left block's right column, right block's left
   // column, the row below (a last row) and the row above (a first row).
@@ -271,21 +278,26 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   const unsigned oL = 8u * iL, oR = 8u * iR, oB = 16u * iB, oA = 16u * iA, oT8 = 8u * tid, oT16 = 16u * tid;
   unsigned char* const E0 = smem + L.edge;
 
-  // rho0 into registers, its edges into parity 0.
-  float2 S[kQR][kQC];
+  // rho0 into registers, its edges into parity 0.  Row r of the block is
+  // S[r][0] = (c0, c2), S[r][1] = (c1, c3); S[kRows] is a spare row: a jump
+  // writes row r's new values over row r-1's old ones (ascending) or row r+1's
+  // (descending), so the rows shift by one slot and back every two jumps and
+  // no register is copied.
+  constexpr int NR = kRows;
+  float2 S[NR + 1][2];
   const float* rho0 = reinterpret_cast<const float*>(p.rho0);
 #pragma unroll
-  for (int r = 0; r < kQR; ++r)
+  for (int r = 0; r < NR; ++r) {
+    float v[kQC];
 #pragma unroll
     for (int c = 0; c < kQC; ++c) {
-      const int m = m0 + c, pa = pb + 2 * r;
-      float a = 0.0f, b = 0.0f;
-      if (owner && m < M) {
-        if (pa < p1) a = rho0[(int64_t)pa * M + m];
-        if (pa + 1 < p1) b = rho0[(int64_t)(pa + 1) * M + m];
-      }
-      S[r][c] = v_make(a, b);
+      const int m = m0 + c, pa = pb + r;
+      v[c] = (owner && m < M && pa < p1) ? rho0[(int64_t)pa * M + m] : 0.0f;
     }
+    S[r][0] = v_make(v[0], v[2]);
+    S[r][1] = v_make(v[1], v[3]);
+  }
+  S[NR][0] = S[NR][1] = v_make(0.0f, 0.0f);
   // The row arrays of the neighbouring CTAs: our first row is the row above
   // CTA rank-1 (its array 0), our last row the row below CTA rank+1 (array 1).
   unsigned char* nb_dn = nullptr;
@@ -295,22 +307,41 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     if (rank + 1 < C && rb == nrb - 1)
       nb_up = cluster.map_shared_rank(E0, rank + 1) + G::row(1) + 16u * (kZero + 1 + qx);
   }
-  auto publish = [&](int par) {
+  // Edges of the block: the left (c0) and right (c3) columns per row pair,
+  // the first and last rows as (c0, c2, c1, c3).
+  auto publish = [&](int par, auto ROTC) {
+    constexpr int ROT = decltype(ROTC)::value;
     unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
 #pragma unroll
     for (int r = 0; r < kQR; ++r) {
-      *reinterpret_cast<float2*>(Ep + G::col(0, r) + oT8) = S[r][0];
-      *reinterpret_cast<float2*>(Ep + G::col(1, r) + oT8) = S[r][kQC - 1];
+      const int s0 = rslot<NR>(2 * r, ROT), s1 = rslot<NR>(2 * r + 1, ROT);
+      float* cl = reinterpret_cast<float*>(Ep + G::col(0, r) + oT8);
+      float* cr = reinterpret_cast<float*>(Ep + G::col(1, r) + oT8);
+      cl[0] = S[s0][0].x;
+      cl[1] = S[s1][0].x;
+      cr[0] = S[s0][1].y;
+      cr[1] = S[s1][1].y;
     }
-    const float4 first = make_float4(S[0][0].x, S[0][1].x, S[0][2].x, S[0][3].x);
-    const float4 last = make_float4(S[kQR - 1][0].y, S[kQR - 1][1].y, S[kQR - 1][2].y, S[kQR - 1][3].y);
-    *reinterpret_cast<float4*>(Ep + G::row(0) + oT16) = first;
-    *reinterpret_cast<float4*>(Ep + G::row(1) + oT16) = last;
+    const int sf = rslot<NR>(0, ROT), sl = rslot<NR>(NR - 1, ROT);
+    float2* fr = reinterpret_cast<float2*>(Ep + G::row(0) + oT16);
+    float2* lr = reinterpret_cast<float2*>(Ep + G::row(1) + oT16);
+    fr[0] = S[sf][0];
+    fr[1] = S[sf][1];
+    lr[0] = S[sl][0];
+    lr[1] = S[sl][1];
     const size_t po = par ? G::par_bytes : 0;
-    if (nb_dn) *reinterpret_cast<float4*>(nb_dn + po) = first;
-    if (nb_up) *reinterpret_cast<float4*>(nb_up + po) = last;
+    if (nb_dn) {
+      float2* d = reinterpret_cast<float2*>(nb_dn + po);
+      d[0] = S[sf][0];
+      d[1] = S[sf][1];
+    }
+    if (nb_up) {
+      float2* d = reinterpret_cast<float2*>(nb_up + po);
+      d[0] = S[sl][0];
+      d[1] = S[sl][1];
+    }
   };
-  if (owner) publish(0);
+  if (owner) publish(0, std::integral_constant<int, 0>{});
   if (C > 1) cluster.sync();
   else __syncthreads();
 
@@ -341,7 +372,8 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
 
   // Observations of rho_k for the active times [l, h] of jump k (Kahan, FP32).
   int ecur = ebeg;
-  auto accumulate = [&](int k, int l, int h) {
+  auto accumulate = [&](int k, int l, int h, auto ROTC) {
+    constexpr int ROT = decltype(ROTC)::value;
     if (!owner || l > h) return;
     const int sk = k & (kStage - 1);
     while (ecur < eend && (ent[ecur].y >> 6) < l) ++ecur;
@@ -349,7 +381,7 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
       const int2 en = ent[e];
       const int ti = en.y >> 6;
       if (ti > h) break;
-      const float v = pick<kQR>(S, en.y & 63);
+      const float v = pick<NR, ROT>(S, en.y & 63);
       const float w = ring[ti * kStage + sk];
       const float y = __fsub_rn(__fmul_rn(w, v), acc_c[en.x]);
       const float s0 = acc_s[en.x];
@@ -375,71 +407,112 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   };
   if (wwarp && any_rec && Kmax >= 1) rec_step(1);
   __syncthreads();
-  accumulate(0, lo, hi);  // rho_0 with the weights of jump 0
+  accumulate(0, lo, hi, std::integral_constant<int, 0>{});  // rho_0 with the weights of jump 0
 
-  // One row pair r of the update, in place.  TOP: the row pair holding row
-  // P-1 (no protein birth out of it, row P absent).
-  auto row_pair = [&](const unsigned char* Ep, int r, int pbk, float (&prevY)[kQC], auto top) {
-    constexpr bool TOP = decltype(top)::value;
-    const float2 lpair = *reinterpret_cast<const float2*>(Ep + G::col(1, r) + oL);  // left block's right column
-    const float2 rpair = *reinterpret_cast<const float2*>(Ep + G::col(0, r) + oR);  // right block's left column
-    float4 above;  // row pb + kRows, for the last row pair
-    if (r + 1 == kQR) above = *reinterpret_cast<const float4*>(Ep + G::row(0) + oA);
-    const int pp = pbk + 2 * r;
-    const float2 fpp = v_make((float)pp, (float)(pp + 1));
-    const float2 cup = v_fma(c_gp, fpp, c_gp);  // gamma_p (p+1) from p+1
-    float2 oldl = lpair;                         // old value of the column to the left
+  // One jump of the block: rho_{k-1} at rotation DIR (0: home, rows
+  // ascending; 1: shifted, rows descending) -> rho_k at rotation 1 - DIR.
+  // Per state, in the shared-memory kernel's order: (1 - e) rho + k_m rho(m-1)
+  // + gamma_m (m+1) rho(m+1) + k_p m rho(p-1) + gamma_p (p+1) rho(p+1); the row
+  // holding P-1 adds k_p m back to 1 - e (no protein birth out of it), rows
+  // beyond it and padding columns stay zero.
+  // Row P-1 (no protein birth out of it: 1 - e gains k_p m back) is handled
+  // without branches when it is a block's last row: every thread adds topA /
+  // topB to the diagonal of its last row, k_p m (both columns of the pair) in
+  // the block holding P-1 and zero elsewhere (adding +0 changes no value); the
+  // row above it is the zero slot.  Warps with a thread whose block holds P-1
+  // elsewhere, rows beyond the box or padding columns run the EDGE update with
+  // explicit checks (warp-uniform, so no warp runs both).
+  const bool edge_t = padcols || (rtop >= 0 && rtop != NR - 1);
+  const bool edge_w = __any_sync(kFull, edge_t);
+  const float2 topA = rtop == NR - 1 ? cdA : v_make(0.0f, 0.0f);
+  const float2 topB = rtop == NR - 1 ? cdB : v_make(0.0f, 0.0f);
+  auto update = [&](int par, auto DIRC, auto EDGEC) {
+    constexpr int DIR = decltype(DIRC)::value;
+    constexpr bool EDGE = decltype(EDGEC)::value;
+    const unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
+    const int rtk = EDGE ? opaque(rtop) : -1;
+    // Row index as a float pair, stepped exactly (integers below 2^24).
+    float2 fp;
+    {
+      const float f0 = (float)opaque(pb + (DIR == 0 ? 0 : NR - 1));
+      fp = v_make(f0, f0);
+    }
+    const float2 fstep = DIR == 0 ? v_make(1.0f, 1.0f) : v_make(-1.0f, -1.0f);
 #pragma unroll
-    for (int c = 0; c < kQC; ++c) {
-      const float2 cur = S[r][c];
-      const float2 right = c + 1 < kQC ? S[r][c + 1] : rpair;
-      const float nx = r + 1 < kQR ? S[r + 1][c].x
-                                   : (c == 0 ? above.x : c == 1 ? above.y : c == 2 ? above.z : above.w);
-      float2 dg = v_fma(c_ngp, fpp, d0p[c]);  // 1 - e_{m,p}
-      if (TOP) {
-        if (pp == P - 1) dg.x = f_add(dg.x, cdv[c]);
-        else dg.y = f_add(dg.y, cdv[c]);
+    for (int i = 0; i < NR; ++i) {
+      const int r = DIR == 0 ? i : NR - 1 - i;
+      const int so = rslot<NR>(r, DIR);                                  // old row r
+      const int sn = DIR == 0 ? (r == 0 ? NR : r - 1) : r;               // its new value
+      // The left block's c3 and the right block's c0 of this row pair, read at
+      // its first row in this jump's order.
+      float2 lp, rp;
+      if ((i & 1) == 0) {
+        lp = *reinterpret_cast<const float2*>(Ep + G::col(1, r >> 1) + oL);
+        rp = *reinterpret_cast<const float2*>(Ep + G::col(0, r >> 1) + oR);
       }
-      float2 y = v_fma(crp[c], right, v_fma(c_l, oldl, v_mul(dg, cur)));
-      y.x = f_fma(cup.x, cur.y, f_fma(cdv[c], prevY[c], y.x));
-      y.y = f_fma(cup.y, nx, f_fma(cdv[c], cur.x, y.y));
-      if (TOP && pp + 1 >= P) y.y = 0.0f;
-      oldl = cur;
-      prevY[c] = cur.y;
-      S[r][c] = y;
+      const float2 A = S[so][0], B = S[so][1];
+      float2 bA, bB, aA, aB;  // rows p-1 and p+1: registers, or the row below / above the block
+      if (r == 0) {
+        const float2* e = reinterpret_cast<const float2*>(Ep + G::row(1) + oB);
+        bA = e[0];
+        bB = e[1];
+      } else {
+        bA = S[rslot<NR>(r - 1, DIR)][0];
+        bB = S[rslot<NR>(r - 1, DIR)][1];
+      }
+      if (r + 1 == NR) {
+        const float2* e = reinterpret_cast<const float2*>(Ep + G::row(0) + oA);
+        aA = e[0];
+        aB = e[1];
+      } else {
+        aA = S[rslot<NR>(r + 1, DIR)][0];
+        aB = S[rslot<NR>(r + 1, DIR)][1];
+      }
+      const float lin = (r & 1) ? lp.y : lp.x;
+      const float rin = (r & 1) ? rp.y : rp.x;
+      float2 dA = v_fma(c_ngp, fp, d0A), dB = v_fma(c_ngp, fp, d0B);  // 1 - e_{m,p}
+      if (EDGE && r == rtk) {
+        dA = v_add(dA, cdA);
+        dB = v_add(dB, cdB);
+      }
+      if (!EDGE && r == NR - 1) {
+        dA = v_add(dA, topA);
+        dB = v_add(dB, topB);
+      }
+      const float2 cup = v_fma(c_gp, fp, c_gp);  // gamma_p (p+1) from p+1
+      float2 yA = v_mul(dA, A);
+      yA.x = f_fma(c_l, lin, yA.x);   // from m - 1: the left block's c3
+      yA.y = f_fma(c_l, B.x, yA.y);   // c1
+      yA = v_fma(crA, B, yA);         // from m + 1: (c1, c3)
+      yA = v_fma(cup, aA, v_fma(cdA, bA, yA));
+      float2 yB = v_fma(c_l2, A, v_mul(dB, B));
+      yB.x = f_fma(crB.x, A.y, yB.x); // from m + 1: c2
+      yB.y = f_fma(crB.y, rin, yB.y); // the right block's c0
+      yB = v_fma(cup, aB, v_fma(cdB, bB, yB));
+      if (EDGE) {
+        if (rtk >= 0 && r > rtk) yA = yB = v_make(0.0f, 0.0f);  // rows beyond the box
+        if (padcols) {                                          // padding columns of the last quad
+          if (!(colmask & 2)) yB.x = 0.0f;
+          if (!(colmask & 4)) yA.y = 0.0f;
+          if (!(colmask & 8)) yB.y = 0.0f;
+        }
+      }
+      S[sn][0] = yA;
+      S[sn][1] = yB;
+      fp = v_add(fp, fstep);
     }
   };
 
   // ---- the jump chain -------------------------------------------------------
-  for (int k = 1; k <= Kmax; ++k) {
+  int k = 1;
+  auto step = [&](auto DIRC) {
+    constexpr int DIR = decltype(DIRC)::value;
+    constexpr int ROT = 1 - DIR;  // rotation of rho_k
     const int par = (k - 1) & 1;
     if (owner) {
-      {
-        // Edges of rho_{k-1} around the block (zero slots outside the box).
-        const unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
-        const float4 below = *reinterpret_cast<const float4*>(Ep + G::row(1) + oB);  // row pb - 1
-        float prevY[kQC] = {below.x, below.y, below.z, below.w};
-        const int pbk = opaque(pb);
-        const int rtk = opaque(rtop);
-#pragma unroll
-        for (int r = 0; r < kQR; ++r) {
-          if (r == rtk) row_pair(Ep, r, pbk, prevY, std::true_type{});  // the row pair holding row P-1
-          else if (rtk >= 0 && r > rtk) {                               // row pairs beyond the box stay zero
-#pragma unroll
-            for (int c = 0; c < kQC; ++c) S[r][c] = v_make(0.0f, 0.0f);
-          } else {
-            row_pair(Ep, r, pbk, prevY, std::false_type{});
-          }
-        }
-        if (colmask != (1 << kQC) - 1) {  // padding columns of the last quad stay zero
-#pragma unroll
-          for (int r = 0; r < kQR; ++r)
-#pragma unroll
-            for (int c = 0; c < kQC; ++c)
-              if (!((colmask >> c) & 1)) S[r][c] = v_make(0.0f, 0.0f);
-        }
-        publish(par ^ 1);
-      }
+      if (edge_w) update(par, DIRC, std::true_type{});
+      else update(par, DIRC, std::false_type{});
+      publish(par ^ 1, std::integral_constant<int, ROT>{});
     }
     // Chunk c (jumps [c kChunk, (c+1) kChunk)) is staged at jump (c-1) kChunk + 1,
     // after the last read of the slots it reuses (chunk c-2's, read up to jump
@@ -454,11 +527,18 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     // Work that touches no edge overlaps the barrier: observations of rho_k,
     // the next chunk of weights, the recurrence one jump ahead.
     advance(k, lo, hi);
-    accumulate(k, lo, hi);
+    accumulate(k, lo, hi, std::integral_constant<int, ROT>{});
     if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
     if (wwarp && any_rec && k + 1 <= Kmax) rec_step(k + 1);
     cluster_wait();
+    ++k;
+  };
+  while (k + 1 <= Kmax) {
+    step(std::integral_constant<int, 0>{});
+    step(std::integral_constant<int, 1>{});
   }
+  if (k <= Kmax) step(std::integral_constant<int, 0>{});
+  // rho_Kmax may be left at rotation 1; only the accumulators are read below.
   cp_async_wait<0>();
 
   // ---- epilogue: sum_g c_g log(a_g) over the cluster's accumulators ---------
