@@ -47,6 +47,12 @@ def parse():
     ap.add_argument("--no-mcmc", action="store_true", help="skip the ESS/s comparison")
     ap.add_argument("--mcmc-iters", type=int, default=400, help="iterations of each timed sampler run")
     ap.add_argument("--mcmc-adapt-iters", type=int, default=1500, help="iteration cap of each adaptive phase")
+    ap.add_argument("--probe", choices=["bd_heavy"], default=None,
+                    help="time one small case for a profiler capture instead of the bench line: bd_heavy = eight "
+                         "birth-death instances of the uneven batch's largest size (N = 18,863, K = 26,884 jumps) "
+                         "on clusters of --probe-cluster CTAs")
+    ap.add_argument("--probe-cluster", type=int, default=4)
+    ap.add_argument("--probe-precision", type=int, default=1, help="1 = FP32, 2 = FP64")
     ap.add_argument("--configs", action="store_true",
                     help="instead of the bench line, measure the other configurations (immigration-death latency, "
                          "uneven batch, general CSR) and an L2-resident copy; prints one JSON object")
@@ -239,6 +245,25 @@ def _bd_K(N, lam, mu, t):
     return np.floor(x + 6.0 * np.sqrt(x)).astype(np.int64) + 1
 
 
+def probe_bd_heavy(cluster: int, precision: int):
+    """Eight birth-death instances N = 18,863, birth 4,700, death 1, t = 1
+    (x = 25,937, K = 26,884): one warm run, then one run timed with CUDA events."""
+    import numpy as np
+    import paper_2312_05647_gb300 as mjp
+    n = 8
+    N = np.full(n, 18863, dtype=np.int64)
+    b = mjp.Batch(N, np.tile([4700.0, 1.0], (n, 1)), np.full(n, 1.0), precision=precision)
+    b.set_option(mjp.OPT_CLUSTER, cluster)
+    o = b.empty_out()
+    b.run(o)
+    ms = _events_ms(lambda: b.run(o))
+    b.check()
+    x = 1.1 * (4700.0 + 18861.0)
+    K = int(np.floor(x + 6.0 * np.sqrt(x))) + 1
+    return {"probe": "bd_heavy", "cluster": cluster, "precision": precision, "instances": n, "N": 18863, "K": K,
+            "ms": ms, "ns_per_jump": ms * 1e6 / K}
+
+
 def other_configs():
     """Measurements of the configurations that are not the bench line."""
     import numpy as np
@@ -359,10 +384,11 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build() if rank == 0 or world == 1 else None
-    if args.configs:
+    if args.configs or args.probe:
         torch.cuda.set_device(local)
         if rank == 0:
-            print(json.dumps(other_configs()), flush=True)
+            res = probe_bd_heavy(args.probe_cluster, args.probe_precision) if args.probe else other_configs()
+            print(json.dumps(res), flush=True)
         return
     if world > 1:
         import torch.distributed as dist

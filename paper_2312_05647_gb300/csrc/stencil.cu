@@ -606,26 +606,36 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   }
 }
 
+// Kernel attributes of one chain_kernel instantiation, raised only when
+// needed (never lowered), so that launches made during CUDA-graph capture
+// issue no attribute calls once a size has been set; the launcher and the
+// occupancy query share them.
 template <typename T, int KIND, bool LL>
-cudaError_t launch_typed(const ChainParams& p, int cluster, int threads, cudaStream_t s) {
-  int tile = p.tile_max > 0 ? p.tile_max : tile_elems(KIND, p.M, p.P, (int)p.N, (int)p.slab);
-  size_t smem = smem_layout(sizeof(T), tile, p.ntimes, p.G, p.nmem, LL).total;
-  auto kern = chain_kernel<T, KIND, LL>;
-  // Attributes are raised only when needed, so that launches made during
-  // CUDA-graph capture issue no attribute calls once a size has been set.
+cudaError_t ensure_attrs(int smem, int cluster) {
   static int smem_set = 0;
   static bool nonportable = false;
+  auto kern = chain_kernel<T, KIND, LL>;
   cudaError_t e;
-  if ((int)smem > smem_set) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > smem_set) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    smem_set = (int)smem;
+    smem_set = smem;
   }
   if (cluster > 8 && !nonportable) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     nonportable = true;
   }
+  return cudaSuccess;
+}
+
+template <typename T, int KIND, bool LL>
+cudaError_t launch_typed(const ChainParams& p, int cluster, int threads, cudaStream_t s) {
+  int tile = p.tile_max > 0 ? p.tile_max : tile_elems(KIND, p.M, p.P, (int)p.N, (int)p.slab);
+  size_t smem = smem_layout(sizeof(T), tile, p.ntimes, p.G, p.nmem, LL).total;
+  auto kern = chain_kernel<T, KIND, LL>;
+  cudaError_t e = ensure_attrs<T, KIND, LL>((int)smem, cluster);
+  if (e != cudaSuccess) return e;
   if (p.B <= 0) return cudaSuccess;  // attribute preparation only
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(p.B * cluster), 1, 1);
@@ -655,11 +665,10 @@ cudaError_t launch_kind(int kind, const ChainParams& p, int cluster, int threads
 template <typename T, int KIND, bool LL>
 int max_clusters_typed(int cluster, int threads, size_t smem) {
   auto kern = chain_kernel<T, KIND, LL>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (ensure_attrs<T, KIND, LL>((int)smem, cluster) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  if (cluster > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)cluster, 1, 1);
   cfg.blockDim = dim3((unsigned)threads, 1, 1);

@@ -166,3 +166,17 @@ def test_register_chain_refusals():
         b.set_option(mjp.OPT_HALO, 0)
     with pytest.raises(MJPError):
         b.set_option(mjp.OPT_CHAIN, 3)
+
+
+def test_shared_memory_attribute_never_lowered():
+    # A large shared-memory batch, then a small single model (whose launch
+    # configuration query sizes the same kernel's shared memory), then a
+    # medium batch: the kernel attribute must still admit the medium launch.
+    import paper_2312_05647_gb300 as mjp
+    big = np.array([20000], dtype=np.int64)
+    _run_batch(big, np.array([[400.0, 1.0]]), np.array([0.01]), np.array([0]), 1, chain=1)
+    cfg = synth.bd_small()
+    _model_expv(64, cfg["theta"], 1, cfg["rho0"], [0.5], chain=1)
+    mid = np.array([6000], dtype=np.int64)
+    got, b = _run_batch(mid, np.array([[300.0, 1.0]]), np.array([0.02]), np.array([0]), 1, chain=1)
+    assert np.abs(got.astype(np.float64) - _oracle_bd(6000, [300.0, 1.0], 0.02, 0)).max() <= TOL[1]
