@@ -298,6 +298,30 @@ def other_configs():
     ms_ll = _events_ms(lambda: mjp.loglik(m, ob, thd, out=lo), reps=3)
     res["immigration_death_N64"] = {"expv_us_per_call": 1e3 * ms / 200, "loglik_evals_s_10k_thetas": 1e4 / (ms_ll / 1e3),
                                     "dtype": "f64", "note": "expv: 200 back-to-back calls (planner + chain kernel)"}
+    # The same solve by fourth-order Runge-Kutta (Method #4): steps to t = 5
+    # and microseconds per call; and a 4,096-state birth-death solve both ways.
+    mr = mjp.Model(cfg["kind"], cfg["dims"], cfg["theta"], mjp.FP64)
+    mr.set_option(mjp.OPT_METHOD, mjp.METHOD_RK4)
+    _, rinfo = mr.expv(r0, cfg["times"], info=True)
+    for _ in range(3):
+        mr.expv(r0, cfg["times"], out=out)
+    ms_rk = _events_ms(lambda: [mr.expv(r0, cfg["times"], out=out) for _ in range(50)], reps=3)
+    N4 = 4096
+    th4 = [1000.0, 1.0]
+    m4 = mjp.Model(mjp.BD1D, [N4], th4, mjp.FP64)
+    r4 = torch.tensor(synth.delta(N4, 0), dtype=torch.float64, device="cuda")
+    o4 = torch.empty((1, N4), dtype=torch.float64, device="cuda")
+    _, i4 = m4.expv(r4, [0.5], info=True)
+    ms4 = _events_ms(lambda: m4.expv(r4, [0.5], out=o4), reps=3)
+    m4.set_option(mjp.OPT_METHOD, mjp.METHOD_RK4)
+    _, i4r = m4.expv(r4, [0.5], info=True)
+    ms4r = _events_ms(lambda: m4.expv(r4, [0.5], out=o4), reps=3)
+    res["rk4_vs_rmjp"] = {
+        "immigration_death_N64": {"rk4_us_per_call": 1e3 * ms_rk / 50, "rk4_steps_to_t5": int(rinfo["K"][-1]),
+                                  "rmjp_us_per_call": 1e3 * ms / 200, "rmjp_jumps_to_t5": 516},
+        "birth_death_N4096_t0.5": {"rk4_ms": ms4r, "rk4_steps": int(i4r["K"][0]), "rmjp_ms": ms4,
+                                   "rmjp_jumps": int(i4["K"][0])},
+        "dtype": "f64"}
     # Uneven batch of 4096 birth-death instances, autotuned, replayed as a CUDA graph.
     bc = synth.bd_batch()
     K = _bd_K(bc["N"], bc["theta"][:, 0], bc["theta"][:, 1], bc["t"])

@@ -96,6 +96,11 @@ extern "C" {
                                    kernel, 2 = register-resident kernel */
 #define MJP_OPT_HALO 8          /* batches, register-resident kernel: halo width h of an instance split over a cluster,
                                    i.e. jumps between two halo exchanges (default 32; 1 .. 1024) */
+#define MJP_OPT_METHOD 9        /* expv_series method: 0 = R-MJP (Algorithm 2, default), 1 = fourth-order Runge-Kutta
+                                   (Method #4, Sec. 2.3; FP64 birth-death models of at most 4,096 states; the times
+                                   are visited in ascending order and each interval is split into
+                                   ceil(interval x max_n |a_nn|) equal steps; the info report then gives
+                                   omega = max_n |a_nn|, K_i = cumulative steps to t_i, eps_i = 0) */
 
 typedef struct mjp_model mjp_model;
 typedef struct mjp_obs mjp_obs;

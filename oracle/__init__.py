@@ -72,6 +72,9 @@ def _lib():
             lib.orc_expv.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_double, ctypes.c_double, _f64p, _f64p,
                                      _i64p, _f64p]
+            lib.orc_rk4.restype = ctypes.c_int
+            lib.orc_rk4.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int, _f64p,
+                                    _i64p, _f64p]
             lib.orc_expm_pade13.restype = ctypes.c_int
             lib.orc_expm_pade13.argtypes = [ctypes.c_int, _f64p, _f64p]
             lib.orc_gillespie.restype = ctypes.c_int
@@ -164,6 +167,27 @@ def expv(csr: CSR, rho0, times, mode: int = PAPER, tol: float = 0.0, omega_facto
     if rc != 0:
         raise ValueError(f"orc_expv failed ({rc})")
     return out, {"omega": om.value, "K": K[:nt].copy(), "eps": eps[:nt].copy()}
+
+
+def rk4(csr: CSR, rho0, times):
+    """rho(t_i) by fourth-order Runge-Kutta (Method #4, Eqs. RKstep and
+    RKintermediate): ascending times, each interval split into
+    ceil(interval x max_n |a_nn|) equal steps (h <= 1 / max_n |a_nn|).
+
+    Returns (out[ntimes, n], info) with info = {"max_exit", "steps"} (steps:
+    cumulative step counts per time, in the caller's order)."""
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    times = np.ascontiguousarray(np.atleast_1d(times), dtype=np.float64)
+    nt = len(times)
+    out = np.zeros((nt, csr.n))
+    steps = np.zeros(max(nt, 1), np.int64)
+    maxe = ctypes.c_double()
+    rc = _lib().orc_rk4(csr.n, _p(csr.row_ptr, _i64p), _p(csr.col, _i32p), _p(csr.val, _f64p),
+                        _p(rho0, _f64p), _p(times, _f64p), nt, _p(out, _f64p), _p(steps, _i64p),
+                        ctypes.byref(maxe))
+    if rc != 0:
+        raise ValueError(f"oracle rk4 failed ({rc})")
+    return out, {"max_exit": maxe.value, "steps": steps[:nt].copy()}
 
 
 def expm(A) -> np.ndarray:

@@ -50,6 +50,7 @@ struct mjp_model {
   int64_t kcap = (int64_t)1 << 26;
   int threads = 0;
   int chain = 0;  // MJP_OPT_CHAIN
+  int method = 0;  // MJP_OPT_METHOD
   int cluster = 0;
   int profile = 0;
   bool timed = false;
@@ -470,6 +471,10 @@ int rate_model_set_option(mjp_model* m, int option, int64_t value) {
       if (value < 0 || value > 2) return fail(MJP_ERR_ARG, "chain must be 0, 1 or 2");
       m->chain = (int)value;
       return MJP_OK;
+    case MJP_OPT_METHOD:
+      if (value < 0 || value > 1) return fail(MJP_ERR_ARG, "method must be 0 (R-MJP) or 1 (RK4)");
+      m->method = (int)value;
+      return MJP_OK;
     case MJP_OPT_ARENA:
       if (value < 0) return fail(MJP_ERR_ARG, "arena capacity must be >= 0");
       m->d_arena.release();
@@ -528,6 +533,67 @@ int rate_model_check(mjp_model* m, void* stream) {
   return map_status(st);
 }
 
+// expv_series by fourth-order Runge-Kutta (Method #4, Sec. 2.3): ascending
+// times, each interval split into ceil(interval x max_n |a_nn|) equal steps;
+// max_n |a_nn| summed per row in the rate matrix's order (death, then birth).
+int expv_rk4(mjp_model* m, const void* rho0, const std::vector<double>& st, const std::vector<int32_t>& order,
+             void* out, mjp_series_info* info, cudaStream_t s) {
+  if (m->kind != MJP_BD1D || m->precision != MJP_FP64)
+    return fail(MJP_ERR_UNSUPPORTED, "RK4 is available for FP64 birth-death models");
+  if (m->N > rk4_max_states()) return fail(MJP_ERR_UNSUPPORTED, "RK4 holds at most 4096 states");
+  const int nt = (int)st.size();
+  const double beta = m->theta[0], gamma = m->theta[1];
+  double maxe = 0.0;
+  for (int64_t n = 0; n < m->N; ++n) {
+    double e = 0.0;
+    if (n >= 1) e = e + gamma * (double)n;
+    if (n + 1 < m->N) e = e + beta;
+    if (e > maxe) maxe = e;
+  }
+  std::vector<int64_t> steps(nt);
+  std::vector<double> h(nt);
+  double tprev = 0.0;
+  for (int q = 0; q < nt; ++q) {
+    const double tau = st[q] - tprev;
+    steps[q] = (maxe > 0.0 && tau > 0.0) ? (int64_t)std::ceil(tau * maxe) : 0;
+    h[q] = steps[q] > 0 ? tau / (double)steps[q] : 0.0;
+    tprev = st[q];
+  }
+  int rc = 0;
+  if ((rc = m->d_orig.ensure(sizeof(int32_t) * nt)) || (rc = m->d_K.ensure(sizeof(int64_t) * nt)) ||
+      (rc = m->d_wtab.ensure(sizeof(double) * nt)) || (rc = m->d_theta.ensure(sizeof(double) * 2)))
+    return rc;
+  MJP_CUDA(cudaMemcpyAsync(m->d_orig.p, order.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_K.p, steps.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_wtab.p, h.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_theta.p, m->theta.data(), sizeof(double) * 2, cudaMemcpyHostToDevice, s));
+  Rk4Params rp = {};
+  rp.theta = m->d_theta.as<double>();
+  rp.N = (int)m->N;
+  rp.rho0 = reinterpret_cast<const double*>(rho0);
+  rp.out = reinterpret_cast<double*>(out);
+  rp.orig = m->d_orig.as<int32_t>();
+  rp.steps = m->d_K.as<int64_t>();
+  rp.hstep = m->d_wtab.as<double>();
+  rp.ntimes = nt;
+  if ((rc = mark(m, 0, s)) || (rc = mark(m, 1, s))) return rc;
+  MJP_CUDA(launch_rk4_bd1d(rp, s));
+  if ((rc = mark(m, 2, s))) return rc;
+  // The host arrays above are pageable: the copies have been staged before
+  // cudaMemcpyAsync returned, so they may go out of scope now.
+  if (info) {
+    MJP_CUDA(cudaStreamSynchronize(s));
+    info->omega = maxe;
+    int64_t total = 0;
+    for (int q = 0; q < nt; ++q) {
+      total += steps[q];
+      if (info->K) info->K[order[q]] = total;
+      if (info->eps) info->eps[order[q]] = 0.0;
+    }
+  }
+  return MJP_OK;
+}
+
 int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes, void* out,
                 mjp_series_info* info, int trunc_mode, double tol, void* stream) {
   if (!m || !rho0 || !times || !out) return fail(MJP_ERR_ARG, "NULL argument");
@@ -543,6 +609,7 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return times[a] < times[b]; });
   std::vector<double> st(nt);
   for (int i = 0; i < nt; ++i) st[i] = times[order[i]];
+  if (m->method == 1) return expv_rk4(m, rho0, st, order, out, info, s);
   if (m->kind == MJP_CSR) {
     std::vector<Win> w;
     int rc = csr_run(m, rho0, st.data(), nt, trunc_mode, tol, s, &w);

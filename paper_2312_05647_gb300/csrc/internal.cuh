@@ -132,6 +132,18 @@ struct CsrJumpParams {
   float* comp;               // FP32 Kahan compensation, ntimes x n
 };
 
+// Fourth-order Runge-Kutta for one birth-death distribution (rk4.cu).
+struct Rk4Params {
+  const double* theta;   // device, {beta, gamma}
+  int N;
+  const double* rho0;    // device, N values
+  double* out;           // device, ntimes x N (caller's time order)
+  const int32_t* orig;   // device, sorted time q -> caller's row
+  const int64_t* steps;  // device, steps of the interval ending at sorted time q
+  const double* hstep;   // device, step length of that interval
+  int ntimes;
+};
+
 }  // namespace mjp
 
 // Host-side launchers implemented in the .cu files.
@@ -173,6 +185,8 @@ bool chain_reg1d_plan(int precision, int64_t Nmax, int ntimes, int cluster, int 
                       bool small = false);
 int64_t chain_reg1d_max_states(int precision);
 cudaError_t launch_chain_reg1d(int precision, const ChainParams& p, const Reg1dPlan& rp, cudaStream_t s);
+int64_t rk4_max_states();
+cudaError_t launch_rk4_bd1d(const Rk4Params& p, cudaStream_t s);
 cudaError_t launch_fill_weights(const Win* win, int ntimes, const int64_t* woff, double* table, cudaStream_t s);
 cudaError_t launch_permute_in(int precision, const void* src, const int32_t* perm, void* dst, int64_t n,
                               cudaStream_t s);

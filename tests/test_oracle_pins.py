@@ -343,3 +343,64 @@ def test_loglik_matches_per_observation_sum():
 def test_log_prior_matches_scipy():
     psi = np.array([0.3, -2.0, 4.6, 1.0])
     assert oracle.log_prior(psi) == pytest.approx(stats.norm.logpdf(psi, 1.0, 1e5).sum(), rel=1e-14)
+
+
+# ---- fourth-order Runge-Kutta (Method #4, Sec. 2.3) --------------------------
+
+@pytest.mark.parametrize("n,deg,seed", [(6, 3, 3), (15, 4, 4)])
+def test_rk4_step_is_degree4_taylor_polynomial(n, deg, seed):
+    # For a linear system one RK4 step (Eqs. RKstep, RKintermediate) is
+    # rho (I + hA + (hA)^2/2 + (hA)^3/6 + (hA)^4/24), formed here from dense
+    # matrix powers (a different sequence of operations).
+    csr = _random_csr(n, deg, seed)
+    A = csr.dense_generator()
+    maxe = oracle.max_exit(csr)
+    h = 0.7 / maxe  # one step: ceil(0.7) = 1
+    gen = np.random.default_rng(seed)
+    rho0 = gen.random(n)
+    rho0 /= rho0.sum()
+    out, info = oracle.rk4(csr, rho0, [h])
+    assert list(info["steps"]) == [1] and info["max_exit"] == maxe
+    hA = h * A
+    P = np.eye(n)
+    term = np.eye(n)
+    for j in range(1, 5):
+        term = term @ hA / j
+        P = P + term
+    assert np.abs(out[0] - rho0 @ P).max() <= 1e-15
+
+
+@pytest.mark.parametrize("a,b,t", [(2.0, 3.0, 0.9), (0.5, 7.5, 3.3), (1.0, 1.0, 10.0)])
+def test_rk4_two_state_iterate_closed_form(a, b, t):
+    # Two states, rates a (0 -> 1) and b (1 -> 0): A has eigenvalues 0 and
+    # -(a + b), so n RK4 steps give exactly pi + (rho0 - pi) R(z)^n with
+    # z = -(a + b) h and R the degree-4 Taylor polynomial of exp.
+    csr = oracle.build_model(oracle.BD1D, [2], [a, b])
+    rho0 = np.array([0.9, 0.1])
+    out, info = oracle.rk4(csr, rho0, [t])
+    ns = math.ceil(t * max(a, b))
+    assert list(info["steps"]) == [ns]
+    z = -(a + b) * (t / ns)
+    R = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    pi = np.array([b, a]) / (a + b)
+    ref = pi + (rho0 - pi) * R ** ns
+    assert np.abs(out[0] - ref).max() <= 1e-14
+    # ... and within the method's error of the exact solution.
+    exact = pi + (rho0 - pi) * math.exp(-(a + b) * t)
+    assert np.abs(out[0] - exact).max() <= ns * abs(z) ** 5 / 120 + 1e-15
+
+
+def test_rk4_times_order_conservation_and_restart():
+    csr = oracle.build_model(oracle.MRNA_PROT2D, [15, 12], [6.0, 1.0, 2.0, 0.3])
+    rho0 = synth.delta(180, 0)
+    times = [0.7, 0.0, 0.25, 0.7, 1.5]
+    out, info = oracle.rk4(csr, rho0, times)
+    assert np.array_equal(out[1], rho0) and info["steps"][1] == 0
+    assert np.array_equal(out[0], out[3])
+    assert np.abs(out.sum(axis=1) - 1.0).max() <= 1e-13
+    # Integrating on from rho(0.25) gives rho(0.7) bit for bit (the step rule
+    # depends only on the interval).
+    rest, _ = oracle.rk4(csr, out[2], [0.7 - 0.25])
+    assert np.array_equal(rest[0], out[0])
+    ref = rho0 @ scipy.linalg.expm(csr.dense_generator() * 1.5)
+    assert np.abs(out[4] - ref).max() <= 1e-5
