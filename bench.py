@@ -316,11 +316,18 @@ def other_configs():
     m4.set_option(mjp.OPT_METHOD, mjp.METHOD_RK4)
     _, i4r = m4.expv(r4, [0.5], info=True)
     ms4r = _events_ms(lambda: m4.expv(r4, [0.5], out=o4), reps=3)
-    res["rk4_vs_rmjp"] = {
+    m4.set_option(mjp.OPT_METHOD, mjp.METHOD_KRYLOV)
+    _, i4k = m4.expv(r4, [0.5], info=True)
+    ms4k = _events_ms(lambda: m4.expv(r4, [0.5], out=o4), reps=3)
+    mr.set_option(mjp.OPT_METHOD, mjp.METHOD_KRYLOV)
+    _, kinfo = mr.expv(r0, cfg["times"], info=True)
+    ms_kr = _events_ms(lambda: [mr.expv(r0, cfg["times"], out=out) for _ in range(50)], reps=3)
+    res["rk4_krylov_vs_rmjp"] = {
         "immigration_death_N64": {"rk4_us_per_call": 1e3 * ms_rk / 50, "rk4_steps_to_t5": int(rinfo["K"][-1]),
+                                  "krylov20_us_per_call": 1e3 * ms_kr / 50, "krylov20_steps_to_t5": int(kinfo["K"][-1]),
                                   "rmjp_us_per_call": 1e3 * ms / 200, "rmjp_jumps_to_t5": 516},
-        "birth_death_N4096_t0.5": {"rk4_ms": ms4r, "rk4_steps": int(i4r["K"][0]), "rmjp_ms": ms4,
-                                   "rmjp_jumps": int(i4["K"][0])},
+        "birth_death_N4096_t0.5": {"rk4_ms": ms4r, "rk4_steps": int(i4r["K"][0]), "krylov20_ms": ms4k,
+                                   "krylov20_steps": int(i4k["K"][0]), "rmjp_ms": ms4, "rmjp_jumps": int(i4["K"][0])},
         "dtype": "f64"}
     # Uneven batch of 4096 birth-death instances, autotuned, replayed as a CUDA graph.
     bc = synth.bd_batch()

@@ -75,6 +75,9 @@ def _lib():
             lib.orc_rk4.restype = ctypes.c_int
             lib.orc_rk4.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int, _f64p,
                                     _i64p, _f64p]
+            lib.orc_krylov.restype = ctypes.c_int
+            lib.orc_krylov.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int,
+                                       ctypes.c_int, _f64p, _i64p, _f64p]
             lib.orc_expm_pade13.restype = ctypes.c_int
             lib.orc_expm_pade13.argtypes = [ctypes.c_int, _f64p, _f64p]
             lib.orc_gillespie.restype = ctypes.c_int
@@ -187,6 +190,25 @@ def rk4(csr: CSR, rho0, times):
                         ctypes.byref(maxe))
     if rc != 0:
         raise ValueError(f"oracle rk4 failed ({rc})")
+    return out, {"max_exit": maxe.value, "steps": steps[:nt].copy()}
+
+
+def krylov(csr: CSR, rho0, times, kappa: int = 20):
+    """rho(t_i) by Krylov steps (Method #5: Algorithm 3 with the full
+    projection of Eq. Krylov_projection, Eq. Krylov_expansion): ascending
+    times, each interval split into ceil(interval x max_n |a_nn| / (2 kappa))
+    equal steps.  Returns (out[ntimes, n], {"max_exit", "steps"})."""
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    times = np.ascontiguousarray(np.atleast_1d(times), dtype=np.float64)
+    nt = len(times)
+    out = np.zeros((nt, csr.n))
+    steps = np.zeros(max(nt, 1), np.int64)
+    maxe = ctypes.c_double()
+    rc = _lib().orc_krylov(csr.n, _p(csr.row_ptr, _i64p), _p(csr.col, _i32p), _p(csr.val, _f64p),
+                           _p(rho0, _f64p), _p(times, _f64p), nt, int(kappa), _p(out, _f64p), _p(steps, _i64p),
+                           ctypes.byref(maxe))
+    if rc != 0:
+        raise ValueError(f"oracle krylov failed ({rc})")
     return out, {"max_exit": maxe.value, "steps": steps[:nt].copy()}
 
 

@@ -389,6 +389,112 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Krylov subspace (Method #5, Sec. 2.3: Algorithm 3, Eqs. Krylov_projection,*/
+/* Krylov_expansion)                                                        */
+/* ------------------------------------------------------------------------ */
+
+int orc_expm_pade13(int n, const double* A, double* E);
+
+/*
+ * out[i*n + s] = rho(t_i)_s by Krylov steps: the times are visited in
+ * ascending order and each interval between consecutive times (from 0) is
+ * split into n_i = ceil(interval * max_n |a_nn| / (2 kappa)) equal steps dt
+ * (the paper's dt = 2 kappa / max_n |a_nn|).  One step from rho:
+ *   beta = ||rho||_2,  q_1 = rho / beta;
+ *   for i = 1..kappa:  w = q_i A;  for j = 1..i: h_ji = <q_j, w>, w -= h_ji q_j
+ *                      (modified Gram-Schmidt, Algorithm 3's inner loop);
+ *                      if i < kappa: h_(i+1)i = ||w||_2, q_(i+1) = w / h_(i+1)i;
+ *   rho <- beta (Q exp(dt H))[:, 1]   (Eq. Krylov_expansion),
+ * i.e. H = Q^T A^T Q of Eq. Krylov_projection with all kappa columns (the
+ * printed algorithm stops one product short of the last column).  If
+ * h_(i+1)i <= 1e-14 max_n |a_nn| the space is invariant: the step uses the
+ * first i vectors.  steps_out / maxe_out as in orc_rk4.
+ */
+int orc_krylov(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+               const double* rho0, const double* times, int ntimes, int kappa, double* out,
+               int64_t* steps_out, double* maxe_out) {
+  if (n < 1 || ntimes < 0 || kappa < 1 || kappa > 64) return ORC_ERR_ARG;
+  for (int i = 0; i < ntimes; ++i)
+    if (!(times[i] >= 0.0) || isinf(times[i])) return ORC_ERR_ARG;
+  double maxe = orc_max_exit(n, row_ptr, val);
+  if (maxe_out) *maxe_out = maxe;
+  const int K = kappa;
+  int* order = (int*)malloc(sizeof(int) * (size_t)(ntimes > 0 ? ntimes : 1));
+  double* exitr = (double*)malloc(sizeof(double) * (size_t)n);
+  double* rho = (double*)malloc(sizeof(double) * (size_t)n);
+  double* w = (double*)malloc(sizeof(double) * (size_t)n);
+  double* Q = (double*)malloc(sizeof(double) * (size_t)n * K);
+  double* H = (double*)malloc(sizeof(double) * K * K);
+  double* Hm = (double*)malloc(sizeof(double) * K * K);
+  double* E = (double*)malloc(sizeof(double) * K * K);
+  int rc = ORC_OK;
+  if (!order || !exitr || !rho || !w || !Q || !H || !Hm || !E) { rc = ORC_ERR_ALLOC; goto done; }
+  for (int64_t s = 0; s < n; ++s) {
+    double e = 0.0;
+    for (int64_t j = row_ptr[s]; j < row_ptr[s + 1]; ++j) e = e + val[j];
+    exitr[s] = e;
+  }
+  for (int i = 0; i < ntimes; ++i) {
+    int j = i;
+    while (j > 0 && times[order[j - 1]] > times[i]) { order[j] = order[j - 1]; --j; }
+    order[j] = i;
+  }
+  memcpy(rho, rho0, sizeof(double) * (size_t)n);
+  double tprev = 0.0;
+  int64_t total = 0;
+  for (int q = 0; q < ntimes; ++q) {
+    const int ti = order[q];
+    const double tau = times[ti] - tprev;
+    const int64_t ns = (maxe > 0.0 && tau > 0.0) ? (int64_t)ceil(tau * maxe / (2.0 * K)) : 0;
+    const double dt = ns > 0 ? tau / (double)ns : 0.0;
+    for (int64_t step = 0; step < ns; ++step) {
+      double b2 = 0.0;
+      for (int64_t s = 0; s < n; ++s) b2 += rho[s] * rho[s];
+      const double beta = sqrt(b2);
+      if (beta == 0.0) break;
+      for (int64_t s = 0; s < n; ++s) Q[s] = rho[s] / beta;
+      for (int i = 0; i < K * K; ++i) H[i] = 0.0;
+      int m = K;
+      for (int i = 0; i < K; ++i) {
+        rate_apply(n, row_ptr, col, val, exitr, Q + (size_t)i * n, w);
+        for (int j = 0; j <= i; ++j) {
+          const double* qj = Q + (size_t)j * n;
+          double h = 0.0;
+          for (int64_t s = 0; s < n; ++s) h += qj[s] * w[s];
+          H[j * K + i] = h;
+          for (int64_t s = 0; s < n; ++s) w[s] = w[s] - h * qj[s];
+        }
+        if (i + 1 < K) {
+          double h2 = 0.0;
+          for (int64_t s = 0; s < n; ++s) h2 += w[s] * w[s];
+          const double hn = sqrt(h2);
+          if (hn <= 1e-14 * maxe) { m = i + 1; break; }
+          H[(i + 1) * K + i] = hn;
+          double* qn = Q + (size_t)(i + 1) * n;
+          for (int64_t s = 0; s < n; ++s) qn[s] = w[s] / hn;
+        }
+      }
+      for (int a = 0; a < m; ++a)
+        for (int c = 0; c < m; ++c) Hm[a * m + c] = dt * H[a * K + c];
+      rc = orc_expm_pade13(m, Hm, E);
+      if (rc) goto done;
+      for (int64_t s = 0; s < n; ++s) {
+        double v = 0.0;
+        for (int i = 0; i < m; ++i) v += Q[(size_t)i * n + s] * E[i * m + 0];
+        rho[s] = beta * v;
+      }
+    }
+    total += ns;
+    memcpy(out + (size_t)ti * n, rho, sizeof(double) * (size_t)n);
+    if (steps_out) steps_out[ti] = total;
+    tprev = times[ti];
+  }
+done:
+  free(order); free(exitr); free(rho); free(w); free(Q); free(H); free(Hm); free(E);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Dense matrix exponential: scaling and squaring with the degree-13 Pade   */
 /* approximant (N. J. Higham, SIAM J. Matrix Anal. Appl. 26 (2005) 1179).   */
 /* The paper's "conventional" baseline (Sec. 1, Sec. 3.2); used on tiny N.  */

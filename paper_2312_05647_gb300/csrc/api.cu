@@ -51,6 +51,8 @@ struct mjp_model {
   int threads = 0;
   int chain = 0;  // MJP_OPT_CHAIN
   int method = 0;  // MJP_OPT_METHOD
+  int kappa = 20;  // MJP_OPT_KAPPA
+  DevBuf d_kq;     // Krylov basis scratch
   int cluster = 0;
   int profile = 0;
   bool timed = false;
@@ -472,8 +474,12 @@ int rate_model_set_option(mjp_model* m, int option, int64_t value) {
       m->chain = (int)value;
       return MJP_OK;
     case MJP_OPT_METHOD:
-      if (value < 0 || value > 1) return fail(MJP_ERR_ARG, "method must be 0 (R-MJP) or 1 (RK4)");
+      if (value < 0 || value > 2) return fail(MJP_ERR_ARG, "method must be 0 (R-MJP), 1 (RK4) or 2 (Krylov)");
       m->method = (int)value;
+      return MJP_OK;
+    case MJP_OPT_KAPPA:
+      if (value < 1 || value > krylov_max_kappa()) return fail(MJP_ERR_ARG, "kappa must be in [1, 32]");
+      m->kappa = (int)value;
       return MJP_OK;
     case MJP_OPT_ARENA:
       if (value < 0) return fail(MJP_ERR_ARG, "arena capacity must be >= 0");
@@ -533,14 +539,18 @@ int rate_model_check(mjp_model* m, void* stream) {
   return map_status(st);
 }
 
-// expv_series by fourth-order Runge-Kutta (Method #4, Sec. 2.3): ascending
-// times, each interval split into ceil(interval x max_n |a_nn|) equal steps;
-// max_n |a_nn| summed per row in the rate matrix's order (death, then birth).
-int expv_rk4(mjp_model* m, const void* rho0, const std::vector<double>& st, const std::vector<int32_t>& order,
+// expv_series by fourth-order Runge-Kutta (Method #4) or Krylov steps
+// (Method #5), Sec. 2.3: ascending times, each interval split into
+// ceil(interval x max_n |a_nn| / D) equal steps, D = 1 (RK4) or 2 kappa
+// (Krylov); max_n |a_nn| summed per row in the rate matrix's order (death,
+// then birth).
+int expv_ode(mjp_model* m, const void* rho0, const std::vector<double>& st, const std::vector<int32_t>& order,
              void* out, mjp_series_info* info, cudaStream_t s) {
+  const bool kry = m->method == 2;
   if (m->kind != MJP_BD1D || m->precision != MJP_FP64)
-    return fail(MJP_ERR_UNSUPPORTED, "RK4 is available for FP64 birth-death models");
-  if (m->N > rk4_max_states()) return fail(MJP_ERR_UNSUPPORTED, "RK4 holds at most 4096 states");
+    return fail(MJP_ERR_UNSUPPORTED, "RK4 and Krylov steps are available for FP64 birth-death models");
+  if (m->N > (kry ? (int64_t)krylov_max_states() : rk4_max_states()))
+    return fail(MJP_ERR_UNSUPPORTED, "RK4 and Krylov steps hold at most 4096 states");
   const int nt = (int)st.size();
   const double beta = m->theta[0], gamma = m->theta[1];
   double maxe = 0.0;
@@ -550,34 +560,54 @@ int expv_rk4(mjp_model* m, const void* rho0, const std::vector<double>& st, cons
     if (n + 1 < m->N) e = e + beta;
     if (e > maxe) maxe = e;
   }
+  const double div = kry ? 2.0 * m->kappa : 1.0;
   std::vector<int64_t> steps(nt);
   std::vector<double> h(nt);
   double tprev = 0.0;
   for (int q = 0; q < nt; ++q) {
     const double tau = st[q] - tprev;
-    steps[q] = (maxe > 0.0 && tau > 0.0) ? (int64_t)std::ceil(tau * maxe) : 0;
+    steps[q] = (maxe > 0.0 && tau > 0.0) ? (int64_t)std::ceil(kry ? tau * maxe / div : tau * maxe) : 0;
     h[q] = steps[q] > 0 ? tau / (double)steps[q] : 0.0;
     tprev = st[q];
   }
   int rc = 0;
   if ((rc = m->d_orig.ensure(sizeof(int32_t) * nt)) || (rc = m->d_K.ensure(sizeof(int64_t) * nt)) ||
-      (rc = m->d_wtab.ensure(sizeof(double) * nt)) || (rc = m->d_theta.ensure(sizeof(double) * 2)))
+      (rc = m->d_wtab.ensure(sizeof(double) * nt)) || (rc = m->d_theta.ensure(sizeof(double) * 2)) ||
+      (rc = ensure_status(m)))
     return rc;
+  if (kry && (rc = m->d_kq.ensure(sizeof(double) * (size_t)m->kappa * m->N))) return rc;
   MJP_CUDA(cudaMemcpyAsync(m->d_orig.p, order.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
   MJP_CUDA(cudaMemcpyAsync(m->d_K.p, steps.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
   MJP_CUDA(cudaMemcpyAsync(m->d_wtab.p, h.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, s));
   MJP_CUDA(cudaMemcpyAsync(m->d_theta.p, m->theta.data(), sizeof(double) * 2, cudaMemcpyHostToDevice, s));
-  Rk4Params rp = {};
-  rp.theta = m->d_theta.as<double>();
-  rp.N = (int)m->N;
-  rp.rho0 = reinterpret_cast<const double*>(rho0);
-  rp.out = reinterpret_cast<double*>(out);
-  rp.orig = m->d_orig.as<int32_t>();
-  rp.steps = m->d_K.as<int64_t>();
-  rp.hstep = m->d_wtab.as<double>();
-  rp.ntimes = nt;
   if ((rc = mark(m, 0, s)) || (rc = mark(m, 1, s))) return rc;
-  MJP_CUDA(launch_rk4_bd1d(rp, s));
+  if (kry) {
+    KrylovParams kp = {};
+    kp.theta = m->d_theta.as<double>();
+    kp.N = (int)m->N;
+    kp.rho0 = reinterpret_cast<const double*>(rho0);
+    kp.out = reinterpret_cast<double*>(out);
+    kp.orig = m->d_orig.as<int32_t>();
+    kp.steps = m->d_K.as<int64_t>();
+    kp.hstep = m->d_wtab.as<double>();
+    kp.ntimes = nt;
+    kp.kappa = m->kappa;
+    kp.maxe = maxe;
+    kp.Q = m->d_kq.as<double>();
+    kp.status = m->d_status.as<int>();
+    MJP_CUDA(launch_krylov_bd1d(kp, s));
+  } else {
+    Rk4Params rp = {};
+    rp.theta = m->d_theta.as<double>();
+    rp.N = (int)m->N;
+    rp.rho0 = reinterpret_cast<const double*>(rho0);
+    rp.out = reinterpret_cast<double*>(out);
+    rp.orig = m->d_orig.as<int32_t>();
+    rp.steps = m->d_K.as<int64_t>();
+    rp.hstep = m->d_wtab.as<double>();
+    rp.ntimes = nt;
+    MJP_CUDA(launch_rk4_bd1d(rp, s));
+  }
   if ((rc = mark(m, 2, s))) return rc;
   // The host arrays above are pageable: the copies have been staged before
   // cudaMemcpyAsync returned, so they may go out of scope now.
@@ -590,6 +620,7 @@ int expv_rk4(mjp_model* m, const void* rho0, const std::vector<double>& st, cons
       if (info->K) info->K[order[q]] = total;
       if (info->eps) info->eps[order[q]] = 0.0;
     }
+    return rate_model_check(m, (void*)s);
   }
   return MJP_OK;
 }
@@ -609,7 +640,7 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return times[a] < times[b]; });
   std::vector<double> st(nt);
   for (int i = 0; i < nt; ++i) st[i] = times[order[i]];
-  if (m->method == 1) return expv_rk4(m, rho0, st, order, out, info, s);
+  if (m->method != 0) return expv_ode(m, rho0, st, order, out, info, s);
   if (m->kind == MJP_CSR) {
     std::vector<Win> w;
     int rc = csr_run(m, rho0, st.data(), nt, trunc_mode, tol, s, &w);

@@ -186,6 +186,24 @@ bool chain_reg1d_plan(int precision, int64_t Nmax, int ntimes, int cluster, int 
 int64_t chain_reg1d_max_states(int precision);
 cudaError_t launch_chain_reg1d(int precision, const ChainParams& p, const Reg1dPlan& rp, cudaStream_t s);
 int64_t rk4_max_states();
+// Krylov subspace steps for one birth-death distribution (krylov.cu).
+struct KrylovParams {
+  const double* theta;   // device, {beta, gamma}
+  int N;
+  const double* rho0;    // device, N values
+  double* out;           // device, ntimes x N (caller's time order)
+  const int32_t* orig;   // device, sorted time q -> caller's row
+  const int64_t* steps;  // device, steps of the interval ending at sorted time q
+  const double* hstep;   // device, step length of that interval
+  int ntimes;
+  int kappa;             // subspace size
+  double maxe;           // max_n |a_nn| (invariant-space threshold)
+  double* Q;             // device scratch, kappa x N
+  int* status;
+};
+int krylov_max_states();
+int krylov_max_kappa();
+cudaError_t launch_krylov_bd1d(const KrylovParams& p, cudaStream_t s);
 cudaError_t launch_rk4_bd1d(const Rk4Params& p, cudaStream_t s);
 cudaError_t launch_fill_weights(const Win* win, int ntimes, const int64_t* woff, double* table, cudaStream_t s);
 cudaError_t launch_permute_in(int precision, const void* src, const int32_t* perm, void* dst, int64_t n,

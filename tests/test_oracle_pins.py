@@ -404,3 +404,47 @@ def test_rk4_times_order_conservation_and_restart():
     assert np.array_equal(rest[0], out[0])
     ref = rho0 @ scipy.linalg.expm(csr.dense_generator() * 1.5)
     assert np.abs(out[4] - ref).max() <= 1e-5
+
+
+# ---- Krylov subspace steps (Method #5, Sec. 2.3) ------------------------------
+
+@pytest.mark.parametrize("kind,dims,theta,t", [(oracle.BD1D, [12], [3.0, 1.0], 2.0), (oracle.BD1D, [2], [2.0, 5.0], 1.7),
+                                               (oracle.TWOSTATE, [6], [4.0, 1.0, 2.0, 1.0], 0.9)])
+def test_krylov_exact_when_the_space_is_whole(kind, dims, theta, t):
+    # kappa >= N: the Krylov space of every step is the whole space (or an
+    # invariant subspace found early), so each step is exact up to rounding.
+    csr = oracle.build_model(kind, dims, theta)
+    n = csr.n
+    gen = np.random.default_rng(n)
+    rho0 = gen.random(n)
+    rho0 /= rho0.sum()
+    out, info = oracle.krylov(csr, rho0, [t, 0.0, t / 3], kappa=20)
+    ref = rho0 @ scipy.linalg.expm(csr.dense_generator() * t)
+    assert np.abs(out[0] - ref).max() <= 1e-13
+    assert np.array_equal(out[1], rho0) and info["steps"][1] == 0
+    # Ascending times 0, t/3, t: cumulative steps ceil(interval x max_exit / (2 kappa)).
+    s1 = math.ceil(t / 3 * info["max_exit"] / 40)
+    assert list(info["steps"]) == [s1 + math.ceil((t - t / 3) * info["max_exit"] / 40), 0, s1]
+
+
+def test_krylov_one_vector_step_closed_form():
+    # kappa = 1: H = <q, q A> (a Rayleigh quotient) and one step is
+    # rho exp(dt rho A rho^T / rho rho^T).
+    csr = _random_csr(9, 3, 7)
+    A = csr.dense_generator()
+    maxe = oracle.max_exit(csr)
+    t = 1.5 / maxe  # kappa = 1: ceil(1.5 / 2) = 1 step
+    rho0 = np.random.default_rng(7).random(9)
+    out, info = oracle.krylov(csr, rho0, [t], kappa=1)
+    assert list(info["steps"]) == [1]
+    ray = rho0 @ A @ rho0 / (rho0 @ rho0)
+    assert np.abs(out[0] - rho0 * math.exp(t * ray)).max() <= 1e-15
+
+
+def test_krylov_immigration_death_accuracy():
+    cfg = synth.bd_small()
+    csr = oracle.build_model(oracle.BD1D, [64], cfg["theta"])
+    out, info = oracle.krylov(csr, cfg["rho0"], cfg["times"])
+    ref, _ = oracle.expv(csr, cfg["rho0"], cfg["times"], mode=oracle.TOL, tol=1e-16)
+    assert list(info["steps"]) == [1, 2, 3, 5, 11]
+    assert np.abs(out - ref).max() <= 1e-9

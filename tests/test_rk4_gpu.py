@@ -70,4 +70,4 @@ def test_rk4_against_rmjp_and_refusals():
     with pytest.raises(MJPError):
         m.expv(torch.tensor(synth.delta(100, 0), device="cuda"), [1.0])
     with pytest.raises(MJPError):
-        m.set_option(mjp.OPT_METHOD, 2)
+        m.set_option(mjp.OPT_METHOD, 3)
