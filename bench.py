@@ -329,6 +329,19 @@ def other_configs():
         "birth_death_N4096_t0.5": {"rk4_ms": ms4r, "rk4_steps": int(i4r["K"][0]), "krylov20_ms": ms4k,
                                    "krylov20_steps": int(i4k["K"][0]), "rmjp_ms": ms4, "rmjp_jumps": int(i4["K"][0])},
         "dtype": "f64"}
+    # Autoregulatory gene network (Sec. 3.1.3): log-likelihoods of 152 jittered
+    # thetas on Gillespie snapshots of (n_R, n_P), 50 times x 120 cells.
+    ac = synth.autoreg()
+    asn = synth.gillespie_snapshots(ac["kind"], ac["dims"], ac["theta"], ac["times"], ac["cells"], synth.rng(5, 2))
+    aob = mjp.Obs(9600, ac["times"], synth.snapshot_obs(ac["kind"], ac["dims"], asn), ac["rho0"])
+    ath = torch.tensor(synth.jitter(ac["theta"], 152, 0.2, synth.rng(5, 3)), dtype=torch.float64, device="cuda")
+    alo = torch.empty(152, dtype=torch.float64, device="cuda")
+    res["autoreg_40x120_loglik_152"] = {}
+    for prec, name in ((mjp.FP64, "f64"), (mjp.FP32, "f32")):
+        am = mjp.Model(ac["kind"], ac["dims"], ac["theta"], prec)
+        mjp.loglik(am, aob, ath, out=alo)
+        ms_a = _events_ms(lambda: mjp.loglik(am, aob, ath, out=alo), reps=3)
+        res["autoreg_40x120_loglik_152"][name] = {"ms": ms_a, "loglik_evals_s": 152 / (ms_a / 1e3)}
     # Uneven batch of 4096 birth-death instances, autotuned, replayed as a CUDA graph.
     bc = synth.bd_batch()
     K = _bd_K(bc["N"], bc["theta"][:, 0], bc["theta"][:, 1], bc["t"])

@@ -64,6 +64,16 @@ extern "C" {
 #define MJP_MRNA_PROT2D 3
 /* General sparse rate matrix given as CSR (rows = source state). */
 #define MJP_CSR 4
+/* Autoregulatory gene network, Eq. STS_chem / Eq. autoReg_def (Sec. 3.1.3).
+ * dims = {N_R, N_P} (both >= 2); N = 2 N_R N_P, n = n_R + N_R n_P +
+ * N_R N_P sigma (sigma 0 active, 1 inactive); theta = {beta_R, beta_P,
+ * gamma_R, gamma_P, lambda_act, lambda_ina}: transcription n_R+1 at beta_R
+ * (active only), translation n_P+1 at beta_P n_R (either state), decays
+ * gamma_R n_R and gamma_P n_P, binding (active, n_P) -> (inactive, n_P-1) at
+ * lambda_ina n_P, unbinding (inactive, n_P) -> (active, n_P+1) at lambda_act;
+ * transitions whose target leaves the box are dropped (reflecting).  The
+ * chain kernels hold it as N_R columns by 2 N_P rows (row 2 n_P + sigma). */
+#define MJP_AUTOREG 5
 
 /* ---- chain precision --------------------------------------------------- */
 #define MJP_FP32 1 /* FP32 chain, Kahan-compensated FP32 accumulation, FP64 Omega/K/weights */

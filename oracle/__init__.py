@@ -32,7 +32,7 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _LOCK = threading.Lock()
 _LIB = None
 
-BD1D, TWOSTATE, MRNA_PROT2D = 1, 2, 3
+BD1D, TWOSTATE, MRNA_PROT2D, AUTOREG = 1, 2, 3, 5
 PAPER, TOL = 0, 1
 
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -118,7 +118,7 @@ def build_model(kind: int, dims, theta) -> CSR:
     nnz = lib.orc_build_model(kind, _p(d, _i64p), len(d), _p(th, _f64p), len(th), None, None, None, 0)
     if nnz < 0:
         raise ValueError("bad model arguments")
-    n = int(np.prod(d)) * (2 if kind == TWOSTATE else 1)
+    n = int(np.prod(d)) * (2 if kind in (TWOSTATE, AUTOREG) else 1)
     row_ptr = np.zeros(n + 1, np.int64)
     col = np.zeros(max(nnz, 1), np.int32)
     val = np.zeros(max(nnz, 1), np.float64)

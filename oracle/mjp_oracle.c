@@ -33,6 +33,8 @@
 #define ORC_BD1D 1        /* birth-death, Eq. BD_def (Sec. 3.1.1)            */
 #define ORC_TWOSTATE 2    /* two-state birth-death, Eq. Gene_def (Sec. 3.1.2)*/
 #define ORC_MRNA_PROT2D 3 /* mRNA/protein birth-death, built from Eq.       */
+#define ORC_AUTOREG 5     /* autoregulatory gene network, Eq. STS_chem /
+                             Eq. autoReg_def (Sec. 3.1.3)                    */
                           /* STS_chem's R->R+P reaction without switching    */
 
 /* ------------------------------------------------------------------------ */
@@ -124,6 +126,36 @@ int64_t orc_build_model(int kind, const int64_t* dims, int ndims,
       }
     }
     if (row_ptr) row_ptr[M * P] = nnz;
+    return nnz;
+  }
+  if (kind == ORC_AUTOREG) {
+    /*
+     * dims = {N_R, N_P}, theta = {beta_R, beta_P, gamma_R, gamma_P, lambda_act,
+     * lambda_ina}; n = n_R + N_R n_P + N_R N_P sigma (sigma 0 active), N =
+     * 2 N_R N_P.  The reactions of Eq. STS_chem: transcription beta_R (active
+     * only), translation beta_P n_R (either gene state), R decay gamma_R n_R,
+     * P decay gamma_P n_P, binding sigma_act + P -> sigma_ina at lambda_ina n_P,
+     * unbinding sigma_ina -> sigma_act + P at lambda_act; a transition whose
+     * target leaves the box is dropped (reflecting).  Entries in ascending
+     * target order.
+     */
+    if (ndims != 2 || ntheta != 6 || dims[0] < 2 || dims[1] < 2) return ORC_ERR_ARG;
+    int64_t M = dims[0], P = dims[1];
+    double bR = theta[0], bP = theta[1], gR = theta[2], gP = theta[3], la = theta[4], li = theta[5];
+    for (int64_t sg = 0; sg < 2; ++sg)
+      for (int64_t p = 0; p < P; ++p)
+        for (int64_t m = 0; m < M; ++m) {
+          int64_t n = m + M * p + M * P * sg;
+          if (row_ptr) row_ptr[n] = nnz;
+          if (sg == 1 && p + 1 < P) nnz = push(row_ptr, col, val, nnz, cap, n - M * P + M, la);
+          if (p >= 1) nnz = push(row_ptr, col, val, nnz, cap, n - M, gP * (double)p);
+          if (m >= 1) nnz = push(row_ptr, col, val, nnz, cap, n - 1, gR * (double)m);
+          if (sg == 0 && m + 1 < M) nnz = push(row_ptr, col, val, nnz, cap, n + 1, bR);
+          if (p + 1 < P && m >= 1) nnz = push(row_ptr, col, val, nnz, cap, n + M, bP * (double)m);
+          if (sg == 0 && p >= 1) nnz = push(row_ptr, col, val, nnz, cap, n + M * P - M, li * (double)p);
+          if (nnz < 0) return ORC_ERR_ARG;
+        }
+    if (row_ptr) row_ptr[2 * M * P] = nnz;
     return nnz;
   }
   return ORC_ERR_ARG;

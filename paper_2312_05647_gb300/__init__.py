@@ -13,14 +13,14 @@ import ctypes
 import numpy as np
 
 from . import capi
-from .capi import (BD1D, CSR, FP32, FP64, METHOD_KRYLOV, METHOD_RK4, METHOD_RMJP, MRNA_PROT2D, OPT_ARENA,
+from .capi import (AUTOREG, BD1D, CSR, FP32, FP64, METHOD_KRYLOV, METHOD_RK4, METHOD_RMJP, MRNA_PROT2D, OPT_ARENA,
                    OPT_CHAIN, OPT_CLUSTER, OPT_HALO, OPT_K_CAP, OPT_KAPPA, OPT_METHOD, OPT_PROFILE, OPT_RENORM_PERIOD, OPT_THREADS, PTR_DEVICE, PTR_HOST, TRUNC_PAPER, TRUNC_TOL, TWOSTATE,
                    MJPError)
 
-__all__ = ["Model", "Obs", "Batch", "loglik", "BD1D", "TWOSTATE", "MRNA_PROT2D", "CSR", "FP32", "FP64",
+__all__ = ["Model", "Obs", "Batch", "loglik", "BD1D", "TWOSTATE", "MRNA_PROT2D", "AUTOREG", "CSR", "FP32", "FP64",
            "TRUNC_PAPER", "TRUNC_TOL", "MJPError"]
 
-_NTHETA = {BD1D: 2, TWOSTATE: 4, MRNA_PROT2D: 4}
+_NTHETA = {BD1D: 2, TWOSTATE: 4, MRNA_PROT2D: 4, AUTOREG: 6}
 
 
 def _stream_ptr(stream=None):

@@ -17,7 +17,7 @@ MJP_OK = 0
 ERRORS = {-1: "MJP_ERR_ARG", -2: "MJP_ERR_CSR", -3: "MJP_ERR_ALLOC", -4: "MJP_ERR_CUDA",
           -5: "MJP_ERR_DEVICE_TIMEOUT", -6: "MJP_ERR_KCAP", -7: "MJP_ERR_NUMERIC",
           -8: "MJP_ERR_UNSUPPORTED"}
-BD1D, TWOSTATE, MRNA_PROT2D, CSR = 1, 2, 3, 4
+BD1D, TWOSTATE, MRNA_PROT2D, CSR, AUTOREG = 1, 2, 3, 4, 5
 FP32, FP64 = 1, 2
 TRUNC_PAPER, TRUNC_TOL = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1

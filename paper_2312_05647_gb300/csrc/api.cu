@@ -34,6 +34,7 @@ int ntheta_of(int kind) {
     case MJP_BD1D: return 2;
     case MJP_TWOSTATE: return 4;
     case MJP_MRNA_PROT2D: return 4;
+    case MJP_AUTOREG: return 6;
     default: return 0;
   }
 }
@@ -179,6 +180,8 @@ double omega_bound(const mjp_model* m, const double* th) {
     case MJP_TWOSTATE: return 1.1 * (th[0] + th[1] * (double)(m->M - 1) + th[2] + th[3]);
     case MJP_MRNA_PROT2D:
       return 1.1 * (th[0] + (th[1] + th[2]) * (double)(m->M - 1) + th[3] * (double)(m->P - 1));
+    case MJP_AUTOREG:  // Sec. 3.1.3's bound with each decay rate in its place (P = 2 N_P tile rows)
+      return 1.1 * (th[0] + (th[1] + th[2]) * (double)(m->M - 1) + (th[3] + th[5]) * (double)(m->P / 2 - 1) + th[4]);
     default: return 0.0;
   }
 }
@@ -313,7 +316,7 @@ int rate_model_create_stencil(mjp_model** out, int kind, const int64_t* dims, in
                               const double* theta, int ntheta, int precision) {
   if (!out) return fail(MJP_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (kind != MJP_BD1D && kind != MJP_TWOSTATE && kind != MJP_MRNA_PROT2D)
+  if (kind != MJP_BD1D && kind != MJP_TWOSTATE && kind != MJP_MRNA_PROT2D && kind != MJP_AUTOREG)
     return fail(MJP_ERR_ARG, "unknown stencil kind");
   if (precision != MJP_FP32 && precision != MJP_FP64) return fail(MJP_ERR_ARG, "precision must be MJP_FP32 or MJP_FP64");
   if (!dims || !theta) return fail(MJP_ERR_ARG, "dims/theta is NULL");
@@ -329,6 +332,9 @@ int rate_model_create_stencil(mjp_model** out, int kind, const int64_t* dims, in
   } else if (kind == MJP_TWOSTATE) {
     if (ndims != 1 || dims[0] < 2) { delete m; return fail(MJP_ERR_ARG, "TWOSTATE needs dims = {N_R}, N_R >= 2"); }
     m->M = dims[0]; m->P = 2; m->N = 2 * dims[0];
+  } else if (kind == MJP_AUTOREG) {
+    if (ndims != 2 || dims[0] < 2 || dims[1] < 2) { delete m; return fail(MJP_ERR_ARG, "AUTOREG needs dims = {N_R >= 2, N_P >= 2}"); }
+    m->M = dims[0]; m->P = 2 * dims[1]; m->N = 2 * dims[0] * dims[1];
   } else {
     if (ndims != 2 || dims[0] < 2 || dims[1] < 1) { delete m; return fail(MJP_ERR_ARG, "MRNA_PROT2D needs dims = {M >= 2, P >= 1}"); }
     m->M = dims[0]; m->P = dims[1]; m->N = dims[0] * dims[1];

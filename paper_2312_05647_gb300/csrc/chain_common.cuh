@@ -48,7 +48,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // Scaled rates (rate / Omega) of one instance in the chain type.
 template <typename T>
 struct Coef {
-  T a, b, c, d;
+  T a, b, c, d, e, f;
 };
 
 template <typename T, int KIND>
@@ -59,6 +59,8 @@ __device__ __forceinline__ Coef<T> make_coef(const double* th, double omega) {
   k.b = (T)(th[1] * inv);
   k.c = (KIND == MJP_BD1D) ? (T)0 : (T)(th[2] * inv);
   k.d = (KIND == MJP_BD1D) ? (T)0 : (T)(th[3] * inv);
+  k.e = (KIND == MJP_AUTOREG) ? (T)(th[4] * inv) : (T)0;
+  k.f = (KIND == MJP_AUTOREG) ? (T)(th[5] * inv) : (T)0;
   return k;
 }
 

@@ -70,6 +70,15 @@ __device__ double exit_rate(int kind, int64_t M, int64_t P, int64_t n, const dou
       e = __dadd_rn(e, th[2]);
       if (nr >= 1) e = __dadd_rn(e, __dmul_rn(th[1], (double)nr));
     }
+  } else if (kind == MJP_AUTOREG) {  // model index n_R + N_R n_P + N_R N_P sigma; P = 2 N_P tile rows
+    const int64_t Pm = P / 2, sg = n / (M * Pm), rem = n - sg * M * Pm, q = rem / M, m = rem - q * M;
+    // th = {beta_R, beta_P, gamma_R, gamma_P, lambda_act, lambda_ina}, targets ascending
+    if (sg == 1 && q + 1 < Pm) e = __dadd_rn(e, th[4]);
+    if (q >= 1) e = __dadd_rn(e, __dmul_rn(th[3], (double)q));
+    if (m >= 1) e = __dadd_rn(e, __dmul_rn(th[2], (double)m));
+    if (sg == 0 && m + 1 < M) e = __dadd_rn(e, th[0]);
+    if (q + 1 < Pm && m >= 1) e = __dadd_rn(e, __dmul_rn(th[1], (double)m));
+    if (sg == 0 && q >= 1) e = __dadd_rn(e, __dmul_rn(th[5], (double)q));
   } else {  // MRNA_PROT2D: targets n-M, n-1, n+1, n+M
     int64_t p = n / M, m = n - p * M;
     if (p >= 1) e = __dadd_rn(e, __dmul_rn(th[3], (double)p));

@@ -218,6 +218,14 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   const T* rho0 = reinterpret_cast<const T*>(p.rho0);
   const int64_t s0 = p.job_s0 ? p.job_s0[job] : -1;  // rho0 = delta at s0
   auto rho0_at = [&](int64_t n) -> T { return s0 >= 0 ? (T)(n == s0 ? 1 : 0) : rho0[n]; };
+  // Model index of tile row `row`, column `col`.  The autoregulatory model's
+  // tile rows interleave the gene states (row 2 n_P + sigma), so a row pair
+  // holds both gene states of one protein count; its model index is
+  // n_R + N_R n_P + N_R N_P sigma (Sec. 3.1.3).
+  const int Pm = (KIND == MJP_AUTOREG) ? P / 2 : P;
+  auto gidx = [&](int64_t row, int64_t col) -> int64_t {
+    return KIND == MJP_AUTOREG ? col + (int64_t)M * (row >> 1) + (int64_t)M * Pm * (row & 1) : row * M + col;
+  };
   for (int j = tid; j < tile; j += nthr) {
     buf0[j] = (T)0;
     buf1[j] = (T)0;
@@ -226,7 +234,7 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   T msum = (T)0;
   for (int j = tid; j < g.W * g.H; j += nthr) {
     int r = j / g.W, c = j - r * g.W;
-    T v = rho0_at((int64_t)(g.p0 + r) * M + g.m0 + c);
+    T v = rho0_at(gidx(g.p0 + r, g.m0 + c));
     buf0[KIND == MJP_BD1D ? c + 1 : elem2d(g, r, c)] = v;
     msum += v;
   }
@@ -238,14 +246,23 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     if (tid == 0 && g.W > 0 && g.m1 < M) buf0[g.Wp - 1] = rho0_at(g.m1);
   } else if (g.H > 0) {
     for (int c = tid; c < g.W; c += nthr) {
-      if (g.p0 >= 1) buf0[(c + 1) * 2 + 1] = rho0_at((int64_t)(g.p0 - 1) * M + c);
-      if (g.p1 < P) buf0[((g.Hp + 1) * g.Wp + c + 1) * 2] = rho0_at((int64_t)g.p1 * M + c);
+      if (g.p0 >= 1) buf0[(c + 1) * 2 + 1] = rho0_at(gidx(g.p0 - 1, c));
+      if (g.p1 < P) buf0[((g.Hp + 1) * g.Wp + c + 1) * 2] = rho0_at(gidx(g.p1, c));
+      // The autoregulatory update reads both gene states of the neighbouring
+      // protein counts, i.e. whole pad pairs.
+      if (KIND == MJP_AUTOREG && g.p0 >= 2) buf0[(c + 1) * 2] = rho0_at(gidx(g.p0 - 2, c));
+      if (KIND == MJP_AUTOREG && g.p1 + 1 < P) buf0[((g.Hp + 1) * g.Wp + c + 1) * 2 + 1] = rho0_at(gidx(g.p1 + 1, c));
     }
   }
   if (LL) {
     // Tile index of state s in this CTA, or -1 when another CTA owns it.
     auto loc_of = [&](int s) -> int {
       int ps = s / M, ms = s - ps * M;
+      if (KIND == MJP_AUTOREG) {  // tile row 2 n_P + sigma
+        const int sg = s / (M * Pm), rem = s - sg * M * Pm, pm = rem / M;
+        ms = rem - pm * M;
+        ps = 2 * pm + sg;
+      }
       bool mine = ps >= g.p0 && ps < g.p1 && ms >= g.m0 && ms < g.m1;
       return !mine ? -1 : (KIND == MJP_BD1D ? ms - g.m0 + 1 : elem2d(g, ps - g.p0, ms));
     };
@@ -402,6 +419,10 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   const T one = (T)1;
   T cd = (T)0;
   T2 c_l = v_make((T)0, (T)0), c_r = c_l, c_d = c_l, c_dg = c_l, c_sw = c_l, c_gp = c_l, c_ngp = c_l;
+  // Autoregulatory column constants: gamma_R m, beta_R (if m+1 < N_R), beta_P m.
+  const T a_gm = (KIND == MJP_AUTOREG) ? f_mul(co.c, (T)mc) : (T)0;
+  const T a_tx = (KIND == MJP_AUTOREG && mc + 1 < M) ? co.a : (T)0;
+  const T a_tl = (KIND == MJP_AUTOREG) ? f_mul(co.b, (T)mc) : (T)0;
   if (KIND == MJP_TWOSTATE) {
     // Active row (x): birth from m-1, death from m+1, reactivation of the
     // inactive state; inactive row (y): death from m+1, deactivation.
@@ -411,7 +432,11 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     c_r = v_make(cr, cr);
     c_dg = v_make(f_sub(one, f_add(f_add(bm, mc + 1 < M ? co.a : (T)0), co.d)), f_sub(one, f_add(co.c, bm)));
     c_sw = v_make(co.c, co.d);
-  } else if (KIND == MJP_MRNA_PROT2D) {
+  } else if (KIND == MJP_AUTOREG) {
+    const T cr = f_mul(co.c, (T)(mc + 1));                 // gamma_R (m+1) from m+1
+    c_r = v_make(cr, cr);
+  }
+  if (KIND == MJP_MRNA_PROT2D) {
     const T fm = (T)mc;
     const T cr = f_mul(co.b, (T)(mc + 1));                 // gamma_m (m+1) from m+1
     cd = f_mul(co.c, fm);                                  // k_p m from p-1
@@ -504,15 +529,36 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
         const T2 next = sp[W2];
         const T2 left = sp[-1], right = sp[1];
         if (!LL) {
-          expv_accumulate(rn ? f_mul(cur.x, f) : cur.x, (int64_t)pp * M + mc, k - 1, plo, phi, wprev);
+          expv_accumulate(rn ? f_mul(cur.x, f) : cur.x, gidx(pp, mc), k - 1, plo, phi, wprev);
           if (pp + 1 < g.p1)
-            expv_accumulate(rn ? f_mul(cur.y, f) : cur.y, (int64_t)(pp + 1) * M + mc, k - 1, plo, phi, wprev);
+            expv_accumulate(rn ? f_mul(cur.y, f) : cur.y, gidx(pp + 1, mc), k - 1, plo, phi, wprev);
         }
         if (jump) {
           if (KIND == MJP_TWOSTATE) {
             const T2 t1 = v_fma(c_l, left, v_mul(c_dg, cur));
             const T2 t2 = v_fma(c_sw, v_make(cur.y, cur.x), v_mul(c_r, right));
             y = v_add(t1, t2);
+          } else if (KIND == MJP_AUTOREG) {
+            // Pair = (active, inactive) at protein count q: transcription from
+            // m-1 (active only), R decay from m+1, translation from q-1, P
+            // decay from q+1, unbinding from (q-1, inactive) into active,
+            // binding from (q+1, active) into inactive.
+            const int q = pp >> 1;
+            const T fq = (T)q;
+            const bool qtop = q + 1 >= Pm;
+            const T decay = f_add(f_mul(co.d, fq), a_gm);         // gamma_P q + gamma_R m
+            const T tr = qtop ? (T)0 : a_tl;                       // beta_P m, if q+1 exists
+            const T e0 = f_add(f_add(f_add(decay, a_tx), tr), f_mul(co.f, fq));
+            const T e1 = f_add(f_add(decay, tr), qtop ? (T)0 : co.e);
+            y.x = f_mul(f_sub(one, e0), cur.x);
+            y.y = f_mul(f_sub(one, e1), cur.y);
+            y.x = f_fma(co.a, left.x, y.x);
+            y = v_fma(c_r, right, y);
+            y = v_fma(v_make(a_tl, a_tl), prev, y);
+            const T gq = f_mul(co.d, (T)(q + 1));
+            y = v_fma(v_make(gq, gq), next, y);
+            y.x = f_fma(co.e, prev.y, y.x);
+            y.y = f_fma(f_mul(co.f, (T)(q + 1)), next.x, y.y);
           } else {
             T2 dg = v_fma(c_ngp, fpp, c_dg);        // 1 - e_{m,p}
             const T2 cup = v_fma(c_gp, fpp, c_gp);  // gamma_p (p+1) from p+1
@@ -658,6 +704,7 @@ cudaError_t launch_kind(int kind, const ChainParams& p, int cluster, int threads
     case MJP_BD1D: return launch_typed<T, MJP_BD1D, LL>(p, cluster, threads, s);
     case MJP_TWOSTATE: return launch_typed<T, MJP_TWOSTATE, LL>(p, cluster, threads, s);
     case MJP_MRNA_PROT2D: return launch_typed<T, MJP_MRNA_PROT2D, LL>(p, cluster, threads, s);
+    case MJP_AUTOREG: return launch_typed<T, MJP_AUTOREG, LL>(p, cluster, threads, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -693,6 +740,7 @@ int max_clusters_kind(int kind, int cluster, int threads, size_t smem) {
   switch (kind) {
     case MJP_BD1D: return max_clusters_typed<T, MJP_BD1D, LL>(cluster, threads, smem);
     case MJP_TWOSTATE: return max_clusters_typed<T, MJP_TWOSTATE, LL>(cluster, threads, smem);
+    case MJP_AUTOREG: return max_clusters_typed<T, MJP_AUTOREG, LL>(cluster, threads, smem);
     default: return max_clusters_typed<T, MJP_MRNA_PROT2D, LL>(cluster, threads, smem);
   }
 }

@@ -22,7 +22,7 @@ from __future__ import annotations
 import numpy as np
 
 SEED_BASE = 20231205
-BD1D, TWOSTATE, MRNA_PROT2D = 1, 2, 3
+BD1D, TWOSTATE, MRNA_PROT2D, AUTOREG = 1, 2, 3, 5
 
 
 def rng(config_no: int, salt: int = 0) -> np.random.Generator:
@@ -71,6 +71,16 @@ def twostate_promoter(N_R: int = 300):
     [0.5, 10], 100 cells per time, rho0 = (n_R = 0, active)."""
     return dict(kind=TWOSTATE, dims=[N_R], theta=[100.0, 1.0, 2.0, 1.0],
                 rho0=delta(2 * N_R, 0), times=np.linspace(0.5, 10.0, 50), cells=100)
+
+
+def autoreg():
+    """Autoregulatory gene network (Sec. 3.1.3) with the paper's rates for
+    (beta_R, beta_P) = (10, 0.5): gamma_R = 1, gamma_P = 0.1, lambda_act = 0.1,
+    lambda_ina = 0.05; box N_R = 40, N_P = 120 (N = 9,600); 50 times evenly
+    spaced in [0.5, 10], 120 cells each (6,000 observations); rho0 = (0, 0,
+    active)."""
+    return dict(kind=AUTOREG, dims=[40, 120], theta=[10.0, 0.5, 1.0, 0.1, 0.1, 0.05],
+                rho0=delta(9600, 0), times=np.linspace(0.5, 10.0, 50), cells=120)
 
 
 def jitter(theta, B: int, frac: float, gen: np.random.Generator) -> np.ndarray:
@@ -154,6 +164,16 @@ def _propensities(kind, dims, theta, st):
         a = np.stack([np.where(m < M - 1, km, 0.0), gm * m,
                       np.where(p < P - 1, kp * m, 0.0), gp * p], axis=1)
         change = np.array([[1, 0], [-1, 0], [0, 1], [0, -1]])
+    elif kind == AUTOREG:
+        NR, NP = dims
+        bR, bP, gR, gP, lact, lina = theta
+        r, q, s = st[:, 0], st[:, 1], st[:, 2]
+        a = np.stack([np.where((s == 0) & (r < NR - 1), bR, 0.0),            # transcription (active)
+                      np.where(q < NP - 1, bP * r, 0.0),                     # translation
+                      gR * r, gP * q,                                         # decays
+                      np.where(s == 0, lina * q, 0.0),                        # active + P -> inactive
+                      np.where((s == 1) & (q < NP - 1), lact, 0.0)], axis=1)  # inactive -> active + P
+        change = np.array([[1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0], [0, -1, 1], [0, 1, -1]])
     else:
         raise ValueError(kind)
     return a, change
@@ -164,7 +184,7 @@ def gillespie_snapshots(kind: int, dims, theta, times, cells: int, gen: np.rando
     two-state model, active) are simulated to that time; returns a list of
     integer arrays (cells x components): (n,), (n_R, sigma) or (m, p)."""
     times = np.asarray(times, dtype=np.float64)
-    ncomp = 1 if kind == BD1D else 2
+    ncomp = 1 if kind == BD1D else (3 if kind == AUTOREG else 2)
     T = np.repeat(times, cells)
     st = np.zeros((len(T), ncomp), np.int64)
     tau = np.zeros(len(T))
@@ -204,6 +224,10 @@ def snapshot_obs(kind: int, dims, samples):
             NR = dims[0]
             vals, counts = np.unique(smp[:, 0], return_counts=True)
             members = [np.array([v, v + NR]) for v in vals]
+        elif kind == AUTOREG:  # (n_R, n_P) observed, the gene state summed out (Sec. 3.1.3)
+            NR, NP = dims
+            vals, counts = np.unique(smp[:, 0] + NR * smp[:, 1], return_counts=True)
+            members = [np.array([v, v + NR * NP]) for v in vals]
         else:
             M = dims[0]
             keys = smp[:, 0] + M * smp[:, 1]

@@ -448,3 +448,75 @@ def test_krylov_immigration_death_accuracy():
     ref, _ = oracle.expv(csr, cfg["rho0"], cfg["times"], mode=oracle.TOL, tol=1e-16)
     assert list(info["steps"]) == [1, 2, 3, 5, 11]
     assert np.abs(out - ref).max() <= 1e-9
+
+
+# ---- autoregulatory gene network (Sec. 3.1.3, Eq. STS_chem) ------------------
+
+def _autoreg_generator_from_reactions(NR, NP, th):
+    """Dense A built straight from the reaction list of Eq. STS_chem (state
+    tuples, reflecting box): an independent construction of the model."""
+    bR, bP, gR, gP, la, li = th
+    idx = lambda r, p, s: r + NR * p + NR * NP * s
+    N = 2 * NR * NP
+    A = np.zeros((N, N))
+    for s in (0, 1):
+        for p in range(NP):
+            for r in range(NR):
+                moves = []
+                if s == 0:
+                    moves.append(((r + 1, p, 0), bR))          # transcription
+                    moves.append(((r, p - 1, 1), li * p))      # sigma_act + P -> sigma_ina
+                else:
+                    moves.append(((r, p + 1, 0), la))          # sigma_ina -> sigma_act + P
+                moves.append(((r, p + 1, s), bP * r))          # translation
+                moves.append(((r - 1, p, s), gR * r))          # R decay
+                moves.append(((r, p - 1, s), gP * p))          # P decay
+                for (r2, p2, s2), rate in moves:
+                    if 0 <= r2 < NR and 0 <= p2 < NP and rate > 0:
+                        A[idx(r, p, s), idx(r2, p2, s2)] += rate
+    A[np.diag_indices(N)] = -A.sum(axis=1)
+    return A
+
+
+@pytest.mark.parametrize("NR,NP,th", [(4, 3, [2.5, 0.125, 1.0, 0.1, 0.1, 0.05]), (5, 6, [20.0, 1.0, 1.0, 0.1, 0.1, 0.05]),
+                                      (2, 2, [1.0, 2.0, 3.0, 4.0, 5.0, 6.0])])
+def test_autoreg_generator_matches_the_reactions(NR, NP, th):
+    csr = oracle.build_model(oracle.AUTOREG, [NR, NP], th)
+    A = csr.dense_generator()
+    assert np.array_equal(A, _autoreg_generator_from_reactions(NR, NP, th))
+    # The paper's bound on the largest exit rate (Sec. 3.1.3, one decay rate
+    # gamma; the larger of gamma_R, gamma_P keeps it a bound).
+    g = max(th[2], th[3])
+    bound = th[0] + (th[1] + g) * (NR - 1) + (g + th[5]) * (NP - 1) + th[4]
+    assert oracle.max_exit(csr) <= bound
+
+
+def test_autoreg_without_switching_is_the_mrna_protein_model():
+    # lambda_act = lambda_ina = 0 and an active start: the inactive block stays
+    # empty and the active block evolves as the mRNA/protein box.
+    NR, NP = 9, 7
+    th = [5.0, 0.5, 1.0, 0.3, 0.0, 0.0]
+    auto = oracle.build_model(oracle.AUTOREG, [NR, NP], th)
+    mp = oracle.build_model(oracle.MRNA_PROT2D, [NR, NP], [th[0], th[2], th[1], th[3]])
+    rho0 = np.zeros(2 * NR * NP)
+    rho0[: NR * NP] = np.random.default_rng(3).random(NR * NP)
+    rho0 /= rho0.sum()
+    times = [0.4, 2.0]
+    a, _ = oracle.expv(auto, rho0, times, mode=oracle.TOL, tol=1e-16)
+    b, _ = oracle.expv(mp, rho0[: NR * NP], times, mode=oracle.TOL, tol=1e-16)
+    assert np.abs(a[:, : NR * NP] - b).max() <= 1e-14
+    assert not a[:, NR * NP:].any()
+
+
+def test_autoreg_series_matches_expm_and_gillespie():
+    NR, NP = 6, 8
+    th = [4.0, 0.6, 1.0, 0.2, 0.8, 0.3]
+    csr = oracle.build_model(oracle.AUTOREG, [NR, NP], th)
+    rho0 = synth.delta(2 * NR * NP, 0)
+    out, _ = oracle.expv(csr, rho0, [1.5], mode=oracle.TOL, tol=1e-16)
+    ref = rho0 @ scipy.linalg.expm(csr.dense_generator() * 1.5)
+    assert np.abs(out[0] - ref).max() <= 1e-12
+    counts = oracle.gillespie(csr, 0, [1.5], 200000, 11)[0]
+    keep = out[0] * 200000 > 20
+    chi2 = np.sum((counts[keep] - 200000 * out[0][keep]) ** 2 / (200000 * out[0][keep]))
+    assert stats.chi2.sf(chi2, keep.sum() - 1) > 1e-4
