@@ -342,6 +342,32 @@ def other_configs():
         mjp.loglik(am, aob, ath, out=alo)
         ms_a = _events_ms(lambda: mjp.loglik(am, aob, ath, out=alo), reps=3)
         res["autoreg_40x120_loglik_152"][name] = {"ms": ms_a, "loglik_evals_s": 152 / (ms_a / 1e3)}
+    # J-MJP state probabilities (Algorithm 1) on the two-state promoter
+    # (Sec. 3.1.2): 50 times x 100 cells, one observed n_R per cell and its own
+    # jump count k_i ~ Poisson(Omega T_i); beside the R-MJP log-likelihood of
+    # the same snapshots for the same theta.
+    pc = synth.twostate_promoter(300)
+    NR = pc["dims"][0]
+    psn = synth.gillespie_snapshots(pc["kind"], pc["dims"], pc["theta"], pc["times"], pc["cells"], synth.rng(6, 1))
+    pm = mjp.Model(pc["kind"], pc["dims"], pc["theta"], mjp.FP64)
+    pr0 = torch.tensor(pc["rho0"], dtype=torch.float64, device="cuda")
+    pT = np.repeat(pc["times"], pc["cells"])
+    b_, g_, la_, li_ = pc["theta"]
+    rr = np.arange(NR)
+    pomega = 1.1 * max(np.max(g_ * rr + b_ * (rr + 1 < NR) + li_), np.max(la_ + g_ * rr))
+    pk = synth.rng(6, 2).poisson(pomega * pT)
+    pgroups = [np.array([r, r + NR]) for smp in psn for r in smp[:, 0]]
+    pm.jmjp_probs(pr0, pk, pgroups)
+    ms_j = _events_ms(lambda: [pm.jmjp_probs(pr0, pk, pgroups) for _ in range(5)], reps=3) / 5
+    pob = mjp.Obs(2 * NR, pc["times"], synth.snapshot_obs(pc["kind"], pc["dims"], psn), pc["rho0"])
+    pth = torch.tensor([pc["theta"]], dtype=torch.float64, device="cuda")
+    plo = torch.empty(1, dtype=torch.float64, device="cuda")
+    mjp.loglik(pm, pob, pth, out=plo)
+    ms_r = _events_ms(lambda: [mjp.loglik(pm, pob, pth, out=plo) for _ in range(5)], reps=3) / 5
+    res["jmjp_promoter_300"] = {"observations": int(len(pk)), "max_k": int(pk.max()), "jmjp_ms_per_eval": ms_j,
+                                "rmjp_loglik_ms_per_theta": ms_r, "dtype": "f64",
+                                "note": "jmjp: one jmjp_state_probs call (host sort and copies, one CTA, "
+                                        "synchronised); rmjp: one loglik call for the same theta"}
     # Uneven batch of 4096 birth-death instances, autotuned, replayed as a CUDA graph.
     bc = synth.bd_batch()
     K = _bd_K(bc["N"], bc["theta"][:, 0], bc["theta"][:, 1], bc["t"])

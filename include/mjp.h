@@ -224,6 +224,24 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
 int rate_model_last_timing(mjp_model* m, double* ms_plan, double* ms_chain);
 
 /*
+ * J-MJP state probabilities (Method #2, Sec. 2.2.2, Algorithm 1): for the
+ * model's theta, phi[i] = sum over observation i's group of (rho0 B^{k[i]}),
+ * B = I + A / Omega, Omega = 1.1 max_n |a_nn| (Eq. B_def): one chain read at
+ * every observation's own number of virtual jumps.  Birth-death and
+ * two-state models (one CTA; the chain in shared memory).
+ *   rho0       device, N values in the model's precision.
+ *   k          host, nobs jump counts >= 0 (any order).
+ *   group_ptr  host, nobs + 1 (group_ptr[0] = 0): observation i sums the
+ *              states members[group_ptr[i] .. group_ptr[i+1]) (e.g. both gene
+ *              states of an observed n_R, Sec. 3.1.2); every group non-empty.
+ *   phi        host, nobs results (FP64).  Synchronises `stream`.
+ * Errors: MJP_ERR_ARG, MJP_ERR_UNSUPPORTED (other kinds, too many states),
+ * MJP_ERR_ALLOC, MJP_ERR_CUDA.
+ */
+int jmjp_state_probs(mjp_model* m, const void* rho0, int64_t nobs, const int64_t* k, const int64_t* group_ptr,
+                     const int32_t* members, double* phi, void* stream);
+
+/*
  * ---- batches of uneven instances --------------------------------------
  * Many birth-death models (Eq. BD_def) with different sizes N_j, rates
  * theta_j = {beta_j, gamma_j} and one observation time t_j each, rho0 =

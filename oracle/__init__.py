@@ -72,6 +72,9 @@ def _lib():
             lib.orc_expv.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_double, ctypes.c_double, _f64p, _f64p,
                                      _i64p, _f64p]
+            lib.orc_jmjp.restype = ctypes.c_int
+            lib.orc_jmjp.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, ctypes.c_int64, _i64p, _i64p,
+                                     _i32p, ctypes.c_double, _f64p]
             lib.orc_rk4.restype = ctypes.c_int
             lib.orc_rk4.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int, _f64p,
                                     _i64p, _f64p]
@@ -170,6 +173,23 @@ def expv(csr: CSR, rho0, times, mode: int = PAPER, tol: float = 0.0, omega_facto
     if rc != 0:
         raise ValueError(f"orc_expv failed ({rc})")
     return out, {"omega": om.value, "K": K[:nt].copy(), "eps": eps[:nt].copy()}
+
+
+def jmjp_probs(csr: CSR, rho0, k, groups, omega_factor: float = 1.1):
+    """phi_i = sum over group i of (rho0 B^{k_i}) (Algorithm 1, J-MJP): one
+    chain read at each observation's jump count.  groups: list of member
+    arrays (one per observation)."""
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    k = np.ascontiguousarray(k, dtype=np.int64)
+    gp = np.zeros(len(groups) + 1, np.int64)
+    gp[1:] = np.cumsum([len(g) for g in groups])
+    mem = np.ascontiguousarray(np.concatenate(groups) if len(groups) else np.zeros(0), dtype=np.int32)
+    phi = np.zeros(max(len(k), 1))
+    rc = _lib().orc_jmjp(csr.n, _p(csr.row_ptr, _i64p), _p(csr.col, _i32p), _p(csr.val, _f64p), _p(rho0, _f64p),
+                         len(k), _p(k, _i64p), _p(gp, _i64p), _p(mem, _i32p), float(omega_factor), _p(phi, _f64p))
+    if rc != 0:
+        raise ValueError(f"oracle jmjp failed ({rc})")
+    return phi[: len(k)]
 
 
 def rk4(csr: CSR, rho0, times):

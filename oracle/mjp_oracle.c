@@ -336,6 +336,64 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* J-MJP state probabilities (Method #2, Sec. 2.2.2, Algorithm 1)           */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * phi[i] = sum_{s in group i} (rho0 B^{k_i})_s for observations i < nobs,
+ * with B = I + A / Omega, Omega = omega_factor * max_n |a_nn| (Eq. B_def):
+ * one chain rho0 B^k, read at every observation's own jump count k_i
+ * (Algorithm 1's loop; a group sums a hidden component out, Sec. 3.1.2).
+ * If every rate is zero, B = I.
+ */
+int orc_jmjp(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+             const double* rho0, int64_t nobs, const int64_t* k, const int64_t* group_ptr,
+             const int32_t* members, double omega_factor, double* phi) {
+  if (n < 1 || nobs < 0 || !(omega_factor > 1.0)) return ORC_ERR_ARG;
+  int64_t kmax = 0;
+  for (int64_t i = 0; i < nobs; ++i) {
+    if (k[i] < 0) return ORC_ERR_ARG;
+    if (k[i] > kmax) kmax = k[i];
+  }
+  const double maxe = orc_max_exit(n, row_ptr, val);
+  const double omega = omega_factor * maxe;
+  double* bdiag = (double*)malloc(sizeof(double) * (size_t)n);
+  double* boff = (double*)malloc(sizeof(double) * (size_t)(row_ptr[n] > 0 ? row_ptr[n] : 1));
+  double* rho = (double*)malloc(sizeof(double) * (size_t)n);
+  double* nxt = (double*)malloc(sizeof(double) * (size_t)n);
+  int rc = ORC_OK;
+  if (!bdiag || !boff || !rho || !nxt) { rc = ORC_ERR_ALLOC; goto done; }
+  for (int64_t s = 0; s < n; ++s) {
+    double e = 0.0;
+    for (int64_t j = row_ptr[s]; j < row_ptr[s + 1]; ++j) {
+      e = e + val[j];
+      boff[j] = maxe > 0.0 ? val[j] / omega : 0.0;
+    }
+    bdiag[s] = maxe > 0.0 ? 1.0 - e / omega : 1.0;
+  }
+  memcpy(rho, rho0, sizeof(double) * (size_t)n);
+  for (int64_t kk = 0; kk <= kmax; ++kk) {
+    for (int64_t i = 0; i < nobs; ++i) {
+      if (k[i] != kk) continue;
+      double v = 0.0;
+      for (int64_t q = group_ptr[i]; q < group_ptr[i + 1]; ++q) v += rho[members[q]];
+      phi[i] = v;
+    }
+    if (kk == kmax) break;
+    for (int64_t s = 0; s < n; ++s) nxt[s] = 0.0;
+    for (int64_t s = 0; s < n; ++s) {
+      double r = rho[s];
+      nxt[s] += r * bdiag[s];
+      for (int64_t j = row_ptr[s]; j < row_ptr[s + 1]; ++j) nxt[col[j]] += r * boff[j];
+    }
+    double* tmp = rho; rho = nxt; nxt = tmp;
+  }
+done:
+  free(bdiag); free(boff); free(rho); free(nxt);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Fourth-order Runge-Kutta (Method #4, Sec. 2.3: Eqs. RKstep, RKintermediate)*/
 /* ------------------------------------------------------------------------ */
 

@@ -102,6 +102,20 @@ class Model:
     def check(self, stream=None):
         capi.check(capi.lib().rate_model_check(self._h, _stream_ptr(stream)))
 
+    def jmjp_probs(self, rho0, k, groups, stream=None):
+        """J-MJP state probabilities (Algorithm 1): phi_i = sum over groups[i]
+        of (rho0 B^{k_i}) for the model's theta; rho0 a device tensor."""
+        kk = np.ascontiguousarray(k, dtype=np.int64)
+        gp = np.zeros(len(groups) + 1, np.int64)
+        gp[1:] = np.cumsum([len(g) for g in groups])
+        mem = np.ascontiguousarray(np.concatenate(groups), dtype=np.int32)
+        phi = np.zeros(len(kk))
+        capi.check(capi.lib().jmjp_state_probs(self._h, ctypes.c_void_p(rho0.data_ptr()), len(kk),
+                                               kk.ctypes.data_as(capi._i64p), gp.ctypes.data_as(capi._i64p),
+                                               mem.ctypes.data_as(capi._i32p), phi.ctypes.data_as(capi._f64p),
+                                               _stream_ptr(stream)))
+        return phi
+
     def last_timing(self):
         """(planner ms, chain ms) of the last call (needs OPT_PROFILE = 1)."""
         a, b = ctypes.c_double(), ctypes.c_double()

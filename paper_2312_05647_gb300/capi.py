@@ -89,6 +89,7 @@ SIGNATURES = {
     "expv_batch_tune": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_char_p, ctypes.c_int]),
     "expv_batch_check": (ctypes.c_int, [_vp, _vp]),
     "expv_batch_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64]),
+    "jmjp_state_probs": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _i64p, _i64p, _i32p, _f64p, _vp]),
     "expv_batch_destroy": (None, [_vp]),
     "expv_series_static": (ctypes.c_int, [ctypes.c_int, _i64p, ctypes.c_int, _f64p, ctypes.c_int, _vp, _f64p,
                                           ctypes.c_int, _vp, _vp]),

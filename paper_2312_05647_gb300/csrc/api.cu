@@ -54,6 +54,7 @@ struct mjp_model {
   int method = 0;  // MJP_OPT_METHOD
   int kappa = 20;  // MJP_OPT_KAPPA
   DevBuf d_kq;     // Krylov basis scratch
+  DevBuf d_jk, d_jorder, d_jgp, d_jmem, d_jphi;  // J-MJP observations
   int cluster = 0;
   int profile = 0;
   bool timed = false;
@@ -75,6 +76,7 @@ struct mjp_model {
     d_slice_ptr.release(); d_slice_len.release(); d_col.release(); d_val.release(); d_diag.release();
     d_perm.release(); d_rho2.release(); d_outp.release(); d_wtab.release(); d_woff.release();
     d_L.release(); d_K.release();
+    d_kq.release(); d_jk.release(); d_jorder.release(); d_jgp.release(); d_jmem.release(); d_jphi.release();
     d_times.release(); d_orig.release(); d_win.release(); d_info.release();
     d_theta.release(); d_comp.release(); d_status.release(); d_ll.release();
     for (auto& e : ev)
@@ -730,6 +732,86 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
     }
     return rate_model_check(m, stream);
   }
+  return MJP_OK;
+}
+
+int jmjp_state_probs(mjp_model* m, const void* rho0, int64_t nobs, const int64_t* k, const int64_t* group_ptr,
+                     const int32_t* members, double* phi, void* stream) {
+  if (!m || !rho0 || !k || !group_ptr || !members || !phi) return fail(MJP_ERR_ARG, "NULL argument");
+  if (m->kind != MJP_BD1D && m->kind != MJP_TWOSTATE)
+    return fail(MJP_ERR_UNSUPPORTED, "J-MJP probabilities are available for birth-death and two-state models");
+  if (m->N > jmjp_max_states(m->precision)) return fail(MJP_ERR_UNSUPPORTED, "state space too large for one CTA");
+  if (nobs < 1 || nobs > ((int64_t)1 << 31) - 1) return fail(MJP_ERR_ARG, "nobs out of range");
+  if (group_ptr[0] != 0) return fail(MJP_ERR_ARG, "group_ptr[0] must be 0");
+  for (int64_t i = 0; i < nobs; ++i) {
+    if (k[i] < 0) return fail(MJP_ERR_ARG, "jump counts must be >= 0");
+    if (group_ptr[i + 1] <= group_ptr[i]) return fail(MJP_ERR_ARG, "every group needs a member");
+  }
+  const int64_t nmem = group_ptr[nobs];
+  for (int64_t q = 0; q < nmem; ++q)
+    if (members[q] < 0 || members[q] >= m->N) return fail(MJP_ERR_ARG, "member state out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  // Omega = 1.1 max_n |a_nn| (Eq. B_def), each row summed in target order.
+  const double* th = m->theta.data();
+  double maxe = 0.0;
+  for (int64_t n = 0; n < m->N; ++n) {
+    double e = 0.0;
+    if (m->kind == MJP_BD1D) {
+      if (n >= 1) e = e + th[1] * (double)n;
+      if (n + 1 < m->N) e = e + th[0];
+    } else {
+      const int64_t sg = n / m->M, r = n - sg * m->M;
+      if (sg == 0) {
+        if (r >= 1) e = e + th[1] * (double)r;
+        if (r + 1 < m->M) e = e + th[0];
+        e = e + th[3];
+      } else {
+        e = e + th[2];
+        if (r >= 1) e = e + th[1] * (double)r;
+      }
+    }
+    if (e > maxe) maxe = e;
+  }
+  // Observations sorted by jump count (stable), groups in that order.
+  std::vector<int32_t> order(nobs);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return k[a] < k[b]; });
+  std::vector<int64_t> ks(nobs), gp(nobs + 1, 0);
+  std::vector<int32_t> mem((size_t)nmem);
+  for (int64_t o = 0; o < nobs; ++o) {
+    const int32_t i = order[o];
+    ks[o] = k[i];
+    const int64_t c = group_ptr[i + 1] - group_ptr[i];
+    std::copy(members + group_ptr[i], members + group_ptr[i + 1], mem.begin() + gp[o]);
+    gp[o + 1] = gp[o] + c;
+  }
+  int rc = 0;
+  if ((rc = m->d_jk.ensure(sizeof(int64_t) * nobs)) || (rc = m->d_jorder.ensure(sizeof(int32_t) * nobs)) ||
+      (rc = m->d_jgp.ensure(sizeof(int64_t) * (nobs + 1))) || (rc = m->d_jmem.ensure(sizeof(int32_t) * nmem)) ||
+      (rc = m->d_jphi.ensure(sizeof(double) * nobs)) || (rc = m->d_theta.ensure(sizeof(double) * m->theta.size())))
+    return rc;
+  MJP_CUDA(cudaMemcpyAsync(m->d_jk.p, ks.data(), sizeof(int64_t) * nobs, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_jorder.p, order.data(), sizeof(int32_t) * nobs, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_jgp.p, gp.data(), sizeof(int64_t) * (nobs + 1), cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_jmem.p, mem.data(), sizeof(int32_t) * nmem, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_theta.p, m->theta.data(), sizeof(double) * m->theta.size(), cudaMemcpyHostToDevice, s));
+  JmjpParams jp = {};
+  jp.theta = m->d_theta.as<double>();
+  jp.N = (int)m->N;
+  jp.M = (int)m->M;
+  jp.rho0 = rho0;
+  jp.nobs = nobs;
+  jp.ksorted = m->d_jk.as<int64_t>();
+  jp.order = m->d_jorder.as<int32_t>();
+  jp.group_ptr = m->d_jgp.as<int64_t>();
+  jp.members = m->d_jmem.as<int32_t>();
+  jp.phi = m->d_jphi.as<double>();
+  jp.omega = 1.1 * maxe;
+  if ((rc = mark(m, 0, s)) || (rc = mark(m, 1, s))) return rc;
+  MJP_CUDA(launch_jmjp(m->kind, m->precision, jp, s));
+  if ((rc = mark(m, 2, s))) return rc;
+  MJP_CUDA(cudaMemcpyAsync(phi, jp.phi, sizeof(double) * nobs, cudaMemcpyDeviceToHost, s));
+  MJP_CUDA(cudaStreamSynchronize(s));
   return MJP_OK;
 }
 

@@ -201,6 +201,21 @@ struct KrylovParams {
   double* Q;             // device scratch, kappa x N
   int* status;
 };
+// J-MJP state probabilities for one theta (jmjp.cu).
+struct JmjpParams {
+  const double* theta;       // device
+  int N, M;                  // states; M = N_R for the two-state model
+  const void* rho0;          // device, N values (T)
+  int64_t nobs;
+  const int64_t* ksorted;    // device, jump counts sorted ascending
+  const int32_t* order;      // device, sorted position -> caller's observation
+  const int64_t* group_ptr;  // device, nobs + 1 (sorted order)
+  const int32_t* members;    // device
+  double* phi;               // device, nobs (caller's order)
+  double omega;              // 1.1 max_n |a_nn|
+};
+int64_t jmjp_max_states(int precision);
+cudaError_t launch_jmjp(int kind, int precision, const JmjpParams& p, cudaStream_t s);
 int krylov_max_states();
 int krylov_max_kappa();
 cudaError_t launch_krylov_bd1d(const KrylovParams& p, cudaStream_t s);

@@ -520,3 +520,102 @@ def test_autoreg_series_matches_expm_and_gillespie():
     keep = out[0] * 200000 > 20
     chi2 = np.sum((counts[keep] - 200000 * out[0][keep]) ** 2 / (200000 * out[0][keep]))
     assert stats.chi2.sf(chi2, keep.sum() - 1) > 1e-4
+
+
+# --------------------------------------------------------------------------
+# J-MJP state probabilities (Method #2, Algorithm 1)
+# --------------------------------------------------------------------------
+
+def _twostate_generator_from_reactions(NR, th):
+    """Dense A of the two-state promoter (Sec. 3.1.2) from its reactions:
+    state (n_R, sigma), index n_R + N_R sigma, sigma 0 active; reflecting top."""
+    beta, gamma, la, li = th
+    A = np.zeros((2 * NR, 2 * NR))
+    for s in (0, 1):
+        for r in range(NR):
+            i = r + NR * s
+            if s == 0 and r + 1 < NR:
+                A[i, i + 1] += beta                    # transcription while active
+            if r >= 1:
+                A[i, i - 1] += gamma * r               # mRNA decay
+            A[i, r + NR * (1 - s)] += li if s == 0 else la  # promoter switching
+    A[np.diag_indices(2 * NR)] = -A.sum(axis=1)
+    return A
+
+
+def test_jmjp_two_state_ctmc_closed_form():
+    # B = I + A / Omega for a 2-state chain (rates a, b) has eigenvalues 1 and
+    # 1 - (a + b) / Omega: rho0 B^k = pi + (rho0 - pi)(1 - (a + b) / Omega)^k.
+    a, b = 3.0, 0.7
+    csr = oracle.CSR([0, 1, 2], [1, 0], [a, b])
+    rho0 = np.array([0.25, 0.75])
+    omega = 1.1 * max(a, b)
+    pi = np.array([b, a]) / (a + b)
+    ks = np.array([0, 1, 2, 7, 40, 3, 7])
+    phi0 = oracle.jmjp_probs(csr, rho0, ks, [np.array([0])] * len(ks))
+    phi1 = oracle.jmjp_probs(csr, rho0, ks, [np.array([1])] * len(ks))
+    lam = 1.0 - (a + b) / omega
+    for i, k in enumerate(ks):
+        ref = pi + (rho0 - pi) * lam ** int(k)
+        assert abs(phi0[i] - ref[0]) <= 1e-15 and abs(phi1[i] - ref[1]) <= 1e-15
+
+
+@pytest.mark.parametrize("kind,dims,theta", [(oracle.BD1D, [30], [6.0, 0.8]), (oracle.TWOSTATE, [15], [8.0, 1.0, 2.0, 1.0])])
+def test_jmjp_matches_dense_matrix_powers(kind, dims, theta):
+    # rho0 B^k by repeated dense products, A built from the reactions.
+    if kind == oracle.BD1D:
+        n = dims[0]
+        A = np.diag([theta[0]] * (n - 1), 1) + np.diag([theta[1] * r for r in range(1, n)], -1)
+        A[np.diag_indices(n)] = -A.sum(axis=1)
+    else:
+        A = _twostate_generator_from_reactions(dims[0], theta)
+    n = A.shape[0]
+    csr = oracle.build_model(kind, dims, theta)
+    omega = 1.1 * np.max(-np.diag(A))
+    B = np.eye(n) + A / omega
+    gen = np.random.default_rng(n)
+    rho0 = gen.random(n)
+    rho0 /= rho0.sum()
+    ks = gen.integers(0, 120, size=25)
+    ks[0] = 0
+    groups = [gen.choice(n, size=gen.integers(1, 4), replace=False) for _ in ks]
+    phi = oracle.jmjp_probs(csr, rho0, ks, groups)
+    for i, k in enumerate(ks):
+        ref = (rho0 @ np.linalg.matrix_power(B, int(k)))[groups[i]].sum()
+        assert abs(phi[i] - ref) <= 1e-13
+    assert phi[0] == rho0[groups[0]].sum()          # k = 0 reads rho0 itself
+
+
+def test_jmjp_poisson_mixture_is_the_transient_distribution():
+    # Sum_k Poisson(k; Omega t) rho0 B^k = rho0 exp(A t) (Eq. ME_uniform): the
+    # J-MJP chain at every k, mixed with Poisson weights, is the ME solution.
+    NR, th, t = 12, [5.0, 1.0, 2.0, 1.0], 1.3
+    A = _twostate_generator_from_reactions(NR, th)
+    csr = oracle.build_model(oracle.TWOSTATE, [NR], th)
+    omega = 1.1 * np.max(-np.diag(A))
+    rho0 = synth.delta(2 * NR, 0)
+    kmax = int(omega * t + 40 * math.sqrt(omega * t)) + 40
+    ks = np.repeat(np.arange(kmax + 1), 2 * NR)
+    groups = [np.array([s]) for s in np.tile(np.arange(2 * NR), kmax + 1)]
+    phi = oracle.jmjp_probs(csr, rho0, ks, groups).reshape(kmax + 1, 2 * NR)
+    w = stats.poisson.pmf(np.arange(kmax + 1), omega * t)
+    ref = rho0 @ scipy.linalg.expm(A * t)
+    assert np.abs(w @ phi - ref).max() <= 1e-13
+
+
+def test_jmjp_order_and_grouping():
+    csr = oracle.build_model(oracle.TWOSTATE, [20], [30.0, 1.0, 2.0, 1.0])
+    rho0 = synth.delta(40, 0)
+    ks = np.array([50, 3, 50, 0, 17])
+    groups = [np.array([r, r + 20]) for r in (4, 1, 9, 0, 12)]
+    phi = oracle.jmjp_probs(csr, rho0, ks, groups)
+    perm = np.array([4, 2, 0, 3, 1])
+    phi_p = oracle.jmjp_probs(csr, rho0, ks[perm], [groups[i] for i in perm])
+    assert np.array_equal(phi_p, phi[perm])
+    # A group of both gene states is the sum of its two singletons.
+    a = oracle.jmjp_probs(csr, rho0, ks, [g[:1] for g in groups])
+    b = oracle.jmjp_probs(csr, rho0, ks, [g[1:] for g in groups])
+    assert np.abs(a + b - phi).max() <= 1e-16
+    # All states at any k: B is stochastic, the mass stays 1.
+    allg = [np.arange(40)] * 3
+    assert np.abs(oracle.jmjp_probs(csr, rho0, [0, 200, 1000], allg) - 1.0).max() <= 1e-13
