@@ -55,6 +55,7 @@ struct mjp_model {
   int kappa = 20;  // MJP_OPT_KAPPA
   DevBuf d_kq;     // Krylov basis scratch
   DevBuf d_jk, d_jorder, d_jgp, d_jmem, d_jphi;  // J-MJP observations
+  DevBuf d_jmap;                                  // loglik: cluster -> theta, longest chain first
   int cluster = 0;
   int profile = 0;
   bool timed = false;
@@ -77,6 +78,7 @@ struct mjp_model {
     d_perm.release(); d_rho2.release(); d_outp.release(); d_wtab.release(); d_woff.release();
     d_L.release(); d_K.release();
     d_kq.release(); d_jk.release(); d_jorder.release(); d_jgp.release(); d_jmem.release(); d_jphi.release();
+    d_jmap.release();
     d_times.release(); d_orig.release(); d_win.release(); d_info.release();
     d_theta.release(); d_comp.release(); d_status.release(); d_ll.release();
     for (auto& e : ev)
@@ -950,6 +952,7 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   if ((rc = ensure_status(m))) return rc;
   if ((rc = m->d_win.ensure(sizeof(Win) * (size_t)nt * B))) return rc;
   if ((rc = m->d_info.ensure(sizeof(JobInfo) * (size_t)B))) return rc;
+  if ((rc = m->d_jmap.ensure(sizeof(int32_t) * (size_t)B))) return rc;
   const double* d_theta = theta;
   double* d_out = out;
   if (where == MJP_PTR_HOST) {
@@ -969,6 +972,9 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   if ((rc = arena_prepare(m, where == MJP_PTR_HOST ? theta : nullptr, B, obs->times.data(), nt, s, pp))) return rc;
   if ((rc = mark(m, 0, s))) return rc;
   MJP_CUDA(launch_plan(pp, s));
+  // Chains of different theta differ in length (K grows with Omega): start
+  // the longest first so the last wave of clusters holds the short ones.
+  if (B > 1) MJP_CUDA(launch_order_jobs(pp.info, B, m->d_jmap.as<int32_t>(), s));
   if ((rc = mark(m, 1, s))) return rc;
 
   ChainParams cp = {};
@@ -982,6 +988,7 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   cp.G = obs->G; cp.nmem = nmem_list; cp.ll = d_out;
   cp.renorm = (m->precision == MJP_FP32) ? m->renorm : 0;
   cp.slab = slab; cp.status = pp.status;
+  cp.job_map = B > 1 ? m->d_jmap.as<int32_t>() : nullptr;
   if (use_reg) MJP_CUDA(launch_chain_reg2d(cp, rp, s));
   else MJP_CUDA(launch_chain_stencil(m->kind, m->precision, 1, cp, C, T, s));
   if ((rc = mark(m, 2, s))) return rc;

@@ -149,6 +149,8 @@ struct Rk4Params {
 // Host-side launchers implemented in the .cu files.
 namespace mjp {
 cudaError_t launch_plan(const PlanParams& p, cudaStream_t s);
+// map[r] = job with the r-th largest Kmax (ties by index): longest chain first.
+cudaError_t launch_order_jobs(const JobInfo* info, int B, int32_t* map, cudaStream_t s);
 cudaError_t launch_chain_stencil(int kind, int precision, int loglik_mode, const ChainParams& p,
                                  int cluster, int threads, cudaStream_t s);
 int64_t chain_stencil_slab(int kind, int64_t M, int64_t P, int cluster);

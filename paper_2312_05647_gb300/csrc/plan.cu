@@ -288,11 +288,34 @@ __global__ void __launch_bounds__(256) plan_kernel(PlanParams p) {
   }
 }
 
+// Longest chain first: map[r] = the job of rank r by decreasing Kmax (ties
+// by index), so clusters that start in later waves carry the short chains.
+// Each thread ranks one job against all others (a strict total order, so the
+// map is a permutation whatever the keys hold).
+__global__ void order_jobs_kernel(const JobInfo* info, int B, int32_t* map) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B; i += gridDim.x * blockDim.x) {
+    const int64_t ki = info[i].Kmax;
+    int r = 0;
+    for (int j = 0; j < B; ++j) {
+      const int64_t kj = info[j].Kmax;
+      r += (kj > ki || (kj == ki && j < i)) ? 1 : 0;
+    }
+    map[r] = i;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_plan(const PlanParams& p, cudaStream_t s) {
   if (p.B <= 0) return cudaSuccess;
   plan_kernel<<<p.B, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order_jobs(const JobInfo* info, int B, int32_t* map, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const int blocks = (B + 255) / 256 < 1024 ? (B + 255) / 256 : 1024;
+  order_jobs_kernel<<<blocks, 256, 0, s>>>(info, B, map);
   return cudaGetLastError();
 }
 

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
-  const int job = blockIdx.x / C;
+  const int job = p.job_map ? p.job_map[blockIdx.x / C] : (int)(blockIdx.x / C);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int nt = p.ntimes;
   const int M = p.M, P = p.P;
