@@ -356,18 +356,31 @@ def other_configs():
     rr = np.arange(NR)
     pomega = 1.1 * max(np.max(g_ * rr + b_ * (rr + 1 < NR) + li_), np.max(la_ + g_ * rr))
     pk = synth.rng(6, 2).poisson(pomega * pT)
-    pgroups = [np.array([r, r + NR]) for smp in psn for r in smp[:, 0]]
+    nr_obs = np.concatenate([smp[:, 0] for smp in psn])
+    pgroups = (np.arange(0, 2 * len(nr_obs) + 1, 2), np.stack([nr_obs, nr_obs + NR], axis=1).ravel())
+    pm.set_option(mjp.OPT_PROFILE, 1)
     pm.jmjp_probs(pr0, pk, pgroups)
     ms_j = _events_ms(lambda: [pm.jmjp_probs(pr0, pk, pgroups) for _ in range(5)], reps=3) / 5
+    ms_jk = pm.last_timing()[1]
+    pm.set_option(mjp.OPT_PROFILE, 0)
     pob = mjp.Obs(2 * NR, pc["times"], synth.snapshot_obs(pc["kind"], pc["dims"], psn), pc["rho0"])
     pth = torch.tensor([pc["theta"]], dtype=torch.float64, device="cuda")
     plo = torch.empty(1, dtype=torch.float64, device="cuda")
     mjp.loglik(pm, pob, pth, out=plo)
     ms_r = _events_ms(lambda: [mjp.loglik(pm, pob, pth, out=plo) for _ in range(5)], reps=3) / 5
-    res["jmjp_promoter_300"] = {"observations": int(len(pk)), "max_k": int(pk.max()), "jmjp_ms_per_eval": ms_j,
-                                "rmjp_loglik_ms_per_theta": ms_r, "dtype": "f64",
-                                "note": "jmjp: one jmjp_state_probs call (host sort and copies, one CTA, "
-                                        "synchronised); rmjp: one loglik call for the same theta"}
+    pm32 = mjp.Model(pc["kind"], pc["dims"], pc["theta"], mjp.FP32)
+    pr32 = pr0.float()
+    pm32.set_option(mjp.OPT_PROFILE, 1)
+    pm32.jmjp_probs(pr32, pk, pgroups)
+    ms_j32 = _events_ms(lambda: [pm32.jmjp_probs(pr32, pk, pgroups) for _ in range(5)], reps=3) / 5
+    ms_jk32 = pm32.last_timing()[1]
+    res["jmjp_promoter_300"] = {"observations": int(len(pk)), "max_k": int(pk.max()),
+                                "f64": {"call_ms": ms_j, "kernel_ms": ms_jk},
+                                "f32": {"call_ms": ms_j32, "kernel_ms": ms_jk32},
+                                "rmjp_loglik_ms_per_theta_f64": ms_r,
+                                "note": "call: one jmjp_state_probs call (host sort, chunking and copies, one CTA, "
+                                        "synchronised); kernel: CUDA events around the J-MJP kernel; rmjp: one "
+                                        "loglik call for the same theta"}
     # Uneven batch of 4096 birth-death instances, autotuned, replayed as a CUDA graph.
     bc = synth.bd_batch()
     K = _bd_K(bc["N"], bc["theta"][:, 0], bc["theta"][:, 1], bc["t"])

@@ -228,9 +228,10 @@ int rate_model_last_timing(mjp_model* m, double* ms_plan, double* ms_chain);
  * model's theta, phi[i] = sum over observation i's group of (rho0 B^{k[i]}),
  * B = I + A / Omega, Omega = 1.1 max_n |a_nn| (Eq. B_def): one chain read at
  * every observation's own number of virtual jumps.  Birth-death and
- * two-state models (one CTA; the chain in shared memory).
+ * two-state models (one CTA; the chain in shared memory, the observations
+ * staged beside it in chunks sorted by k).
  *   rho0       device, N values in the model's precision.
- *   k          host, nobs jump counts >= 0 (any order).
+ *   k          host, nobs jump counts in [0, 2^31 - 1) (any order).
  *   group_ptr  host, nobs + 1 (group_ptr[0] = 0): observation i sums the
  *              states members[group_ptr[i] .. group_ptr[i+1]) (e.g. both gene
  *              states of an observed n_R, Sec. 3.1.2); every group non-empty.

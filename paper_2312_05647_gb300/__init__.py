@@ -104,11 +104,17 @@ class Model:
 
     def jmjp_probs(self, rho0, k, groups, stream=None):
         """J-MJP state probabilities (Algorithm 1): phi_i = sum over groups[i]
-        of (rho0 B^{k_i}) for the model's theta; rho0 a device tensor."""
+        of (rho0 B^{k_i}) for the model's theta; rho0 a device tensor.  groups:
+        a list of member arrays, or the flat pair (group_ptr, members) with
+        group_ptr[0] = 0 and len(group_ptr) = len(k) + 1."""
         kk = np.ascontiguousarray(k, dtype=np.int64)
-        gp = np.zeros(len(groups) + 1, np.int64)
-        gp[1:] = np.cumsum([len(g) for g in groups])
-        mem = np.ascontiguousarray(np.concatenate(groups), dtype=np.int32)
+        if isinstance(groups, tuple) and len(groups) == 2 and np.ndim(groups[0]) == 1 and len(groups[0]) == len(kk) + 1:
+            gp = np.ascontiguousarray(groups[0], dtype=np.int64)
+            mem = np.ascontiguousarray(groups[1], dtype=np.int32)
+        else:
+            gp = np.zeros(len(groups) + 1, np.int64)
+            gp[1:] = np.cumsum([len(g) for g in groups])
+            mem = np.ascontiguousarray(np.concatenate(groups), dtype=np.int32)
         phi = np.zeros(len(kk))
         capi.check(capi.lib().jmjp_state_probs(self._h, ctypes.c_void_p(rho0.data_ptr()), len(kk),
                                                kk.ctypes.data_as(capi._i64p), gp.ctypes.data_as(capi._i64p),

@@ -54,7 +54,7 @@ struct mjp_model {
   int method = 0;  // MJP_OPT_METHOD
   int kappa = 20;  // MJP_OPT_KAPPA
   DevBuf d_kq;     // Krylov basis scratch
-  DevBuf d_jk, d_jorder, d_jgp, d_jmem, d_jphi;  // J-MJP observations
+  DevBuf d_jk, d_jorder, d_jgp, d_jmem, d_jphi, d_jchunk;  // J-MJP observations
   DevBuf d_jmap;                                  // loglik: cluster -> theta, longest chain first
   int cluster = 0;
   int profile = 0;
@@ -77,7 +77,7 @@ struct mjp_model {
     d_slice_ptr.release(); d_slice_len.release(); d_col.release(); d_val.release(); d_diag.release();
     d_perm.release(); d_rho2.release(); d_outp.release(); d_wtab.release(); d_woff.release();
     d_L.release(); d_K.release();
-    d_kq.release(); d_jk.release(); d_jorder.release(); d_jgp.release(); d_jmem.release(); d_jphi.release();
+    d_kq.release(); d_jk.release(); d_jorder.release(); d_jgp.release(); d_jmem.release(); d_jphi.release(); d_jchunk.release();
     d_jmap.release();
     d_times.release(); d_orig.release(); d_win.release(); d_info.release();
     d_theta.release(); d_comp.release(); d_status.release(); d_ll.release();
@@ -775,40 +775,66 @@ int jmjp_state_probs(mjp_model* m, const void* rho0, int64_t nobs, const int64_t
     if (e > maxe) maxe = e;
   }
   // Observations sorted by jump count (stable), groups in that order.
+  for (int64_t i = 0; i < nobs; ++i)
+    if (k[i] > INT32_MAX - 1) return fail(MJP_ERR_UNSUPPORTED, "jump counts must be below 2^31 - 1");
+  if (nmem > INT32_MAX) return fail(MJP_ERR_ARG, "too many members");
   std::vector<int32_t> order(nobs);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return k[a] < k[b]; });
-  std::vector<int64_t> ks(nobs), gp(nobs + 1, 0);
+  std::vector<int32_t> ks(nobs), gp(nobs + 1, 0);
   std::vector<int32_t> mem((size_t)nmem);
   for (int64_t o = 0; o < nobs; ++o) {
     const int32_t i = order[o];
-    ks[o] = k[i];
+    ks[o] = (int32_t)k[i];
     const int64_t c = group_ptr[i + 1] - group_ptr[i];
     std::copy(members + group_ptr[i], members + group_ptr[i + 1], mem.begin() + gp[o]);
-    gp[o + 1] = gp[o] + c;
+    gp[o + 1] = gp[o] + (int32_t)c;
   }
+  // Chunks of sorted observations that fit the shared memory beside the chain:
+  // 12 bytes per observation (k, position, group offset) + 4 per member, the
+  // space split by the mean group size.
+  const size_t avail = jmjp_chunk_bytes(m->precision, (int)m->N);
+  const double mbar = (double)nmem / (double)nobs;
+  int64_t cap_obs = (int64_t)((double)(avail - 4) / (12.0 + 4.0 * mbar));
+  cap_obs = std::max<int64_t>(1, std::min<int64_t>(cap_obs, nobs));
+  const int64_t cap_mem = ((int64_t)avail - 4 - 12 * cap_obs) / 4;
+  std::vector<int32_t> chunk(1, 0);
+  for (int64_t o = 0; o < nobs;) {
+    const int64_t s0 = o;
+    int64_t used = 0;
+    while (o < nobs && o - s0 < cap_obs && used + (gp[o + 1] - gp[o]) <= cap_mem) used += gp[o + 1] - gp[o], ++o;
+    if (o == s0) return fail(MJP_ERR_UNSUPPORTED, "an observation group does not fit shared memory");
+    chunk.push_back((int32_t)o);
+  }
+  const int nchunks = (int)chunk.size() - 1;
   int rc = 0;
-  if ((rc = m->d_jk.ensure(sizeof(int64_t) * nobs)) || (rc = m->d_jorder.ensure(sizeof(int32_t) * nobs)) ||
-      (rc = m->d_jgp.ensure(sizeof(int64_t) * (nobs + 1))) || (rc = m->d_jmem.ensure(sizeof(int32_t) * nmem)) ||
-      (rc = m->d_jphi.ensure(sizeof(double) * nobs)) || (rc = m->d_theta.ensure(sizeof(double) * m->theta.size())))
+  if ((rc = m->d_jk.ensure(sizeof(int32_t) * nobs)) || (rc = m->d_jorder.ensure(sizeof(int32_t) * nobs)) ||
+      (rc = m->d_jgp.ensure(sizeof(int32_t) * (nobs + 1))) || (rc = m->d_jmem.ensure(sizeof(int32_t) * nmem)) ||
+      (rc = m->d_jphi.ensure(sizeof(double) * nobs)) || (rc = m->d_jchunk.ensure(sizeof(int32_t) * chunk.size())) ||
+      (rc = m->d_theta.ensure(sizeof(double) * m->theta.size())))
     return rc;
-  MJP_CUDA(cudaMemcpyAsync(m->d_jk.p, ks.data(), sizeof(int64_t) * nobs, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_jk.p, ks.data(), sizeof(int32_t) * nobs, cudaMemcpyHostToDevice, s));
   MJP_CUDA(cudaMemcpyAsync(m->d_jorder.p, order.data(), sizeof(int32_t) * nobs, cudaMemcpyHostToDevice, s));
-  MJP_CUDA(cudaMemcpyAsync(m->d_jgp.p, gp.data(), sizeof(int64_t) * (nobs + 1), cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_jgp.p, gp.data(), sizeof(int32_t) * (nobs + 1), cudaMemcpyHostToDevice, s));
   MJP_CUDA(cudaMemcpyAsync(m->d_jmem.p, mem.data(), sizeof(int32_t) * nmem, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_jchunk.p, chunk.data(), sizeof(int32_t) * chunk.size(), cudaMemcpyHostToDevice, s));
   MJP_CUDA(cudaMemcpyAsync(m->d_theta.p, m->theta.data(), sizeof(double) * m->theta.size(), cudaMemcpyHostToDevice, s));
   JmjpParams jp = {};
   jp.theta = m->d_theta.as<double>();
   jp.N = (int)m->N;
   jp.M = (int)m->M;
   jp.rho0 = rho0;
-  jp.nobs = nobs;
-  jp.ksorted = m->d_jk.as<int64_t>();
+  jp.nobs = (int)nobs;
+  jp.ksorted = m->d_jk.as<int32_t>();
   jp.order = m->d_jorder.as<int32_t>();
-  jp.group_ptr = m->d_jgp.as<int64_t>();
+  jp.group_ptr = m->d_jgp.as<int32_t>();
   jp.members = m->d_jmem.as<int32_t>();
   jp.phi = m->d_jphi.as<double>();
   jp.omega = 1.1 * maxe;
+  jp.nchunks = nchunks;
+  jp.chunk = m->d_jchunk.as<int32_t>();
+  jp.cap_obs = (int)cap_obs;
+  jp.cap_mem = (int)cap_mem;
   if ((rc = mark(m, 0, s)) || (rc = mark(m, 1, s))) return rc;
   MJP_CUDA(launch_jmjp(m->kind, m->precision, jp, s));
   if ((rc = mark(m, 2, s))) return rc;

@@ -208,15 +208,20 @@ struct JmjpParams {
   const double* theta;       // device
   int N, M;                  // states; M = N_R for the two-state model
   const void* rho0;          // device, N values (T)
-  int64_t nobs;
-  const int64_t* ksorted;    // device, jump counts sorted ascending
+  int nobs;
+  const int32_t* ksorted;    // device, jump counts sorted ascending
   const int32_t* order;      // device, sorted position -> caller's observation
-  const int64_t* group_ptr;  // device, nobs + 1 (sorted order)
+  const int32_t* group_ptr;  // device, nobs + 1 (sorted order)
   const int32_t* members;    // device
   double* phi;               // device, nobs (caller's order)
   double omega;              // 1.1 max_n |a_nn|
+  int nchunks;               // chunks of sorted observations staged in shared memory
+  const int32_t* chunk;      // device, nchunks + 1: first observation of each chunk
+  int cap_obs, cap_mem;      // shared-memory capacity of a chunk (observations, members)
 };
 int64_t jmjp_max_states(int precision);
+// Shared-memory bytes left for observation chunks beside the chain of N states.
+size_t jmjp_chunk_bytes(int precision, int N);
 cudaError_t launch_jmjp(int kind, int precision, const JmjpParams& p, cudaStream_t s);
 int krylov_max_states();
 int krylov_max_kappa();

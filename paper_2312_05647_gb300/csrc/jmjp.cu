@@ -4,9 +4,11 @@
 //
 // One CTA evolves the chain for one theta with rho double-buffered in shared
 // memory (birth-death and two-state models, the paper's J-MJP examples).  The
-// observations arrive sorted by k; after jump k every thread advances the same
-// pointer over the observations with k_i = k and the CTA reads their groups
-// (state-parallel sums from shared memory) before the next jump.
+// observations arrive sorted by k and cut into chunks that fit the rest of
+// shared memory (jump counts, caller positions, group offsets and members);
+// a chunk is copied in once, so the reads of jump k touch only shared memory:
+// every thread advances the same pointer over the chunk's observations with
+// k_i = k and the CTA sums their groups (FP64) before the next jump.
 #include "chain_common.cuh"
 #include "internal.cuh"
 
@@ -14,11 +16,21 @@ namespace mjp {
 
 namespace {
 
-template <typename T, int KIND>
+constexpr size_t kJmjpSmem = 227 * 1024 - 1024;  // dynamic shared memory per CTA at most
+
+__host__ __device__ inline size_t jmjp_rho_bytes(int N, size_t elt) { return align_up(2 * elt * (size_t)N, 16); }
+
+// R > 0: every thread holds the coefficients of its R states in registers
+// (N <= R x threads); R = 0 rebuilds them at every jump.
+template <typename T, int KIND, int R>
 __global__ void __launch_bounds__(1024, 1) jmjp_kernel(const JmjpParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* const buf0 = reinterpret_cast<T*>(smem);
   T* const buf1 = buf0 + p.N;
+  int32_t* const s_k = reinterpret_cast<int32_t*>(smem + jmjp_rho_bytes(p.N, sizeof(T)));
+  int32_t* const s_ord = s_k + p.cap_obs;
+  int32_t* const s_gp = s_ord + p.cap_obs;
+  int32_t* const s_mem = s_gp + p.cap_obs + 1;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int N = p.N, NR = p.M;
   const double inv = p.omega > 0.0 ? 1.0 / p.omega : 0.0;
@@ -26,41 +38,101 @@ __global__ void __launch_bounds__(1024, 1) jmjp_kernel(const JmjpParams p) {
   const T la = KIND == MJP_TWOSTATE ? (T)(p.theta[2] * inv) : (T)0;
   const T li = KIND == MJP_TWOSTATE ? (T)(p.theta[3] * inv) : (T)0;
   const T one = (T)1;
-  for (int n = tid; n < N; n += nthr) buf0[n] = reinterpret_cast<const T*>(p.rho0)[n];
-  __syncthreads();
-  int64_t ptr = 0;
-  for (int64_t k = 0;; ++k) {
-    const T* cur = (k & 1) ? buf1 : buf0;
-    // Observations with k_i = k, in sorted order.
-    int64_t hi = ptr;
-    while (hi < p.nobs && p.ksorted[hi] == k) ++hi;
-    for (int64_t o = ptr + tid; o < hi; o += nthr) {
-      double v = 0.0;
-      for (int64_t q = p.group_ptr[o]; q < p.group_ptr[o + 1]; ++q) v += (double)cur[p.members[q]];
-      p.phi[p.order[o]] = v;
+  // Coefficients of state n in the gather form of rho B: y_n = d_n rho_n +
+  // b rho_{n-1} + g_n rho_{n+1} (+ s rho_sw, the other gene state), built once
+  // (the same operations as Eq. B_def's entries) and reused at every jump.
+  struct Cf {
+    T d, b, g, s;
+    int lo, hi, sw;
+  };
+  auto coef = [&](int n) {
+    Cf c;
+    if (KIND == MJP_BD1D) {
+      const T fn = (T)n;
+      c.d = f_sub(one, f_add(f_mul(g, fn), n + 1 < N ? b : (T)0));
+      c.b = b;
+      c.lo = n >= 1 ? n - 1 : -1;
+      c.g = n + 1 < N ? f_mul(g, f_add(fn, one)) : (T)0;
+      c.hi = n + 1 < N ? n + 1 : -1;
+      c.s = (T)0;
+      c.sw = n;
+    } else {  // two-state: n = n_R + sigma N_R, sigma 0 active
+      const int sg = n >= NR ? 1 : 0, r = n - sg * NR;
+      const T fr = (T)r;
+      const T e = sg == 0 ? f_add(f_add(f_mul(g, fr), r + 1 < NR ? b : (T)0), li) : f_add(la, f_mul(g, fr));
+      c.d = f_sub(one, e);
+      c.b = b;
+      c.lo = (sg == 0 && r >= 1) ? n - 1 : -1;                 // birth from r-1
+      c.g = r + 1 < NR ? f_mul(g, f_add(fr, one)) : (T)0;      // death from r+1
+      c.hi = r + 1 < NR ? n + 1 : -1;
+      c.s = sg == 0 ? la : li;                                 // switching in
+      c.sw = sg == 0 ? n + NR : n - NR;
     }
-    ptr = hi;
-    if (ptr >= p.nobs) break;
+    return c;
+  };
+  Cf cf[R > 0 ? R : 1];
+#pragma unroll
+  for (int j = 0; j < (R > 0 ? R : 1); ++j) cf[j] = coef(min(tid + j * nthr, N - 1));
+  for (int n = tid; n < N; n += nthr) buf0[n] = reinterpret_cast<const T*>(p.rho0)[n];
+  // Chunk c: sorted observations [chunk[c], chunk[c+1]) and their members.
+  int c = 0, cn = 0, lp = 0;
+  auto load_chunk = [&](int cc) {
+    const int o0 = p.chunk[cc], o1 = p.chunk[cc + 1];
+    const int m0 = p.group_ptr[o0], m1 = p.group_ptr[o1];
+    for (int i = tid; i < o1 - o0; i += nthr) {
+      s_k[i] = p.ksorted[o0 + i];
+      s_ord[i] = p.order[o0 + i];
+    }
+    for (int i = tid; i <= o1 - o0; i += nthr) s_gp[i] = p.group_ptr[o0 + i] - m0;
+    for (int i = tid; i < m1 - m0; i += nthr) s_mem[i] = p.members[m0 + i];
+    cn = o1 - o0;
+  };
+  load_chunk(0);
+  __syncthreads();
+  for (int k = 0;; ++k) {
+    const T* cur = (k & 1) ? buf1 : buf0;
+    // Observations with k_i = k, in sorted order (possibly across chunks).
+    for (;;) {
+      if (lp == cn && c + 1 < p.nchunks) {
+        __syncthreads();  // every read of the old chunk is done
+        load_chunk(++c);
+        lp = 0;
+        __syncthreads();
+      }
+      int hi = lp;
+      while (hi < cn && s_k[hi] == k) ++hi;
+      for (int o = lp + tid; o < hi; o += nthr) {
+        double v = 0.0;
+        for (int q = s_gp[o]; q < s_gp[o + 1]; ++q) v += (double)cur[s_mem[q]];
+        p.phi[s_ord[o]] = v;
+      }
+      lp = hi;
+      if (lp < cn || c + 1 >= p.nchunks) break;
+    }
+    if (lp >= cn && c + 1 >= p.nchunks) break;  // every observation read
     // rho <- rho B (gather form, rates into n scaled by 1/Omega).
     T* nxt = (k & 1) ? buf0 : buf1;
-    for (int n = tid; n < N; n += nthr) {
-      T y;
-      if (KIND == MJP_BD1D) {
-        const T fn = (T)n;
-        const T e = f_add(f_mul(g, fn), n + 1 < N ? b : (T)0);
-        y = f_mul(f_sub(one, e), cur[n]);
-        if (n >= 1) y = f_fma(b, cur[n - 1], y);
-        if (n + 1 < N) y = f_fma(f_mul(g, f_add(fn, one)), cur[n + 1], y);
-      } else {  // two-state: n = n_R + sigma N_R, sigma 0 active
-        const int sg = n >= NR ? 1 : 0, r = n - sg * NR;
-        const T fr = (T)r;
-        const T e = sg == 0 ? f_add(f_add(f_mul(g, fr), r + 1 < NR ? b : (T)0), li) : f_add(la, f_mul(g, fr));
-        y = f_mul(f_sub(one, e), cur[n]);
-        if (sg == 0 && r >= 1) y = f_fma(b, cur[n - 1], y);                        // birth from r-1
-        if (r + 1 < NR) y = f_fma(f_mul(g, f_add(fr, one)), cur[n + 1], y);        // death from r+1
-        y = f_fma(sg == 0 ? la : li, cur[sg == 0 ? n + NR : n - NR], y);           // switching in
+    if (R > 0) {
+#pragma unroll
+      for (int j = 0; j < (R > 0 ? R : 1); ++j) {
+        const int n = tid + j * nthr;
+        if (n < N) {
+          T y = f_mul(cf[j].d, cur[n]);
+          if (cf[j].lo >= 0) y = f_fma(cf[j].b, cur[cf[j].lo], y);
+          if (cf[j].hi >= 0) y = f_fma(cf[j].g, cur[cf[j].hi], y);
+          if (KIND == MJP_TWOSTATE) y = f_fma(cf[j].s, cur[cf[j].sw], y);
+          nxt[n] = y;
+        }
       }
-      nxt[n] = y;
+    } else {
+      for (int n = tid; n < N; n += nthr) {
+        const Cf c = coef(n);
+        T y = f_mul(c.d, cur[n]);
+        if (c.lo >= 0) y = f_fma(c.b, cur[c.lo], y);
+        if (c.hi >= 0) y = f_fma(c.g, cur[c.hi], y);
+        if (KIND == MJP_TWOSTATE) y = f_fma(c.s, cur[c.sw], y);
+        nxt[n] = y;
+      }
     }
     __syncthreads();
   }
@@ -68,9 +140,10 @@ __global__ void __launch_bounds__(1024, 1) jmjp_kernel(const JmjpParams p) {
 
 template <typename T, int KIND>
 cudaError_t launch_jmjp_typed(const JmjpParams& p, cudaStream_t s) {
-  const size_t smem = 2 * sizeof(T) * (size_t)p.N;
-  auto kern = jmjp_kernel<T, KIND>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = jmjp_rho_bytes(p.N, sizeof(T)) + 4 * (3 * (size_t)p.cap_obs + 1 + (size_t)p.cap_mem);
+  if (smem > kJmjpSmem) return cudaErrorInvalidValue;
+  auto kern = p.N <= 1024 ? jmjp_kernel<T, KIND, 1> : p.N <= 4096 ? jmjp_kernel<T, KIND, 4> : jmjp_kernel<T, KIND, 0>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJmjpSmem);
   if (e != cudaSuccess) return e;
   const int threads = p.N >= 1024 ? 1024 : (p.N + 31) / 32 * 32;
   kern<<<1, threads, smem, s>>>(p);
@@ -79,7 +152,16 @@ cudaError_t launch_jmjp_typed(const JmjpParams& p, cudaStream_t s) {
 
 }  // namespace
 
-int64_t jmjp_max_states(int precision) { return (int64_t)(227 * 1024 - 1024) / (2 * (precision == MJP_FP64 ? 8 : 4)); }
+// Leaves room for chunks of at least 256 observations of 4 members.
+int64_t jmjp_max_states(int precision) {
+  const size_t elt = precision == MJP_FP64 ? 8 : 4;
+  return (int64_t)((kJmjpSmem - 4 * (3 * 256 + 1 + 1024)) / (2 * elt)) / 4 * 4;
+}
+
+size_t jmjp_chunk_bytes(int precision, int N) {
+  const size_t used = jmjp_rho_bytes(N, precision == MJP_FP64 ? 8 : 4);
+  return used < kJmjpSmem ? kJmjpSmem - used : 0;
+}
 
 cudaError_t launch_jmjp(int kind, int precision, const JmjpParams& p, cudaStream_t s) {
   if (p.nobs <= 0) return cudaSuccess;

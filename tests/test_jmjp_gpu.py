@@ -56,6 +56,25 @@ def test_jmjp_matches_oracle(prec, kind, dims, theta, kmax, nobs):
     assert np.abs(got - ref).max() <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", [2, 1])
+@pytest.mark.parametrize("kind,dims,theta,kmax,nobs", [
+    (synth.TWOSTATE, [300], [100.0, 1.0, 2.0, 1.0], 1500, 30000),   # several chunks of observations
+    (synth.BD1D, [14000], [3000.0, 1.0], 150, 1200),                # a chain filling shared memory
+])
+def test_jmjp_chunked_observations(prec, kind, dims, theta, kmax, nobs):
+    # More observations than one shared-memory chunk holds: equal jump counts
+    # straddle the chunk boundaries.
+    N = synth.n_states(kind, dims)
+    gen = np.random.default_rng(nobs)
+    rho0 = gen.random(N)
+    rho0 /= rho0.sum()
+    ks = np.sort(gen.integers(0, kmax + 1, size=nobs))[gen.permutation(nobs)]
+    groups = [gen.choice(N, size=gen.integers(1, 4), replace=False) for _ in range(nobs)]
+    got = _gpu(kind, dims, theta, rho0, ks, groups, prec)
+    ref = oracle.jmjp_probs(oracle.build_model(kind, dims, theta), rho0, ks, groups)
+    assert np.abs(got - ref).max() <= TOL[prec]
+
+
 def test_jmjp_promoter_snapshots():
     # Jump counts drawn as in Sec. 2.2.2: k_i ~ Poisson(Omega T_i) at the
     # promoter's collection times, one observed n_R per cell (both gene states).
@@ -70,6 +89,9 @@ def test_jmjp_promoter_snapshots():
     got = _gpu(cfg["kind"], cfg["dims"], cfg["theta"], cfg["rho0"], ks, groups, 2)
     ref = oracle.jmjp_probs(csr, cfg["rho0"], ks, groups)
     assert np.abs(got - ref).max() <= 1e-12
+    # The same groups passed flat as (group_ptr, members).
+    flat = (np.arange(0, 2 * len(ks) + 1, 2), np.concatenate(groups))
+    np.testing.assert_array_equal(_gpu(cfg["kind"], cfg["dims"], cfg["theta"], cfg["rho0"], ks, flat, 2), got)
 
 
 def test_jmjp_refusals():
@@ -87,6 +109,8 @@ def test_jmjp_refusals():
     big = mjp.Model(synth.BD1D, [40000], [2.0, 1.0], mjp.FP64)
     with pytest.raises(MJPError):
         big.jmjp_probs(torch.tensor(synth.delta(40000, 0), device="cuda"), [3], [np.array([0])])
+    with pytest.raises(MJPError):
+        m.jmjp_probs(r, [2 ** 31], [np.array([0])])    # jump counts below 2^31 - 1
     two_d = mjp.Model(synth.MRNA_PROT2D, [10, 10], [5.0, 1.0, 1.0, 0.2], mjp.FP64)
     with pytest.raises(MJPError):
         two_d.jmjp_probs(torch.tensor(synth.delta(100, 0), device="cuda"), [3], [np.array([0])])
