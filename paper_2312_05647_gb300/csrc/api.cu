@@ -835,6 +835,7 @@ int jmjp_state_probs(mjp_model* m, const void* rho0, int64_t nobs, const int64_t
   jp.chunk = m->d_jchunk.as<int32_t>();
   jp.cap_obs = (int)cap_obs;
   jp.cap_mem = (int)cap_mem;
+  jp.kmax = ks[nobs - 1];
   if ((rc = mark(m, 0, s)) || (rc = mark(m, 1, s))) return rc;
   MJP_CUDA(launch_jmjp(m->kind, m->precision, jp, s));
   if ((rc = mark(m, 2, s))) return rc;

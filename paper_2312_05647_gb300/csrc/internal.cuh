@@ -218,6 +218,7 @@ struct JmjpParams {
   int nchunks;               // chunks of sorted observations staged in shared memory
   const int32_t* chunk;      // device, nchunks + 1: first observation of each chunk
   int cap_obs, cap_mem;      // shared-memory capacity of a chunk (observations, members)
+  int kmax;                  // largest jump count
 };
 int64_t jmjp_max_states(int precision);
 // Shared-memory bytes left for observation chunks beside the chain of N states.

@@ -6,9 +6,10 @@
 // memory (birth-death and two-state models, the paper's J-MJP examples).  The
 // observations arrive sorted by k and cut into chunks that fit the rest of
 // shared memory (jump counts, caller positions, group offsets and members);
-// a chunk is copied in once, so the reads of jump k touch only shared memory:
-// every thread advances the same pointer over the chunk's observations with
-// k_i = k and the CTA sums their groups (FP64) before the next jump.
+// a chunk is copied in once, so the reads of jump k touch only shared memory.
+// One warp walks the sorted observations (a ballot finds those with k_i = k)
+// and sums their groups (FP64) from rho_k while the other warps form
+// rho_{k+1}; one CTA barrier per jump.
 #include "chain_common.cuh"
 #include "internal.cuh"
 
@@ -20,8 +21,10 @@ constexpr size_t kJmjpSmem = 227 * 1024 - 1024;  // dynamic shared memory per CT
 
 __host__ __device__ inline size_t jmjp_rho_bytes(int N, size_t elt) { return align_up(2 * elt * (size_t)N, 16); }
 
-// R > 0: every thread holds the coefficients of its R states in registers
-// (N <= R x threads); R = 0 rebuilds them at every jump.
+// Threads [0, nupd) update the chain (R > 0: each holds the coefficients of
+// its R states in registers, N <= R x nupd; R = 0 rebuilds them at every
+// jump); the last warp reads the observations of each jump and loads later
+// chunks, so those reads run beside the update instead of before it.
 template <typename T, int KIND, int R>
 __global__ void __launch_bounds__(1024, 1) jmjp_kernel(const JmjpParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -31,7 +34,9 @@ __global__ void __launch_bounds__(1024, 1) jmjp_kernel(const JmjpParams p) {
   int32_t* const s_ord = s_k + p.cap_obs;
   int32_t* const s_gp = s_ord + p.cap_obs;
   int32_t* const s_mem = s_gp + p.cap_obs + 1;
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+  const int nupd = nthr - 32;
+  const bool reader = tid >= nupd;
   const int N = p.N, NR = p.M;
   const double inv = p.omega > 0.0 ? 1.0 / p.omega : 0.0;
   const T b = (T)(p.theta[0] * inv), g = (T)(p.theta[1] * inv);
@@ -71,67 +76,78 @@ __global__ void __launch_bounds__(1024, 1) jmjp_kernel(const JmjpParams p) {
     return c;
   };
   Cf cf[R > 0 ? R : 1];
+  if (!reader) {
 #pragma unroll
-  for (int j = 0; j < (R > 0 ? R : 1); ++j) cf[j] = coef(min(tid + j * nthr, N - 1));
+    for (int j = 0; j < (R > 0 ? R : 1); ++j) cf[j] = coef(min(tid + j * nupd, N - 1));
+  }
   for (int n = tid; n < N; n += nthr) buf0[n] = reinterpret_cast<const T*>(p.rho0)[n];
-  // Chunk c: sorted observations [chunk[c], chunk[c+1]) and their members.
-  int c = 0, cn = 0, lp = 0;
-  auto load_chunk = [&](int cc) {
+  // Chunk c: sorted observations [chunk[c], chunk[c+1]) and their members,
+  // copied by threads [t0, t0 + nt) (the whole CTA for chunk 0, later the reader).
+  auto load_chunk = [&](int cc, int t0, int nt) {
     const int o0 = p.chunk[cc], o1 = p.chunk[cc + 1];
     const int m0 = p.group_ptr[o0], m1 = p.group_ptr[o1];
-    for (int i = tid; i < o1 - o0; i += nthr) {
+    for (int i = tid - t0; i < o1 - o0; i += nt) {
       s_k[i] = p.ksorted[o0 + i];
       s_ord[i] = p.order[o0 + i];
     }
-    for (int i = tid; i <= o1 - o0; i += nthr) s_gp[i] = p.group_ptr[o0 + i] - m0;
-    for (int i = tid; i < m1 - m0; i += nthr) s_mem[i] = p.members[m0 + i];
-    cn = o1 - o0;
+    for (int i = tid - t0; i <= o1 - o0; i += nt) s_gp[i] = p.group_ptr[o0 + i] - m0;
+    for (int i = tid - t0; i < m1 - m0; i += nt) s_mem[i] = p.members[m0 + i];
+    return o1 - o0;
   };
-  load_chunk(0);
+  int c = 0, lp = 0;
+  int cn = load_chunk(0, 0, nthr);
   __syncthreads();
-  for (int k = 0;; ++k) {
+  for (int k = 0; k <= p.kmax; ++k) {
     const T* cur = (k & 1) ? buf1 : buf0;
-    // Observations with k_i = k, in sorted order (possibly across chunks).
-    for (;;) {
-      if (lp == cn && c + 1 < p.nchunks) {
-        __syncthreads();  // every read of the old chunk is done
-        load_chunk(++c);
-        lp = 0;
-        __syncthreads();
+    if (reader) {
+      // Observations with k_i = k: a prefix of the rest of the sorted list.
+      for (;;) {
+        if (lp == cn && c + 1 < p.nchunks) {
+          __syncwarp();  // the reader's reads of the old chunk are done
+          cn = load_chunk(++c, nupd, 32);
+          lp = 0;
+          __syncwarp();
+        }
+        int hi = lp;
+        for (;;) {
+          const int idx = hi + lane;
+          const unsigned bal = __ballot_sync(kFull, idx < cn && s_k[idx] == k);
+          const int run = bal == kFull ? 32 : __ffs(~bal) - 1;
+          hi += run;
+          if (run < 32) break;
+        }
+        for (int o = lp + lane; o < hi; o += 32) {
+          double v = 0.0;
+          for (int q = s_gp[o]; q < s_gp[o + 1]; ++q) v += (double)cur[s_mem[q]];
+          p.phi[s_ord[o]] = v;
+        }
+        lp = hi;
+        if (lp < cn || c + 1 >= p.nchunks) break;
       }
-      int hi = lp;
-      while (hi < cn && s_k[hi] == k) ++hi;
-      for (int o = lp + tid; o < hi; o += nthr) {
-        double v = 0.0;
-        for (int q = s_gp[o]; q < s_gp[o + 1]; ++q) v += (double)cur[s_mem[q]];
-        p.phi[s_ord[o]] = v;
-      }
-      lp = hi;
-      if (lp < cn || c + 1 >= p.nchunks) break;
-    }
-    if (lp >= cn && c + 1 >= p.nchunks) break;  // every observation read
-    // rho <- rho B (gather form, rates into n scaled by 1/Omega).
-    T* nxt = (k & 1) ? buf0 : buf1;
-    if (R > 0) {
+    } else if (k < p.kmax) {
+      // rho <- rho B (gather form, rates into n scaled by 1/Omega).
+      T* nxt = (k & 1) ? buf0 : buf1;
+      if (R > 0) {
 #pragma unroll
-      for (int j = 0; j < (R > 0 ? R : 1); ++j) {
-        const int n = tid + j * nthr;
-        if (n < N) {
-          T y = f_mul(cf[j].d, cur[n]);
-          if (cf[j].lo >= 0) y = f_fma(cf[j].b, cur[cf[j].lo], y);
-          if (cf[j].hi >= 0) y = f_fma(cf[j].g, cur[cf[j].hi], y);
-          if (KIND == MJP_TWOSTATE) y = f_fma(cf[j].s, cur[cf[j].sw], y);
+        for (int j = 0; j < (R > 0 ? R : 1); ++j) {
+          const int n = tid + j * nupd;
+          if (n < N) {
+            T y = f_mul(cf[j].d, cur[n]);
+            if (cf[j].lo >= 0) y = f_fma(cf[j].b, cur[cf[j].lo], y);
+            if (cf[j].hi >= 0) y = f_fma(cf[j].g, cur[cf[j].hi], y);
+            if (KIND == MJP_TWOSTATE) y = f_fma(cf[j].s, cur[cf[j].sw], y);
+            nxt[n] = y;
+          }
+        }
+      } else {
+        for (int n = tid; n < N; n += nupd) {
+          const Cf cc = coef(n);
+          T y = f_mul(cc.d, cur[n]);
+          if (cc.lo >= 0) y = f_fma(cc.b, cur[cc.lo], y);
+          if (cc.hi >= 0) y = f_fma(cc.g, cur[cc.hi], y);
+          if (KIND == MJP_TWOSTATE) y = f_fma(cc.s, cur[cc.sw], y);
           nxt[n] = y;
         }
-      }
-    } else {
-      for (int n = tid; n < N; n += nthr) {
-        const Cf c = coef(n);
-        T y = f_mul(c.d, cur[n]);
-        if (c.lo >= 0) y = f_fma(c.b, cur[c.lo], y);
-        if (c.hi >= 0) y = f_fma(c.g, cur[c.hi], y);
-        if (KIND == MJP_TWOSTATE) y = f_fma(c.s, cur[c.sw], y);
-        nxt[n] = y;
       }
     }
     __syncthreads();
@@ -142,11 +158,11 @@ template <typename T, int KIND>
 cudaError_t launch_jmjp_typed(const JmjpParams& p, cudaStream_t s) {
   const size_t smem = jmjp_rho_bytes(p.N, sizeof(T)) + 4 * (3 * (size_t)p.cap_obs + 1 + (size_t)p.cap_mem);
   if (smem > kJmjpSmem) return cudaErrorInvalidValue;
-  auto kern = p.N <= 1024 ? jmjp_kernel<T, KIND, 1> : p.N <= 4096 ? jmjp_kernel<T, KIND, 4> : jmjp_kernel<T, KIND, 0>;
+  const int nupd = p.N >= 992 ? 992 : (p.N + 31) / 32 * 32;  // updaters; one more warp reads
+  auto kern = p.N <= nupd ? jmjp_kernel<T, KIND, 1> : p.N <= 4 * nupd ? jmjp_kernel<T, KIND, 4> : jmjp_kernel<T, KIND, 0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJmjpSmem);
   if (e != cudaSuccess) return e;
-  const int threads = p.N >= 1024 ? 1024 : (p.N + 31) / 32 * 32;
-  kern<<<1, threads, smem, s>>>(p);
+  kern<<<1, nupd + 32, smem, s>>>(p);
   return cudaGetLastError();
 }
 
