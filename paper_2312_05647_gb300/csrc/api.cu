@@ -1000,8 +1000,11 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   if ((rc = mark(m, 0, s))) return rc;
   MJP_CUDA(launch_plan(pp, s));
   // Chains of different theta differ in length (K grows with Omega): start
-  // the longest first so the last wave of clusters holds the short ones.
-  if (B > 1) MJP_CUDA(launch_order_jobs(pp.info, B, m->d_jmap.as<int32_t>(), s));
+  // the longest first so the last wave of clusters holds the short ones.  The
+  // ranking compares all pairs, so batches above kOrderMax keep launch order.
+  constexpr int kOrderMax = 8192;
+  const bool ordered = B > 1 && B <= kOrderMax;
+  if (ordered) MJP_CUDA(launch_order_jobs(pp.info, B, m->d_jmap.as<int32_t>(), s));
   if ((rc = mark(m, 1, s))) return rc;
 
   ChainParams cp = {};
@@ -1015,7 +1018,7 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   cp.G = obs->G; cp.nmem = nmem_list; cp.ll = d_out;
   cp.renorm = (m->precision == MJP_FP32) ? m->renorm : 0;
   cp.slab = slab; cp.status = pp.status;
-  cp.job_map = B > 1 ? m->d_jmap.as<int32_t>() : nullptr;
+  cp.job_map = ordered ? m->d_jmap.as<int32_t>() : nullptr;
   if (use_reg) MJP_CUDA(launch_chain_reg2d(cp, rp, s));
   else MJP_CUDA(launch_chain_stencil(m->kind, m->precision, 1, cp, C, T, s));
   if ((rc = mark(m, 2, s))) return rc;
