@@ -522,7 +522,7 @@ def main():
         pm, cm = model.last_timing()
         plan_ms.append(pm)
         chain_ms.append(cm)
-        launches += 3 if args.batch > 1 else 2   # planner, longest-first ordering, chain
+        launches += 3 if 1 < args.batch <= 8192 else 2   # planner, longest-first ordering, chain
     clk = clocks.stop()
     model.check()
     ll_dev = out.cpu().numpy()
