@@ -322,7 +322,18 @@ def other_configs():
     mr.set_option(mjp.OPT_METHOD, mjp.METHOD_KRYLOV)
     _, kinfo = mr.expv(r0, cfg["times"], info=True)
     ms_kr = _events_ms(lambda: [mr.expv(r0, cfg["times"], out=out) for _ in range(50)], reps=3)
+    # The promoter (two-state, N_R = 300) solved to its last collection time, t = 10.
+    mp = mjp.Model(synth.TWOSTATE, [300], [100.0, 1.0, 2.0, 1.0], mjp.FP64)
+    rp0 = torch.tensor(synth.delta(600, 0), dtype=torch.float64, device="cuda")
+    op = torch.empty((1, 600), dtype=torch.float64, device="cuda")
+    prom = {}
+    for name, meth in (("rmjp", mjp.METHOD_RMJP), ("rk4", mjp.METHOD_RK4), ("krylov20", mjp.METHOD_KRYLOV)):
+        mp.set_option(mjp.OPT_METHOD, meth)
+        _, ip = mp.expv(rp0, [10.0], info=True)
+        prom[name + "_ms"] = _events_ms(lambda: mp.expv(rp0, [10.0], out=op), reps=3)
+        prom[name + ("_jumps" if meth == mjp.METHOD_RMJP else "_steps")] = int(ip["K"][0])
     res["rk4_krylov_vs_rmjp"] = {
+        "promoter_NR300_t10": prom,
         "immigration_death_N64": {"rk4_us_per_call": 1e3 * ms_rk / 50, "rk4_steps_to_t5": int(rinfo["K"][-1]),
                                   "krylov20_us_per_call": 1e3 * ms_kr / 50, "krylov20_steps_to_t5": int(kinfo["K"][-1]),
                                   "rmjp_us_per_call": 1e3 * ms / 200, "rmjp_jumps_to_t5": 516},

@@ -108,8 +108,8 @@ extern "C" {
                                    i.e. jumps between two halo exchanges (default 32; 1 .. 1024) */
 #define MJP_OPT_METHOD 9        /* expv_series method: 0 = R-MJP (Algorithm 2, default), 1 = fourth-order Runge-Kutta
                                    (Method #4), 2 = Krylov subspace steps (Method #5, Algorithm 3 with the full
-                                   projection of Eq. Krylov_projection).  1 and 2: FP64 birth-death models of at
-                                   most 4,096 states; the times are visited in ascending order and each interval is
+                                   projection of Eq. Krylov_projection).  1 and 2: FP64 birth-death and two-state
+                                   models of at most 4,096 states; the times are visited in ascending order and each interval is
                                    split into ceil(interval x max_n |a_nn| / D) equal steps, D = 1 (RK4) or
                                    2 kappa (Krylov, Sec. 2.3); the info report then gives omega = max_n |a_nn|,
                                    K_i = cumulative steps to t_i, eps_i = 0 */

@@ -557,17 +557,30 @@ int rate_model_check(mjp_model* m, void* stream) {
 int expv_ode(mjp_model* m, const void* rho0, const std::vector<double>& st, const std::vector<int32_t>& order,
              void* out, mjp_series_info* info, cudaStream_t s) {
   const bool kry = m->method == 2;
-  if (m->kind != MJP_BD1D || m->precision != MJP_FP64)
-    return fail(MJP_ERR_UNSUPPORTED, "RK4 and Krylov steps are available for FP64 birth-death models");
+  if ((m->kind != MJP_BD1D && m->kind != MJP_TWOSTATE) || m->precision != MJP_FP64)
+    return fail(MJP_ERR_UNSUPPORTED, "RK4 and Krylov steps are available for FP64 birth-death and two-state models");
   if (m->N > (kry ? (int64_t)krylov_max_states() : rk4_max_states()))
     return fail(MJP_ERR_UNSUPPORTED, "RK4 and Krylov steps hold at most 4096 states");
   const int nt = (int)st.size();
-  const double beta = m->theta[0], gamma = m->theta[1];
+  const double* th = m->theta.data();
+  // max_n |a_nn|, each row summed in ascending target order.
   double maxe = 0.0;
   for (int64_t n = 0; n < m->N; ++n) {
     double e = 0.0;
-    if (n >= 1) e = e + gamma * (double)n;
-    if (n + 1 < m->N) e = e + beta;
+    if (m->kind == MJP_BD1D) {
+      if (n >= 1) e = e + th[1] * (double)n;
+      if (n + 1 < m->N) e = e + th[0];
+    } else {
+      const int64_t sg = n / m->M, r = n - sg * m->M;
+      if (sg == 0) {
+        if (r >= 1) e = e + th[1] * (double)r;
+        if (r + 1 < m->M) e = e + th[0];
+        e = e + th[3];
+      } else {
+        e = e + th[2];
+        if (r >= 1) e = e + th[1] * (double)r;
+      }
+    }
     if (e > maxe) maxe = e;
   }
   const double div = kry ? 2.0 * m->kappa : 1.0;
@@ -582,19 +595,21 @@ int expv_ode(mjp_model* m, const void* rho0, const std::vector<double>& st, cons
   }
   int rc = 0;
   if ((rc = m->d_orig.ensure(sizeof(int32_t) * nt)) || (rc = m->d_K.ensure(sizeof(int64_t) * nt)) ||
-      (rc = m->d_wtab.ensure(sizeof(double) * nt)) || (rc = m->d_theta.ensure(sizeof(double) * 2)) ||
+      (rc = m->d_wtab.ensure(sizeof(double) * nt)) || (rc = m->d_theta.ensure(sizeof(double) * m->theta.size())) ||
       (rc = ensure_status(m)))
     return rc;
   if (kry && (rc = m->d_kq.ensure(sizeof(double) * (size_t)m->kappa * m->N))) return rc;
   MJP_CUDA(cudaMemcpyAsync(m->d_orig.p, order.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
   MJP_CUDA(cudaMemcpyAsync(m->d_K.p, steps.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
   MJP_CUDA(cudaMemcpyAsync(m->d_wtab.p, h.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, s));
-  MJP_CUDA(cudaMemcpyAsync(m->d_theta.p, m->theta.data(), sizeof(double) * 2, cudaMemcpyHostToDevice, s));
+  MJP_CUDA(cudaMemcpyAsync(m->d_theta.p, m->theta.data(), sizeof(double) * m->theta.size(), cudaMemcpyHostToDevice, s));
   if ((rc = mark(m, 0, s)) || (rc = mark(m, 1, s))) return rc;
   if (kry) {
     KrylovParams kp = {};
     kp.theta = m->d_theta.as<double>();
+    kp.kind = m->kind;
     kp.N = (int)m->N;
+    kp.M = (int)m->M;
     kp.rho0 = reinterpret_cast<const double*>(rho0);
     kp.out = reinterpret_cast<double*>(out);
     kp.orig = m->d_orig.as<int32_t>();
@@ -605,18 +620,20 @@ int expv_ode(mjp_model* m, const void* rho0, const std::vector<double>& st, cons
     kp.maxe = maxe;
     kp.Q = m->d_kq.as<double>();
     kp.status = m->d_status.as<int>();
-    MJP_CUDA(launch_krylov_bd1d(kp, s));
+    MJP_CUDA(launch_krylov(kp, s));
   } else {
     Rk4Params rp = {};
     rp.theta = m->d_theta.as<double>();
+    rp.kind = m->kind;
     rp.N = (int)m->N;
+    rp.M = (int)m->M;
     rp.rho0 = reinterpret_cast<const double*>(rho0);
     rp.out = reinterpret_cast<double*>(out);
     rp.orig = m->d_orig.as<int32_t>();
     rp.steps = m->d_K.as<int64_t>();
     rp.hstep = m->d_wtab.as<double>();
     rp.ntimes = nt;
-    MJP_CUDA(launch_rk4_bd1d(rp, s));
+    MJP_CUDA(launch_rk4(rp, s));
   }
   if ((rc = mark(m, 2, s))) return rc;
   // The host arrays above are pageable: the copies have been staged before

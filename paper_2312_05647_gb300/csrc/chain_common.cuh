@@ -30,6 +30,62 @@ __device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cl
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Row n of y = x A (Eq. A_def) for the FP64 comparison methods, matrix-free:
+// y_n = (inflows in ascending source order) - x_n e_n, with e_n summed over
+// row n in ascending target order.  Birth-death: inflow beta from n-1 and
+// gamma (n+1) from n+1.  Two-state (n = n_R + sigma N_R, sigma 0 active):
+// active states gain beta from n-1 (n_R >= 1), gamma (n_R+1) from n+1 and
+// lambda_act from the inactive partner n + N_R; inactive states gain
+// lambda_ina from the active partner n - N_R (a lower index, so it comes
+// first) and gamma (n_R+1) from n+1.  Coefficients of missing sources are 0.
+// The death coefficient gamma (n_R+1) and the exit rate are kept per state.
+__device__ inline void rate_row_coef(int kind, int n, int N, int NR, const double* th, double& dn, double& ex) {
+  dn = ex = 0.0;
+  if (n < 0 || n >= N) return;
+  if (kind == MJP_BD1D) {
+    double e = 0.0;
+    if (n >= 1) e = __dadd_rn(e, __dmul_rn(th[1], (double)n));
+    if (n + 1 < N) e = __dadd_rn(e, th[0]);
+    ex = e;
+    dn = n + 1 < N ? __dmul_rn(th[1], (double)(n + 1)) : 0.0;
+    return;
+  }
+  const int sg = n >= NR ? 1 : 0, r = n - sg * NR;
+  dn = r + 1 < NR ? __dmul_rn(th[1], (double)(r + 1)) : 0.0;
+  double e = 0.0;
+  if (sg == 0) {
+    if (r >= 1) e = __dadd_rn(e, __dmul_rn(th[1], (double)r));
+    if (r + 1 < NR) e = __dadd_rn(e, th[0]);
+    e = __dadd_rn(e, th[3]);
+  } else {
+    e = __dadd_rn(e, th[2]);
+    if (r >= 1) e = __dadd_rn(e, __dmul_rn(th[1], (double)r));
+  }
+  ex = e;
+}
+// y_n from the staged vector X (N values); xn = x_n.
+__device__ inline double rate_apply_row(int kind, int n, int N, int NR, const double* th, double dn, double ex,
+                                        const double* X, double xn) {
+  const double left = n >= 1 ? X[n - 1] : 0.0;
+  const double right = n + 1 < N ? X[n + 1] : 0.0;
+  if (kind == MJP_BD1D) {
+    double t = __dmul_rn(left, th[0]);
+    t = __dadd_rn(t, __dmul_rn(right, dn));
+    return __dsub_rn(t, __dmul_rn(xn, ex));
+  }
+  const bool act = n < NR;
+  double t;
+  if (act) {
+    t = __dmul_rn(left, n >= 1 ? th[0] : 0.0);
+    t = __dadd_rn(t, __dmul_rn(right, dn));
+    t = __dadd_rn(t, __dmul_rn(X[n + NR], th[2]));
+  } else {
+    t = __dmul_rn(X[n - NR], th[3]);
+    t = __dadd_rn(t, __dmul_rn(right, dn));
+  }
+  return __dsub_rn(t, __dmul_rn(xn, ex));
+}
+
 // Asynchronous global -> shared copy of one float or double (cp.async).
 __device__ __forceinline__ void cp_async_elem(float* sdst, const float* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);

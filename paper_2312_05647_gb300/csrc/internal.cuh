@@ -134,8 +134,9 @@ struct CsrJumpParams {
 
 // Fourth-order Runge-Kutta for one birth-death distribution (rk4.cu).
 struct Rk4Params {
-  const double* theta;   // device, {beta, gamma}
-  int N;
+  const double* theta;   // device, {beta, gamma} or {beta, gamma, lambda_act, lambda_ina}
+  int kind;              // MJP_BD1D or MJP_TWOSTATE
+  int N, M;              // states; M = N_R for the two-state model
   const double* rho0;    // device, N values
   double* out;           // device, ntimes x N (caller's time order)
   const int32_t* orig;   // device, sorted time q -> caller's row
@@ -190,8 +191,9 @@ cudaError_t launch_chain_reg1d(int precision, const ChainParams& p, const Reg1dP
 int64_t rk4_max_states();
 // Krylov subspace steps for one birth-death distribution (krylov.cu).
 struct KrylovParams {
-  const double* theta;   // device, {beta, gamma}
-  int N;
+  const double* theta;   // device, {beta, gamma} or {beta, gamma, lambda_act, lambda_ina}
+  int kind;              // MJP_BD1D or MJP_TWOSTATE
+  int N, M;              // states; M = N_R for the two-state model
   const double* rho0;    // device, N values
   double* out;           // device, ntimes x N (caller's time order)
   const int32_t* orig;   // device, sorted time q -> caller's row
@@ -226,8 +228,8 @@ size_t jmjp_chunk_bytes(int precision, int N);
 cudaError_t launch_jmjp(int kind, int precision, const JmjpParams& p, cudaStream_t s);
 int krylov_max_states();
 int krylov_max_kappa();
-cudaError_t launch_krylov_bd1d(const KrylovParams& p, cudaStream_t s);
-cudaError_t launch_rk4_bd1d(const Rk4Params& p, cudaStream_t s);
+cudaError_t launch_krylov(const KrylovParams& p, cudaStream_t s);
+cudaError_t launch_rk4(const Rk4Params& p, cudaStream_t s);
 cudaError_t launch_fill_weights(const Win* win, int ntimes, const int64_t* woff, double* table, cudaStream_t s);
 cudaError_t launch_permute_in(int precision, const void* src, const int32_t* perm, void* dst, int64_t n,
                               cudaStream_t s);

@@ -169,59 +169,48 @@ __device__ int cta_expm(int m, const double* A, double* E, double* W, int* flag)
 }
 
 template <int R, int kMaxT>
-__global__ void __launch_bounds__(kMaxT, 1) krylov_bd1d_kernel(const KrylovParams p) {
+__global__ void __launch_bounds__(kMaxT, 1) krylov_kernel(const KrylovParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int ES = nthr + 1;
   const int N = p.N, K = p.kappa;
-  double* E = reinterpret_cast<double*>(smem);        // [parity][first, last][nthr + 1]
-  double* red = E + 4 * ES;                            // 33
+  double* X = reinterpret_cast<double*>(smem);        // [parity][N]: the vector being multiplied
+  double* red = X + 2 * (size_t)N;                     // 33
   double* H = red + 33;                                // kKmax x kKmax
   double* Hm = H + kKmax * kKmax;                      // m x m
   double* Ex = Hm + kKmax * kKmax;                     // m x m
   double* W = Ex + kKmax * kKmax;                      // 9 m x m
   __shared__ int s_flag;
-  const double beta_r = p.theta[0], gamma = p.theta[1];
   const double maxe = p.maxe;
 
-  // Inflow gamma (n+1) from n+1 and the exit rate of each held state (death,
-  // then birth: the rate matrix's row order); zero beyond the box.
-  double dn[R], ex[R], r[R], w[R];
+  // Rates of each held state (Eq. A_def, the rate matrix's row order); zero
+  // beyond the box.
+  double r[R], w[R];
+  double dn[R], ex[R];
 #pragma unroll
   for (int j = 0; j < R; ++j) {
     const int n = tid * R + j;
-    const bool in = n < N;
-    double e = 0.0;
-    if (in && n >= 1) e = __dadd_rn(e, __dmul_rn(gamma, (double)n));
-    if (in && n + 1 < N) e = __dadd_rn(e, beta_r);
-    ex[j] = e;
-    dn[j] = (in && n + 1 < N) ? __dmul_rn(gamma, (double)(n + 1)) : 0.0;
-    r[j] = in ? p.rho0[n] : 0.0;
+    rate_row_coef(p.kind, n, N, p.M, p.theta, dn[j], ex[j]);
+    r[j] = n < N ? p.rho0[n] : 0.0;
     w[j] = 0.0;
   }
-  if (tid < 4) E[tid * ES + nthr] = 0.0;
-  const int iL = tid > 0 ? tid - 1 : nthr;
-  const int iR = tid + 1 < nthr ? tid + 1 : nthr;
   double* const Qb = p.Q;  // [K][N]
   auto qrow = [&](int i) { return Qb + (int64_t)i * N; };
 
   int par = 0;
-  // y = v A for the thread's run.
+  // y = v A for the thread's run; v staged whole at parity par (the
+  // two-state partner lies N_R states away).
   auto apply = [&](const double (&v)[R], double (&y)[R]) {
-    E[(par * 2 + 0) * ES + tid] = v[0];
-    E[(par * 2 + 1) * ES + tid] = v[R - 1];
+    double* const Xp = X + (size_t)par * N;
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (tid * R + j < N) Xp[tid * R + j] = v[j];
     __syncthreads();
-    const double vl = E[(par * 2 + 1) * ES + iL];
-    const double vr = E[(par * 2 + 0) * ES + iR];
     par ^= 1;
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-      const double left = j > 0 ? v[j - 1] : vl;
-      const double right = j + 1 < R ? v[j + 1] : vr;
-      double t = __dmul_rn(left, beta_r);
-      t = __dadd_rn(t, __dmul_rn(right, dn[j]));
+      const int n = tid * R + j;
       // States beyond the box stay zero (they enter the norms and products).
-      y[j] = tid * R + j < N ? __dsub_rn(t, __dmul_rn(v[j], ex[j])) : 0.0;
+      y[j] = n < N ? rate_apply_row(p.kind, n, N, p.M, p.theta, dn[j], ex[j], Xp, v[j]) : 0.0;
     }
   };
 
@@ -311,8 +300,8 @@ __global__ void __launch_bounds__(kMaxT, 1) krylov_bd1d_kernel(const KrylovParam
 template <int R, int kMaxT>
 cudaError_t launch_krylov_typed(const KrylovParams& p, cudaStream_t s) {
   const int threads = (int)(((p.N + R - 1) / R + 31) / 32 * 32);
-  const size_t smem = sizeof(double) * (4 * (size_t)(threads + 1) + 33 + 12 * (size_t)kKmax * kKmax);
-  auto kern = krylov_bd1d_kernel<R, kMaxT>;
+  const size_t smem = sizeof(double) * (2 * (size_t)p.N + 33 + 12 * (size_t)kKmax * kKmax);
+  auto kern = krylov_kernel<R, kMaxT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<1, threads, smem, s>>>(p);
@@ -324,8 +313,10 @@ cudaError_t launch_krylov_typed(const KrylovParams& p, cudaStream_t s) {
 int krylov_max_states() { return 8 * 512; }
 int krylov_max_kappa() { return kKmax; }
 
-cudaError_t launch_krylov_bd1d(const KrylovParams& p, cudaStream_t s) {
-  if (p.N < 1 || p.N > krylov_max_states() || p.kappa < 1 || p.kappa > kKmax) return cudaErrorInvalidValue;
+cudaError_t launch_krylov(const KrylovParams& p, cudaStream_t s) {
+  if (p.N < 1 || p.N > krylov_max_states() || p.kappa < 1 || p.kappa > kKmax ||
+      (p.kind != MJP_BD1D && p.kind != MJP_TWOSTATE))
+    return cudaErrorInvalidValue;
   if (p.N <= 512) return launch_krylov_typed<1, 512>(p, s);
   return launch_krylov_typed<8, 512>(p, s);
 }

@@ -1,18 +1,17 @@
-// rk4.cu -- fourth-order Runge-Kutta for birth-death models (Method #4 of the
-// paper, Sec. 2.3: Eqs. RKstep and RKintermediate), FP64, the comparison
-// method beside R-MJP.
+// rk4.cu -- fourth-order Runge-Kutta for birth-death and two-state models
+// (Method #4 of the paper, Sec. 2.3: Eqs. RKstep and RKintermediate), FP64,
+// the comparison method beside R-MJP.
 //
 // One CTA evolves one distribution; thread t holds R consecutive states in
 // registers (rho, the stage input x and the partial sum of the deltas).  A
-// stage y = x A (Eq. A_def, matrix-free from theta) needs the neighbours of
-// a thread's run, which travel through shared memory (the first and last
-// state of every thread, double-buffered by stage parity, a zero slot at the
-// box ends): one CTA barrier per stage, four per step.  The times are visited
+// stage y = x A (Eq. A_def, matrix-free from theta) reads the neighbours and
+// the two-state partner from the stage input staged whole in shared memory
+// (double-buffered by stage parity): one CTA barrier per stage, four per step.  The times are visited
 // in ascending order; each interval between consecutive times is split into
 // the host-computed number of equal steps (h <= 1 / max_n |a_nn|).
 //
-// The operations per state follow the oracle's order exactly (inflow from
-// n-1, then from n+1, then minus the exit; the deltas summed as
+// The operations per state follow the oracle's order exactly (inflows in
+// ascending source order, then minus the exit; the deltas summed as
 // ((d1 + 2 d2) + 2 d3) + d4, divided by 6), with explicit unfused roundings,
 // so the GPU result equals the oracle's to the bit.
 #include "chain_common.cuh"
@@ -23,51 +22,37 @@ namespace mjp {
 namespace {
 
 template <int R, int kMaxT>
-__global__ void __launch_bounds__(kMaxT, 1) rk4_bd1d_kernel(const Rk4Params p) {
+__global__ void __launch_bounds__(kMaxT, 1) rk4_kernel(const Rk4Params p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  double* const E = reinterpret_cast<double*>(smem);  // [parity][first, last][nthr + 1]
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int ES = nthr + 1;
+  double* const X = reinterpret_cast<double*>(smem);  // [parity][N]: the stage input
+  const int tid = threadIdx.x;
   const int N = p.N;
-  const double beta = p.theta[0], gamma = p.theta[1];
   const double* rho0 = p.rho0;
 
-  // Coefficients of the held states: inflow gamma (n+1) from n+1 and the exit
-  // rate e_n summed in the rate matrix's row order (death, then birth);
-  // states beyond the box hold zero and have zero coefficients.
-  double r[R], x[R], acc[R], dn[R], ex[R];
+  // Rates of the held states (states beyond the box hold zero).
+  double r[R], x[R], acc[R];
+  double dn[R], ex[R];
 #pragma unroll
   for (int j = 0; j < R; ++j) {
     const int n = tid * R + j;
-    const bool in = n < N;
-    double e = 0.0;
-    if (in && n >= 1) e = __dadd_rn(e, __dmul_rn(gamma, (double)n));
-    if (in && n + 1 < N) e = __dadd_rn(e, beta);
-    ex[j] = e;
-    dn[j] = (in && n + 1 < N) ? __dmul_rn(gamma, (double)(n + 1)) : 0.0;
-    r[j] = in ? rho0[n] : 0.0;
+    rate_row_coef(p.kind, n, N, p.M, p.theta, dn[j], ex[j]);
+    r[j] = n < N ? rho0[n] : 0.0;
     x[j] = 0.0;
     acc[j] = 0.0;
   }
-  const double bin = beta;  // inflow from n-1 (x_{-1} is the zero slot)
-  if (tid < 4) E[tid * ES + nthr] = 0.0;
-  const int iL = tid > 0 ? tid - 1 : nthr;
-  const int iR = tid + 1 < nthr ? tid + 1 : nthr;
 
-  // y = v A for the thread's run, v's edges published at parity par.
+  // y = v A for the thread's run; v staged whole at parity par (the
+  // two-state partner lies N_R states away).
   auto apply = [&](const double (&v)[R], double (&y)[R], int par) {
-    E[(par * 2 + 0) * ES + tid] = v[0];
-    E[(par * 2 + 1) * ES + tid] = v[R - 1];
+    double* const Xp = X + (size_t)par * N;
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (tid * R + j < N) Xp[tid * R + j] = v[j];
     __syncthreads();
-    const double vl = E[(par * 2 + 1) * ES + iL];
-    const double vr = E[(par * 2 + 0) * ES + iR];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-      const double left = j > 0 ? v[j - 1] : vl;
-      const double right = j + 1 < R ? v[j + 1] : vr;
-      double t = __dmul_rn(left, bin);
-      t = __dadd_rn(t, __dmul_rn(right, dn[j]));
-      y[j] = __dsub_rn(t, __dmul_rn(v[j], ex[j]));
+      const int n = tid * R + j;
+      y[j] = n < N ? rate_apply_row(p.kind, n, N, p.M, p.theta, dn[j], ex[j], Xp, v[j]) : 0.0;
     }
   };
 
@@ -121,8 +106,11 @@ __global__ void __launch_bounds__(kMaxT, 1) rk4_bd1d_kernel(const Rk4Params p) {
 template <int R, int kMaxT>
 cudaError_t launch_rk4_typed(const Rk4Params& p, cudaStream_t s) {
   const int threads = (int)(((p.N + R - 1) / R + 31) / 32 * 32);
-  const size_t smem = sizeof(double) * 4 * (size_t)(threads + 1);
-  rk4_bd1d_kernel<R, kMaxT><<<1, threads, smem, s>>>(p);
+  const size_t smem = sizeof(double) * 2 * (size_t)p.N;
+  auto kern = rk4_kernel<R, kMaxT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<1, threads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -130,8 +118,8 @@ cudaError_t launch_rk4_typed(const Rk4Params& p, cudaStream_t s) {
 
 int64_t rk4_max_states() { return 8 * 512; }
 
-cudaError_t launch_rk4_bd1d(const Rk4Params& p, cudaStream_t s) {
-  if (p.N < 1 || p.N > rk4_max_states()) return cudaErrorInvalidValue;
+cudaError_t launch_rk4(const Rk4Params& p, cudaStream_t s) {
+  if (p.N < 1 || p.N > rk4_max_states() || (p.kind != MJP_BD1D && p.kind != MJP_TWOSTATE)) return cudaErrorInvalidValue;
   if (p.N <= 1024) return launch_rk4_typed<1, 1024>(p, s);
   return launch_rk4_typed<8, 512>(p, s);
 }

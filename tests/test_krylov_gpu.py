@@ -21,10 +21,10 @@ def _built():
     torch.cuda.set_device(0)
 
 
-def _krylov_gpu(N, theta, rho0, times, kappa=20, prec=2):
+def _krylov_gpu(N, theta, rho0, times, kappa=20, prec=2, kind=synth.BD1D):
     import torch
     import paper_2312_05647_gb300 as mjp
-    m = mjp.Model(synth.BD1D, [N], theta, prec)
+    m = mjp.Model(kind, [N], theta, prec)
     m.set_option(mjp.OPT_METHOD, mjp.METHOD_KRYLOV)
     m.set_option(mjp.OPT_KAPPA, kappa)
     r = torch.tensor(rho0, dtype=m.torch_dtype, device="cuda")
@@ -49,6 +49,23 @@ def test_krylov_matches_oracle(N, theta, times, kappa):
     rho0 /= rho0.sum()
     got, info = _krylov_gpu(N, theta, rho0, times, kappa)
     ref, rinfo = oracle.krylov(oracle.build_model(oracle.BD1D, [N], theta), rho0, times, kappa=kappa)
+    assert info["omega"] == rinfo["max_exit"]
+    assert list(info["K"]) == list(rinfo["steps"])
+    assert np.abs(got - ref).max() <= 1e-12
+
+
+@pytest.mark.parametrize("NR,theta,times,kappa", [
+    (300, [100.0, 1.0, 2.0, 1.0], [0.5, 0.05], 20),          # the promoter of Sec. 3.1.2
+    (2, [3.0, 0.5, 1.5, 2.0], [1.0, 0.3], 20),               # 4 states: the space is whole
+    (37, [20.0, 0.5, 0.3, 1.5], [0.7], 8),
+    (2048, [900.0, 1.0, 2.0, 1.0], [0.002], 20),
+])
+def test_krylov_two_state_matches_oracle(NR, theta, times, kappa):
+    gen = np.random.default_rng(NR + kappa)
+    rho0 = gen.random(2 * NR)
+    rho0 /= rho0.sum()
+    got, info = _krylov_gpu(NR, theta, rho0, times, kappa, kind=synth.TWOSTATE)
+    ref, rinfo = oracle.krylov(oracle.build_model(oracle.TWOSTATE, [NR], theta), rho0, times, kappa=kappa)
     assert info["omega"] == rinfo["max_exit"]
     assert list(info["K"]) == list(rinfo["steps"])
     assert np.abs(got - ref).max() <= 1e-12

@@ -619,3 +619,23 @@ def test_jmjp_order_and_grouping():
     # All states at any k: B is stochastic, the mass stays 1.
     allg = [np.arange(40)] * 3
     assert np.abs(oracle.jmjp_probs(csr, rho0, [0, 200, 1000], allg) - 1.0).max() <= 1e-13
+
+
+def test_rk4_two_state_step_from_the_reactions():
+    # One RK4 step on the two-state promoter equals the degree-4 Taylor
+    # polynomial of hA with A built from the reaction list (not the oracle's CSR).
+    NR, th = 9, [6.0, 0.7, 1.3, 0.4]
+    A = _twostate_generator_from_reactions(NR, th)
+    csr = oracle.build_model(oracle.TWOSTATE, [NR], th)
+    maxe = float(np.max(-np.diag(A)))
+    assert oracle.max_exit(csr) == maxe
+    h = 0.9 / maxe
+    rho0 = np.random.default_rng(9).random(2 * NR)
+    rho0 /= rho0.sum()
+    out, info = oracle.rk4(csr, rho0, [h])
+    assert list(info["steps"]) == [1]
+    P, term = np.eye(2 * NR), np.eye(2 * NR)
+    for j in range(1, 5):
+        term = term @ (h * A) / j
+        P = P + term
+    assert np.abs(out[0] - rho0 @ P).max() <= 1e-15

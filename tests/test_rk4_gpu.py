@@ -19,10 +19,10 @@ def _built():
     torch.cuda.set_device(0)
 
 
-def _rk4_gpu(N, theta, rho0, times, prec=2):
+def _rk4_gpu(N, theta, rho0, times, prec=2, kind=synth.BD1D):
     import torch
     import paper_2312_05647_gb300 as mjp
-    m = mjp.Model(synth.BD1D, [N], theta, prec)
+    m = mjp.Model(kind, [N], theta, prec)
     m.set_option(mjp.OPT_METHOD, mjp.METHOD_RK4)
     r = torch.tensor(rho0, dtype=m.torch_dtype, device="cuda")
     out, info = m.expv(r, times, info=True)
@@ -48,6 +48,23 @@ def test_rk4_matches_oracle_bitwise(N, theta, times):
     assert info["omega"] == rinfo["max_exit"]
     assert list(info["K"]) == list(rinfo["steps"])
     assert np.abs(got - ref).max() <= 1e-12
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("NR,theta,times", [
+    (300, [100.0, 1.0, 2.0, 1.0], [0.5, 0.05, 0.2]),        # the promoter of Sec. 3.1.2
+    (2, [3.0, 0.5, 1.5, 2.0], [1.0, 0.3]),
+    (37, [20.0, 0.5, 0.3, 1.5], [0.7, 2.0]),
+    (2048, [900.0, 1.0, 2.0, 1.0], [0.002]),                # 4,096 states, 8 per thread
+])
+def test_rk4_two_state_matches_oracle_bitwise(NR, theta, times):
+    gen = np.random.default_rng(NR)
+    rho0 = gen.random(2 * NR)
+    rho0 /= rho0.sum()
+    got, info = _rk4_gpu(NR, theta, rho0, times, kind=synth.TWOSTATE)
+    ref, rinfo = oracle.rk4(oracle.build_model(oracle.TWOSTATE, [NR], theta), rho0, times)
+    assert info["omega"] == rinfo["max_exit"]
+    assert list(info["K"]) == list(rinfo["steps"])
     np.testing.assert_array_equal(got, ref)
 
 
