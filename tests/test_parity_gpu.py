@@ -1,6 +1,6 @@
 """GPU path (through the C ABI) against the CPU oracle, element by element.
 
-Tolerances (the benchmark spec): max |GPU - oracle| <= 1e-12 for the FP64 chain and
+Tolerances: max |GPU - oracle| <= 1e-12 for the FP64 chain and
 <= 1e-6 for the FP32 chain, on transient distributions, same truncation mode.
 Integer results of the planner (K_i) are compared exactly."""
 import numpy as np
