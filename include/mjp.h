@@ -45,7 +45,7 @@ extern "C" {
 #define MJP_ERR_DEVICE_TIMEOUT (-5) /* a bounded device wait ran out */
 #define MJP_ERR_KCAP (-6)           /* truncation index K above the configured cap */
 #define MJP_ERR_NUMERIC (-7)        /* non-finite or negative probability produced */
-#define MJP_ERR_UNSUPPORTED (-8)    /* valid request this build does not handle */
+#define MJP_ERR_UNSUPPORTED (-8)    /* valid request the library does not handle */
 
 /* ---- model kinds ------------------------------------------------------- */
 /* Birth-death, Eq. BD_def (Sec. 3.1.1). dims = {N}; theta = {beta, gamma}:
