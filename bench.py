@@ -66,13 +66,33 @@ def dist_env():
     return world, rank, local
 
 
+def rank_thetas(rank: int, batch: int):
+    """The thetas rank `rank` evaluates: its own seeded jitter of the
+    mRNA/protein rates (weak scaling: every rank a full batch of its own)."""
+    import synth
+    return synth.jitter(synth.mrna_protein()["theta"], batch, 0.2, synth.rng(2, 1000 + rank))
+
+
 def workload(rank: int, batch: int):
     import synth
     cfg = synth.mrna_protein()
     snaps = synth.gillespie_snapshots(cfg["kind"], cfg["dims"], cfg["theta"], cfg["times"], 100, synth.rng(2, 0))
     obs = synth.snapshot_obs(cfg["kind"], cfg["dims"], snaps)
-    thetas = synth.jitter(cfg["theta"], batch, 0.2, synth.rng(2, 1000 + rank))
-    return cfg, obs, thetas
+    return cfg, obs, rank_thetas(rank, batch)
+
+
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The largest x over all ranks (all_reduce MAX), x itself on one rank."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, steps: int, seconds_max: float) -> float:
+    """Units all ranks processed per second of the slowest rank."""
+    return world * units_per_rank * steps / seconds_max
 
 
 def kmax_of(theta, dims, tmax):
@@ -538,11 +558,8 @@ def main():
     model.check()
     ll_dev = out.cpu().numpy()
     total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms_max = float(t.item())
-    value = world * B * args.steps / (total_ms_max / 1e3)
+    total_ms_max = max_over_ranks(total_ms, world, dev)
+    value = whole_job_rate(world, B, args.steps, total_ms_max / 1e3)
 
     # ---- end to end through the public API (host theta in, host loglik out) -
     pinned_theta = torch.tensor(thetas, dtype=torch.float64).pin_memory()
@@ -554,10 +571,7 @@ def main():
         t0 = time.perf_counter()
         ll_host = mjp.loglik(model, ob, th_host)
         e2e_s += time.perf_counter() - t0
-    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = world * B * args.steps / float(t.item())
+    e2e_value = whole_job_rate(world, B, args.steps, max_over_ranks(e2e_s, world, dev))
     assert np.array_equal(ll_host, ll_dev), "host and device calls disagree"
 
     if rank != 0:
