@@ -37,6 +37,10 @@ extern "C" {
 #endif
 
 /* ---- status codes ------------------------------------------------------ */
+/* Every call that returns int returns one of these; no C++ exception crosses
+ * this interface (a failed host allocation is MJP_ERR_ALLOC, any other
+ * host-side exception MJP_ERR_ARG).  mjp_last_error() describes the last
+ * failure on the calling thread. */
 #define MJP_OK 0
 #define MJP_ERR_ARG (-1)            /* invalid argument (NULL, size, NaN, t < 0, ...) */
 #define MJP_ERR_CSR (-2)            /* malformed CSR (row_ptr not monotone, column out of range, diagonal entry, negative rate) */

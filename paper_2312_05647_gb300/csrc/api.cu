@@ -317,7 +317,7 @@ const char* mjp_last_error(void) { return mjp::last_error().c_str(); }
 const char* mjp_version(void) { return "mjp-gb300 0.1 (sm_103a)"; }
 
 int rate_model_create_stencil(mjp_model** out, int kind, const int64_t* dims, int ndims,
-                              const double* theta, int ntheta, int precision) {
+                              const double* theta, int ntheta, int precision) try {
   if (!out) return fail(MJP_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (kind != MJP_BD1D && kind != MJP_TWOSTATE && kind != MJP_MRNA_PROT2D && kind != MJP_AUTOREG)
@@ -346,10 +346,12 @@ int rate_model_create_stencil(mjp_model** out, int kind, const int64_t* dims, in
   if (m->N > ((int64_t)1 << 31) - 1) { delete m; return fail(MJP_ERR_ARG, "too many states"); }
   *out = m;
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 int rate_model_create_csr(mjp_model** out, int64_t n, const int64_t* row_ptr, const int32_t* col,
-                          const double* rate, int precision) {
+                          const double* rate, int precision) try {
   if (!out) return fail(MJP_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (n < 1 || n > ((int64_t)1 << 31) - 1) return fail(MJP_ERR_ARG, "n out of range");
@@ -453,18 +455,22 @@ int rate_model_create_csr(mjp_model** out, int64_t n, const int64_t* row_ptr, co
   }
   *out = m;
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int rate_model_set_theta(mjp_model* m, const double* theta, int ntheta) {
+int rate_model_set_theta(mjp_model* m, const double* theta, int ntheta) try {
   if (!m || !theta) return fail(MJP_ERR_ARG, "NULL argument");
   if (m->kind == MJP_CSR) return fail(MJP_ERR_ARG, "CSR models have no theta");
   if (ntheta != ntheta_of(m->kind)) return fail(MJP_ERR_ARG, "wrong number of parameters");
   if (!finite_nonneg(theta, ntheta)) return fail(MJP_ERR_ARG, "rates must be finite and >= 0");
   m->theta.assign(theta, theta + ntheta);
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int rate_model_set_option(mjp_model* m, int option, int64_t value) {
+int rate_model_set_option(mjp_model* m, int option, int64_t value) try {
   if (!m) return fail(MJP_ERR_ARG, "NULL model");
   switch (option) {
     case MJP_OPT_RENORM_PERIOD:
@@ -516,13 +522,15 @@ int rate_model_set_option(mjp_model* m, int option, int64_t value) {
     default:
       return fail(MJP_ERR_ARG, "unknown option");
   }
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 int64_t rate_model_num_states(const mjp_model* m) { return m ? m->N : -1; }
 
 void rate_model_destroy(mjp_model* m) { delete m; }
 
-int rate_model_last_timing(mjp_model* m, double* ms_plan, double* ms_chain) {
+int rate_model_last_timing(mjp_model* m, double* ms_plan, double* ms_chain) try {
   if (!m) return fail(MJP_ERR_ARG, "NULL model");
   if (!m->profile || !m->timed) return fail(MJP_ERR_ARG, "no profiled call (set MJP_OPT_PROFILE first)");
   MJP_CUDA(cudaEventSynchronize(m->ev[2]));
@@ -532,9 +540,11 @@ int rate_model_last_timing(mjp_model* m, double* ms_plan, double* ms_chain) {
   if (ms_plan) *ms_plan = a;
   if (ms_chain) *ms_chain = b;
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int rate_model_check(mjp_model* m, void* stream) {
+int rate_model_check(mjp_model* m, void* stream) try {
   if (!m) return fail(MJP_ERR_ARG, "NULL model");
   MJP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   if (m->d_arena_ctl.p) {  // windows that did not fit ran the in-kernel recurrence: grow
@@ -547,6 +557,8 @@ int rate_model_check(mjp_model* m, void* stream) {
   MJP_CUDA(cudaMemcpy(&st, m->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
   MJP_CUDA(cudaMemset(m->d_status.p, 0, sizeof(int)));
   return map_status(st);
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 // expv_series by fourth-order Runge-Kutta (Method #4) or Krylov steps
@@ -653,7 +665,7 @@ int expv_ode(mjp_model* m, const void* rho0, const std::vector<double>& st, cons
 }
 
 int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes, void* out,
-                mjp_series_info* info, int trunc_mode, double tol, void* stream) {
+                mjp_series_info* info, int trunc_mode, double tol, void* stream) try {
   if (!m || !rho0 || !times || !out) return fail(MJP_ERR_ARG, "NULL argument");
   if (ntimes < 1 || ntimes > kMaxTimes) return fail(MJP_ERR_ARG, "ntimes must be in [1, 256]");
   if (trunc_mode != MJP_TRUNC_PAPER && trunc_mode != MJP_TRUNC_TOL) return fail(MJP_ERR_ARG, "unknown truncation mode");
@@ -752,10 +764,12 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
     return rate_model_check(m, stream);
   }
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 int jmjp_state_probs(mjp_model* m, const void* rho0, int64_t nobs, const int64_t* k, const int64_t* group_ptr,
-                     const int32_t* members, double* phi, void* stream) {
+                     const int32_t* members, double* phi, void* stream) try {
   if (!m || !rho0 || !k || !group_ptr || !members || !phi) return fail(MJP_ERR_ARG, "NULL argument");
   if (m->kind != MJP_BD1D && m->kind != MJP_TWOSTATE)
     return fail(MJP_ERR_UNSUPPORTED, "J-MJP probabilities are available for birth-death and two-state models");
@@ -859,11 +873,13 @@ int jmjp_state_probs(mjp_model* m, const void* rho0, int64_t nobs, const int64_t
   MJP_CUDA(cudaMemcpyAsync(phi, jp.phi, sizeof(double) * nobs, cudaMemcpyDeviceToHost, s));
   MJP_CUDA(cudaStreamSynchronize(s));
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 int mjp_obs_create(mjp_obs** out, int64_t n, int ntimes, const double* times,
                    const int64_t* group_ptr, const double* counts, const int64_t* member_ptr,
-                   const int32_t* members, const double* rho0) {
+                   const int32_t* members, const double* rho0) try {
   if (!out) return fail(MJP_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (n < 1 || ntimes < 1 || ntimes > kMaxTimes) return fail(MJP_ERR_ARG, "bad n or ntimes");
@@ -936,12 +952,14 @@ int mjp_obs_create(mjp_obs** out, int64_t n, int ntimes, const double* times,
   }
   *out = o;
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 void mjp_obs_destroy(mjp_obs* obs) { delete obs; }
 
 int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double* out, int where,
-           int trunc_mode, double tol, void* stream) {
+           int trunc_mode, double tol, void* stream) try {
   if (!m || !obs || !out) return fail(MJP_ERR_ARG, "NULL argument");
   if (B < 1) return fail(MJP_ERR_ARG, "B must be >= 1");
   if (where != MJP_PTR_HOST && where != MJP_PTR_DEVICE) return fail(MJP_ERR_ARG, "where must be MJP_PTR_HOST or MJP_PTR_DEVICE");
@@ -1044,6 +1062,8 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
     return rate_model_check(m, stream);
   }
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 }  // extern "C"

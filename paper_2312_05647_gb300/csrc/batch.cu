@@ -300,7 +300,7 @@ int prepare(mjp_batch* b) {
 extern "C" {
 
 int expv_batch_create(mjp_batch** out, int kind, int n_inst, const int64_t* N, const double* theta,
-                      const double* t, const int64_t* s0, int precision) {
+                      const double* t, const int64_t* s0, int precision) try {
   if (!out) return fail(MJP_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (kind != MJP_BD1D) return fail(MJP_ERR_UNSUPPORTED, "batches hold birth-death instances (MJP_BD1D)");
@@ -341,15 +341,19 @@ int expv_batch_create(mjp_batch** out, int kind, int n_inst, const int64_t* N, c
   cudaGetLastError();
   *out = b;
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int expv_batch_offsets(const mjp_batch* b, int64_t* offsets) {
+int expv_batch_offsets(const mjp_batch* b, int64_t* offsets) try {
   if (!b || !offsets) return fail(MJP_ERR_ARG, "NULL argument");
   std::copy(b->off.begin(), b->off.end(), offsets);
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int expv_batch_run(mjp_batch* b, void* out, int use_graph, void* stream) {
+int expv_batch_run(mjp_batch* b, void* out, int use_graph, void* stream) try {
   if (!b || !out) return fail(MJP_ERR_ARG, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
   int rc = prepare(b);
@@ -380,9 +384,11 @@ int expv_batch_run(mjp_batch* b, void* out, int use_graph, void* stream) {
   }
   MJP_CUDA(cudaGraphLaunch(b->exec, s));
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int expv_batch_check(mjp_batch* b, void* stream) {
+int expv_batch_check(mjp_batch* b, void* stream) try {
   if (!b) return fail(MJP_ERR_ARG, "NULL batch");
   MJP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   if (!b->d_status.p) return MJP_OK;
@@ -392,9 +398,11 @@ int expv_batch_check(mjp_batch* b, void* stream) {
   if (st == kStatusKcap) return fail(MJP_ERR_KCAP, "truncation index K above the cap");
   if (st) return fail(MJP_ERR_NUMERIC, "device reported a numerical error");
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int expv_batch_tune(mjp_batch* b, void* out, void* stream, char* cfg, int cfg_len) {
+int expv_batch_tune(mjp_batch* b, void* out, void* stream, char* cfg, int cfg_len) try {
   if (!b || !out) return fail(MJP_ERR_ARG, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
   int rc = prepare(b);
@@ -488,9 +496,11 @@ int expv_batch_tune(mjp_batch* b, void* out, void* stream, char* cfg, int cfg_le
                b->heavy_factor, best, heavy);
   }
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int expv_batch_set_option(mjp_batch* b, int option, int64_t value) {
+int expv_batch_set_option(mjp_batch* b, int option, int64_t value) try {
   if (!b) return fail(MJP_ERR_ARG, "NULL batch");
   switch (option) {
     case MJP_OPT_CHAIN:
@@ -511,6 +521,8 @@ int expv_batch_set_option(mjp_batch* b, int option, int64_t value) {
   }
   b->grouped = false;
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 void expv_batch_destroy(mjp_batch* b) { delete b; }

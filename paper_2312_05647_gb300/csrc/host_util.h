@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <new>
+#include <stdexcept>
 #include <string>
 
 #include "mjp.h"
@@ -15,6 +17,30 @@ std::string& last_error();
 
 inline int fail(int code, const std::string& msg) {
   last_error() = msg;
+  return code;
+}
+
+// Status of the exception being handled: no C++ exception crosses the C ABI.
+// Every entry point returning a status ends in a handler that calls this; a
+// failed host allocation (std::bad_alloc, std::length_error) is MJP_ERR_ALLOC,
+// anything else MJP_ERR_ARG.  Call only inside a catch block.
+inline int exception_status() noexcept {
+  int code = MJP_ERR_ARG;
+  const char* msg = "unexpected host-side exception";
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    code = MJP_ERR_ALLOC;
+    msg = "host allocation failed";
+  } catch (const std::length_error&) {
+    code = MJP_ERR_ALLOC;
+    msg = "host allocation too large";
+  } catch (...) {
+  }
+  try {
+    last_error() = msg;
+  } catch (...) {
+  }
   return code;
 }
 

@@ -357,7 +357,7 @@ const void* mlp_norm(const mjp_mlp* net) { return net->norm.p; }
 
 extern "C" {
 
-int mjp_mlp_create(mjp_mlp** out, uint64_t seed) {
+int mjp_mlp_create(mjp_mlp** out, uint64_t seed) try {
   if (!out) return fail(MJP_ERR_ARG, "NULL out");
   *out = nullptr;
   mjp_mlp* net = new mjp_mlp();
@@ -387,6 +387,8 @@ int mjp_mlp_create(mjp_mlp** out, uint64_t seed) {
   }
   *out = net;
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 void mjp_mlp_destroy(mjp_mlp* net) {
@@ -398,7 +400,7 @@ void mjp_mlp_destroy(mjp_mlp* net) {
   delete net;
 }
 
-int mjp_mlp_set_params(mjp_mlp* net, const float* params, const double* norm, int where, void* stream) {
+int mjp_mlp_set_params(mjp_mlp* net, const float* params, const double* norm, int where, void* stream) try {
   if (!net) return fail(MJP_ERR_ARG, "NULL network");
   int rc = check_where(where);
   if (rc) return rc;
@@ -430,9 +432,11 @@ int mjp_mlp_set_params(mjp_mlp* net, const float* params, const double* norm, in
   net->t = 0;
   MJP_CUDA(cudaStreamSynchronize(s));
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_mlp_get_params(mjp_mlp* net, float* params, double* norm, int where, void* stream) {
+int mjp_mlp_get_params(mjp_mlp* net, float* params, double* norm, int where, void* stream) try {
   if (!net) return fail(MJP_ERR_ARG, "NULL network");
   int rc = check_where(where);
   if (rc) return rc;
@@ -442,9 +446,11 @@ int mjp_mlp_get_params(mjp_mlp* net, float* params, double* norm, int where, voi
   if (norm) MJP_CUDA(cudaMemcpyAsync(norm, net->norm.p, sizeof(Norm), k, s));
   if (where == MJP_PTR_HOST) MJP_CUDA(cudaStreamSynchronize(s));
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_mlp_fit_norm(mjp_mlp* net, const double* psi, const double* y, int64_t n, int where, void* stream) {
+int mjp_mlp_fit_norm(mjp_mlp* net, const double* psi, const double* y, int64_t n, int where, void* stream) try {
   if (!net || !psi || !y) return fail(MJP_ERR_ARG, "NULL argument");
   if (n < 1) return fail(MJP_ERR_ARG, "n must be >= 1");
   int rc = check_where(where);
@@ -456,9 +462,11 @@ int mjp_mlp_fit_norm(mjp_mlp* net, const double* psi, const double* y, int64_t n
   MJP_CUDA(cudaGetLastError());
   if (where == MJP_PTR_HOST) MJP_CUDA(cudaStreamSynchronize(s));
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_mlp_forward(mjp_mlp* net, const double* psi, int64_t n, double* out, int where, void* stream) {
+int mjp_mlp_forward(mjp_mlp* net, const double* psi, int64_t n, double* out, int where, void* stream) try {
   if (!net || !psi || !out) return fail(MJP_ERR_ARG, "NULL argument");
   if (n < 1) return fail(MJP_ERR_ARG, "n must be >= 1");
   int rc = check_where(where);
@@ -484,10 +492,12 @@ int mjp_mlp_forward(mjp_mlp* net, const double* psi, int64_t n, double* out, int
     MJP_CUDA(cudaStreamSynchronize(s));
   }
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 int mjp_mlp_loss_grad(mjp_mlp* net, const double* psi, const double* y, int64_t n, double* loss, float* grad,
-                      int where, void* stream) {
+                      int where, void* stream) try {
   if (!net || !psi || !y) return fail(MJP_ERR_ARG, "NULL argument");
   if (n < 1 || n > 0xFFFFFFFFLL) return fail(MJP_ERR_ARG, "n must be in [1, 2^32)");
   int rc = check_where(where);
@@ -528,10 +538,12 @@ int mjp_mlp_loss_grad(mjp_mlp* net, const double* psi, const double* y, int64_t 
     MJP_CUDA(cudaStreamSynchronize(s));
   }
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 int mjp_mlp_train(mjp_mlp* net, const double* psi, const double* y, int64_t n, const mjp_train_cfg* cfg,
-                  double* losses, int where, void* stream) {
+                  double* losses, int where, void* stream) try {
   if (!net || !psi || !y || !cfg) return fail(MJP_ERR_ARG, "NULL argument");
   if (n < 1 || n > 0xFFFFFFFFLL) return fail(MJP_ERR_ARG, "n must be in [1, 2^32)");
   if (cfg->steps < 1 || cfg->steps > 0xFFFFFFFFLL) return fail(MJP_ERR_ARG, "steps must be in [1, 2^32)");
@@ -601,6 +613,8 @@ int mjp_mlp_train(mjp_mlp* net, const double* psi, const double* y, int64_t n, c
     MJP_CUDA(cudaStreamSynchronize(s));
   }
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 }  // extern "C"

@@ -40,7 +40,7 @@ size_t up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 extern "C" int expv_series_static(int kind, const int64_t* dims, int ndims, const double* theta, int ntheta,
                                   const float* rho0, const double* times, int ntimes, float* out,
-                                  void* stream) {
+                                  void* stream) try {
   using namespace mjp;
   if (!dims || !theta || !rho0 || !times || !out) return fail(MJP_ERR_ARG, "NULL argument");
   if (ntimes < 1 || ntimes > kMaxTimes) return fail(MJP_ERR_ARG, "ntimes must be in [1, 256]");
@@ -161,4 +161,6 @@ extern "C" int expv_series_static(int kind, const int64_t* dims, int ndims, cons
   if (st_host == kStatusKcap) return fail(MJP_ERR_KCAP, "truncation index K above the cap");
   if (st_host != 0) return fail(MJP_ERR_NUMERIC, "device reported a numerical error");
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }

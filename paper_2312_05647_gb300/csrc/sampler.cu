@@ -710,7 +710,7 @@ int64_t sum_count(const std::vector<int64_t>& cnt, int which) {
 extern "C" {
 
 int mjp_sampler_create(mjp_sampler** out, mjp_model* m, const mjp_obs* obs, int chains, int64_t capacity,
-                       int64_t eval_capacity, uint64_t seed) {
+                       int64_t eval_capacity, uint64_t seed) try {
   if (!out || !m || !obs) return fail(MJP_ERR_ARG, "NULL argument");
   *out = nullptr;
   if (chains < 1 || chains > 4096) return fail(MJP_ERR_ARG, "chains must be in [1, 4096]");
@@ -768,6 +768,8 @@ int mjp_sampler_create(mjp_sampler** out, mjp_model* m, const mjp_obs* obs, int 
   }
   *out = s;
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 void mjp_sampler_destroy(mjp_sampler* s) {
@@ -776,7 +778,7 @@ void mjp_sampler_destroy(mjp_sampler* s) {
   delete s;
 }
 
-int mjp_sampler_set_state(mjp_sampler* s, const double* psi, int where, void* stream) {
+int mjp_sampler_set_state(mjp_sampler* s, const double* psi, int where, void* stream) try {
   if (!s || !psi) return fail(MJP_ERR_ARG, "NULL argument");
   if (where != MJP_PTR_HOST && where != MJP_PTR_DEVICE) return fail(MJP_ERR_ARG, "bad where");
   cudaStream_t st = (cudaStream_t)stream;
@@ -803,9 +805,11 @@ int mjp_sampler_set_state(mjp_sampler* s, const double* psi, int where, void* st
   set_best_kernel<<<blocks_for(s->C, 128), 128, 0, st>>>(d);
   MJP_CUDA(cudaGetLastError());
   return settle(s, st);
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_sampler_get_state(mjp_sampler* s, double* psi, double* ll, int where, void* stream) {
+int mjp_sampler_get_state(mjp_sampler* s, double* psi, double* ll, int where, void* stream) try {
   if (!s) return fail(MJP_ERR_ARG, "NULL sampler");
   if (where != MJP_PTR_HOST && where != MJP_PTR_DEVICE) return fail(MJP_ERR_ARG, "bad where");
   cudaStream_t st = (cudaStream_t)stream;
@@ -814,9 +818,11 @@ int mjp_sampler_get_state(mjp_sampler* s, double* psi, double* ll, int where, vo
   if (ll) MJP_CUDA(cudaMemcpyAsync(ll, s->ll.p, (size_t)s->C * sizeof(double), k, st));
   if (where == MJP_PTR_HOST) MJP_CUDA(cudaStreamSynchronize(st));
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_sampler_set_cov(mjp_sampler* s, const double* Z, void* stream) {
+int mjp_sampler_set_cov(mjp_sampler* s, const double* Z, void* stream) try {
   if (!s || !Z) return fail(MJP_ERR_ARG, "NULL argument");
   for (int i = 0; i < 16; ++i)
     if (!std::isfinite(Z[i])) return fail(MJP_ERR_ARG, "Z must be finite");
@@ -824,17 +830,21 @@ int mjp_sampler_set_cov(mjp_sampler* s, const double* Z, void* stream) {
     for (int b = 0; b < a; ++b)
       if (Z[a * 4 + b] != Z[b * 4 + a]) return fail(MJP_ERR_ARG, "Z must be symmetric");
   return set_cov_device(s, Z, (cudaStream_t)stream);
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_sampler_get_cov(mjp_sampler* s, double* Z, void* stream) {
+int mjp_sampler_get_cov(mjp_sampler* s, double* Z, void* stream) try {
   if (!s || !Z) return fail(MJP_ERR_ARG, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
   MJP_CUDA(cudaMemcpyAsync(Z, s->Z.p, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
   MJP_CUDA(cudaStreamSynchronize(st));
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_sampler_adapt_cov(mjp_sampler* s, int64_t window, double eps, void* stream) {
+int mjp_sampler_adapt_cov(mjp_sampler* s, int64_t window, double eps, void* stream) try {
   if (!s) return fail(MJP_ERR_ARG, "NULL sampler");
   if (window < 2 || window > s->cap) return fail(MJP_ERR_ARG, "window must be in [2, capacity]");
   if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(MJP_ERR_ARG, "eps must be finite and >= 0");
@@ -851,9 +861,11 @@ int mjp_sampler_adapt_cov(mjp_sampler* s, int64_t window, double eps, void* stre
   MJP_CUDA(cudaStreamSynchronize(st));
   if (!s->h_ctl[2]) return fail(MJP_ERR_NUMERIC, "updated Z is not positive definite (Z kept)");
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_sampler_run_plain(mjp_sampler* s, int64_t iters, int rec, void* stream) {
+int mjp_sampler_run_plain(mjp_sampler* s, int64_t iters, int rec, void* stream) try {
   if (!s) return fail(MJP_ERR_ARG, "NULL sampler");
   if (iters < 0) return fail(MJP_ERR_ARG, "iters must be >= 0");
   cudaStream_t st = (cudaStream_t)stream;
@@ -870,9 +882,11 @@ int mjp_sampler_run_plain(mjp_sampler* s, int64_t iters, int rec, void* stream) 
     s->rounds += 1;
   }
   return settle(s, st);
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_sampler_run_da(mjp_sampler* s, mjp_mlp* net, int64_t iters, int max_inner, int rec, void* stream) {
+int mjp_sampler_run_da(mjp_sampler* s, mjp_mlp* net, int64_t iters, int max_inner, int rec, void* stream) try {
   if (!s || !net) return fail(MJP_ERR_ARG, "NULL argument");
   if (iters < 0) return fail(MJP_ERR_ARG, "iters must be >= 0");
   if (max_inner < 1 || max_inner > 1024) return fail(MJP_ERR_ARG, "max_inner must be in [1, 1024]");
@@ -903,9 +917,11 @@ int mjp_sampler_run_da(mjp_sampler* s, mjp_mlp* net, int64_t iters, int max_inne
     if (nactive == 0) break;
   }
   return settle(s, st);
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_sampler_clear(mjp_sampler* s, int evals, void* stream) {
+int mjp_sampler_clear(mjp_sampler* s, int evals, void* stream) try {
   if (!s) return fail(MJP_ERR_ARG, "NULL sampler");
   cudaStream_t st = (cudaStream_t)stream;
   MJP_CUDA(cudaMemsetAsync(s->cnt.p, 0, (size_t)s->C * NCNT * sizeof(int64_t), st));
@@ -918,9 +934,11 @@ int mjp_sampler_clear(mjp_sampler* s, int evals, void* stream) {
   if (evals) s->evn = 0;
   s->rounds = 0;
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_sampler_stats_get(mjp_sampler* s, mjp_sampler_stats* out, void* stream) {
+int mjp_sampler_stats_get(mjp_sampler* s, mjp_sampler_stats* out, void* stream) try {
   if (!s || !out) return fail(MJP_ERR_ARG, "NULL argument");
   std::vector<int64_t> cnt, nrec;
   int rc = read_counts(s, (cudaStream_t)stream, cnt, &nrec);
@@ -935,9 +953,11 @@ int mjp_sampler_stats_get(mjp_sampler* s, mjp_sampler_stats* out, void* stream) 
   out->kept = std::max<int64_t>(kept, 0);
   out->evals_kept = s->evn;
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_sampler_trace(mjp_sampler* s, double* out, int where, void* stream) {
+int mjp_sampler_trace(mjp_sampler* s, double* out, int where, void* stream) try {
   if (!s || !out) return fail(MJP_ERR_ARG, "NULL argument");
   if (where != MJP_PTR_HOST && where != MJP_PTR_DEVICE) return fail(MJP_ERR_ARG, "bad where");
   cudaStream_t st = (cudaStream_t)stream;
@@ -964,17 +984,21 @@ int mjp_sampler_trace(mjp_sampler* s, double* out, int where, void* stream) {
     tmp.release();
   }
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_sampler_evals(mjp_sampler* s, const double** psi, const double** ll, int64_t* n) {
+int mjp_sampler_evals(mjp_sampler* s, const double** psi, const double** ll, int64_t* n) try {
   if (!s || !psi || !ll || !n) return fail(MJP_ERR_ARG, "NULL argument");
   *psi = s->evpsi.as<double>();
   *ll = s->evll.as<double>();
   *n = s->evn;
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
-int mjp_sampler_adapt(mjp_sampler* s, const mjp_adapt_cfg* cfg, mjp_adapt_report* rep, void* stream) {
+int mjp_sampler_adapt(mjp_sampler* s, const mjp_adapt_cfg* cfg, mjp_adapt_report* rep, void* stream) try {
   if (!s || !cfg) return fail(MJP_ERR_ARG, "NULL argument");
   if (cfg->cycle < 1 || cfg->every < cfg->cycle || cfg->every % cfg->cycle != 0)
     return fail(MJP_ERR_ARG, "every must be a positive multiple of cycle");
@@ -1027,10 +1051,12 @@ int mjp_sampler_adapt(mjp_sampler* s, const mjp_adapt_cfg* cfg, mjp_adapt_report
   }
   if (rep) *rep = r;
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 int mjp_ess(const double* trace, int64_t chains, int64_t len, int params, double* ess, double* mean, double* var,
-            double* mcse_mean, double* mcse_var, int where, void* stream) {
+            double* mcse_mean, double* mcse_var, int where, void* stream) try {
   if (!trace) return fail(MJP_ERR_ARG, "NULL trace");
   if (chains < 1 || len < 4 || params < 1 || params > 1024) return fail(MJP_ERR_ARG, "bad trace shape");
   if (chains * (int64_t)params > (int64_t)1 << 30) return fail(MJP_ERR_ARG, "trace too large");
@@ -1077,6 +1103,8 @@ int mjp_ess(const double* trace, int64_t chains, int64_t len, int params, double
   cev.release();
   res.release();
   return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
 }
 
 }  // extern "C"
