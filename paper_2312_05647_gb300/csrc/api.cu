@@ -47,7 +47,7 @@ struct mjp_model {
   int64_t N = 0, M = 0, P = 1;
   std::vector<double> theta;
   // options
-  int renorm = 0;
+  int renorm = kDefectPeriod;  // MJP_OPT_RENORM_PERIOD
   int64_t kcap = (int64_t)1 << 26;
   int threads = 0;
   int chain = 0;  // MJP_OPT_CHAIN
@@ -474,7 +474,8 @@ int rate_model_set_option(mjp_model* m, int option, int64_t value) try {
   if (!m) return fail(MJP_ERR_ARG, "NULL model");
   switch (option) {
     case MJP_OPT_RENORM_PERIOD:
-      if (value < 0 || value > (1 << 30)) return fail(MJP_ERR_ARG, "renorm period out of range");
+      if (value < 0 || value > (1 << 20) || value % 8 != 0)
+        return fail(MJP_ERR_ARG, "renorm period must be 0 or a multiple of 8 in [8, 2^20]");
       m->renorm = (int)value;
       return MJP_OK;
     case MJP_OPT_K_CAP:
@@ -700,17 +701,17 @@ int expv_series(mjp_model* m, const void* rho0, const double* times, int ntimes,
   }
 
   // Birth-death chains: the register-resident kernel (one CTA, or the fewest
-  // CTAs of a cluster that hold the chain, halo 32) unless renormalisation or
-  // a thread count is asked for.
+  // CTAs of a cluster that hold the chain, halo 32) unless a thread count is
+  // asked for.
   Reg1dPlan rp1 = {};
   bool use_reg1 = false;
-  if (m->kind == MJP_BD1D && m->chain != 1 && m->threads == 0 && !(m->precision == MJP_FP32 && m->renorm > 0)) {
+  if (m->kind == MJP_BD1D && m->chain != 1 && m->threads == 0) {
     const int c0 = m->cluster > 0 ? m->cluster : 1, c1 = m->cluster > 0 ? m->cluster : 8;
     for (int c = c0; c <= c1 && !use_reg1; ++c) use_reg1 = chain_reg1d_plan(m->precision, m->N, nt, c, 32, &rp1, true);
   }
   if (m->chain == 2 && m->kind == MJP_BD1D && !use_reg1)
     return fail(MJP_ERR_UNSUPPORTED, "the register-resident expv chain needs a birth-death model without "
-                                     "renormalisation or a forced thread count that fits 8 CTAs");
+                                     "a forced thread count that fits 8 CTAs");
   int C = 0, T = 0;
   int64_t slab = 0;
   int rc = 0;
@@ -999,16 +1000,15 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   int64_t slab = 0;
   // The chain keeps a generic member list only for groups of > 2 members.
   const int nmem_list = obs->maxmem > 2 ? obs->nmem : 0;
-  // Register-resident chain: FP32 mRNA/protein boxes, no renormalisation, no
-  // forced launch shape.
+  // Register-resident chain: FP32 mRNA/protein boxes, no forced launch shape.
   RegPlan rp = {};
   bool use_reg = false;
-  if (m->chain != 1 && m->kind == MJP_MRNA_PROT2D && m->precision == MJP_FP32 && m->renorm == 0 &&
+  if (m->chain != 1 && m->kind == MJP_MRNA_PROT2D && m->precision == MJP_FP32 &&
       (m->chain == 2 || (m->cluster == 0 && m->threads == 0)))
     use_reg = chain_reg2d_plan(m->M, m->P, nt, obs->nmem, 8, m->threads, &rp);
   if (m->chain == 2 && !use_reg)
     return fail(MJP_ERR_UNSUPPORTED, "the register-resident chain needs an FP32 mRNA/protein box without "
-                                     "renormalisation that fits 8 CTAs");
+                                     "a forced thread count that fits 8 CTAs");
   int rc = 0;
   if (!use_reg && (rc = stencil_config(m, 1, nt, obs->G, nmem_list, &C, &T, &slab))) return rc;
   if ((rc = ensure_status(m))) return rc;

@@ -68,6 +68,7 @@ struct mjp_batch {
   int chain = 0;
   int reg_heavy_cluster = 4, reg_halo = 32;
   double reg_heavy_factor = 1.0;
+  int renorm = kDefectPeriod;  // FP32: exit-defect correction period (MJP_OPT_RENORM_PERIOD)
   int sms = 152;
   Group groups[kGroups];
   bool uploaded = false, grouped = false;
@@ -277,7 +278,7 @@ int enqueue(mjp_batch* b, void* out, cudaStream_t s) {
     cp.M = 1; cp.P = 1; cp.N = 1; cp.ntheta = 2; cp.theta = pp.theta; cp.B = (int)g.jobs.size();
     cp.ntimes = 1; cp.orig = nullptr; cp.win = pp.win; cp.info = pp.info; cp.rho0 = nullptr;
     cp.out = out; cp.out_stride = 0; cp.comp = b->d_comp.as<float>(); cp.comp_stride = 0;
-    cp.renorm = 0; cp.slab = 1; cp.status = pp.status;
+    cp.renorm = b->precision == MJP_FP32 ? b->renorm : 0; cp.slab = 1; cp.status = pp.status;
     cp.jobN = pp.jobN; cp.job_off = b->d_off.as<int64_t>(); cp.job_map = g.d_map.as<int32_t>();
     cp.job_s0 = b->d_s0.as<int64_t>(); cp.tile_max = g.tile; cp.arena = b->d_arena.p;
     if (g.reg) MJP_CUDA(launch_chain_reg1d(b->precision, cp, g.rp, b->side[gi]));
@@ -515,6 +516,11 @@ int expv_batch_set_option(mjp_batch* b, int option, int64_t value) try {
     case MJP_OPT_HALO:
       if (value < 1 || value > 1024) return fail(MJP_ERR_ARG, "halo must be in [1, 1024]");
       b->reg_halo = (int)value;
+      break;
+    case MJP_OPT_RENORM_PERIOD:
+      if (value < 0 || value > (1 << 20) || value % 8 != 0)
+        return fail(MJP_ERR_ARG, "renorm period must be 0 or a multiple of 8 in [8, 2^20]");
+      b->renorm = (int)value;
       break;
     default:
       return fail(MJP_ERR_ARG, "option not supported by batches");

@@ -151,5 +151,100 @@ __device__ __forceinline__ double2 v_fma(double2 a, double2 b, double2 c) {
 __device__ __forceinline__ float2 v_make(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 v_make(double a, double b) { return make_double2(a, b); }
 
+// Compensated FP32 jump.  A chain stored in FP32 loses about half an ulp of
+// every state at every jump, and over the tens of thousands of jumps of a
+// slowly relaxing chain these roundings add up coherently (relative errors of
+// 1e-4 at K ~ 7e4).  The compensated jump writes the update in delta form,
+//   t = lo_n + sum_{m -> n} rho_m lambda_mn / Omega - (e_n / Omega) rho_n,
+//   y = rho_n + t,   lo_n <- t - (y - rho_n),
+// so each state carries the part of t that the addition rounded away (its
+// residual lo_n) into the next jump instead of losing it.  The value of the
+// chain is rho_n + lo_n; only rho_n is read by the neighbours and by the
+// weighted sum (lo_n is below half an ulp of rho_n).
+//
+// Column sums of B are 1 (Eq. B_def) only in exact arithmetic: the exit
+// coefficient e_n / Omega, rounded to FP32, differs from the sum of the
+// rounded outflow coefficients the neighbours apply by a defect d_n of up to
+// half an ulp, which creates or destroys mass at every jump.  Every
+// kDefectPeriod jumps each state adds kDefectPeriod d_n rho_n to its residual
+// (d_n formed exactly in FP64 from the FP32 coefficients), which restores the
+// conservation of B to second order in the period.  Both corrections are
+// local to a state, so every thread layout, cluster shape and halo gives
+// bit-identical chains.  The period is MJP_OPT_RENORM_PERIOD (default
+// kDefectPeriod, a multiple of every register kernel's round length).
+
+__device__ __forceinline__ float comp_finish(float cur, float t, float& lo) {
+  const float y = __fadd_rn(cur, t);
+  lo = __fsub_rn(t, __fsub_rn(y, cur));
+  return y;
+}
+__device__ __forceinline__ float2 comp_finish(float2 cur, float2 t, float2& lo) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  const float2 y = __fadd2_rn(cur, t);
+  lo = __ffma2_rn(__ffma2_rn(cur, m1, y), m1, t);  // t - (y - cur), each step exact as in comp_finish(float)
+  return y;
+}
+// One compensated birth-death jump of a pair: inflows from the left (birth)
+// and right (death), then the exit ne = -e_n / Omega.
+__device__ __forceinline__ float2 comp_jump(float2 cur, float2& lo, float2 cl, float2 left, float2 cr, float2 right,
+                                            float2 ne) {
+  float2 t = __ffma2_rn(cl, left, lo);
+  t = __ffma2_rn(cr, right, t);
+  t = __ffma2_rn(ne, cur, t);
+  return comp_finish(cur, t, lo);
+}
+__device__ __forceinline__ float comp_jump(float cur, float& lo, float cl, float left, float cr, float right,
+                                           float ne) {
+  float t = __fmaf_rn(cl, left, lo);
+  t = __fmaf_rn(cr, right, t);
+  t = __fmaf_rn(ne, cur, t);
+  return comp_finish(cur, t, lo);
+}
+
+// Exit defects (exit coefficient minus the outflow coefficients that the
+// neighbours apply) of the models whose FP32 chains run in more than one
+// kernel; every kernel forms them with these functions, so the corrections
+// agree to the bit.
+//
+// Birth-death state n: exit fl(fl(gamma n) + beta'), outflows beta' (to n+1,
+// absent at N-1) and fl(gamma n) (to n-1); the defect is the rounding error
+// of one addition, exact in FP64 and in FP32.
+template <typename T>
+__device__ __forceinline__ float bd_defect(const Coef<T>& co, int n, int N) {
+  const float bn = __fmul_rn((float)co.b, (float)n);
+  const float ain = n + 1 < N ? (float)co.a : 0.0f;
+  const float e = __fadd_rn(bn, ain);
+  return (float)(((double)e - (double)bn) - (double)ain);
+}
+// mRNA/protein column m: e0 = fl(fl(fl(gamma_m m) + k_m') + fl(k_p m)) (k_m'
+// = k_m below the last column), the exit without the protein decay, and its
+// column defect e0 - (its three outflows), formed in FP64 and rounded.
+struct MrnaCol {
+  float e0, eps;
+};
+template <typename T>
+__device__ __forceinline__ MrnaCol mrna_col(const Coef<T>& co, int m, int M) {
+  const float bm = __fmul_rn((float)co.b, (float)m);
+  const float ain = m + 1 < M ? (float)co.a : 0.0f;
+  const float cd = __fmul_rn((float)co.c, (float)m);
+  MrnaCol r;
+  r.e0 = __fadd_rn(__fadd_rn(bm, ain), cd);
+  r.eps = (float)((((double)r.e0 - (double)bm) - (double)ain) - (double)cd);
+  return r;
+}
+// Defect of state (m, p): the chain's exit is e = fl(e0 + gamma_p p) (one
+// fused multiply-add) and the outflow to p-1 is fl(gamma_p p); the row part
+// e - e0 - fl(gamma_p p) is formed exactly (both subtractions are of numbers
+// within a factor of two of each other), then added to the column part.  In
+// row P-1 the exit adds k_p m back as a separate term and the outflow to p+1
+// is absent, so the same defect holds there.
+__device__ __forceinline__ float mrna_defect(const MrnaCol& col, float gp, int p) {
+  const float fp = (float)p;
+  const float e = __fmaf_rn(gp, fp, col.e0);
+  const float dpf = __fmul_rn(gp, fp);
+  const float row = dpf >= col.e0 ? __fsub_rn(__fsub_rn(e, dpf), col.e0) : __fsub_rn(__fsub_rn(e, col.e0), dpf);
+  return __fadd_rn(col.eps, row);
+}
+
 }  // namespace
 }  // namespace mjp

@@ -14,6 +14,9 @@ constexpr int kMaxGroups = 8192;   // observation groups per loglik call
 constexpr int kMaxTheta = 8;
 constexpr int kWeightLead = 4;   // jumps the weight prefetch runs ahead
 constexpr int kWeightRing = 6;   // ring slots (> lead + 1)
+// Default period (jumps) of the exit-defect correction of the compensated
+// FP32 chain (MJP_OPT_RENORM_PERIOD; chain_common.cuh).
+constexpr int kDefectPeriod = 32;
 
 // Device status word bits (first error wins; read by rate_model_check).
 enum DevStatus : int {
@@ -99,7 +102,7 @@ struct ChainParams {
   int G;
   int nmem;                // length of the generic member list kept on chip (0: every group has <= 2 members)
   double* ll;              // device, B
-  int renorm;              // period in jumps (0 = off)
+  int renorm;              // FP32: period in jumps of the exit-defect correction (0 = off)
   int64_t slab;            // states per CTA of the cluster (whole rows for 2-D models)
   int* status;
   // Batches of uneven birth-death instances (all nullable):
@@ -167,7 +170,7 @@ struct RegPlan {
   int rows;      // rows per CTA (a multiple of 2 qr)
   int nq;        // column quads (ceil(M / 4))
   int qr;        // row pairs per thread (4 or 5)
-  int tmax;      // threads per CTA at most: 512 (one CTA per SM) or 256 (two)
+  int tmax;      // threads per CTA at most (384, one CTA per SM)
   int threads;   // per CTA, including the weights warp
   size_t smem;   // dynamic shared memory per CTA
 };

@@ -152,7 +152,7 @@ extern "C" int expv_series_static(int kind, const int64_t* dims, int ndims, cons
   cp.ntheta = ntheta; cp.theta = pp.theta; cp.B = 1; cp.ntimes = ntimes;
   cp.orig = reinterpret_cast<const int32_t*>(base + o_orig); cp.win = pp.win; cp.info = pp.info; cp.rho0 = rho0;
   cp.out = out; cp.out_stride = 0; cp.comp = reinterpret_cast<float*>(base + o_comp); cp.comp_stride = 0;
-  cp.renorm = 0; cp.slab = slab; cp.status = d_status;
+  cp.renorm = kDefectPeriod; cp.slab = slab; cp.status = d_status;
   MJP_CUDA(launch_chain_stencil(kind, MJP_FP32, 0, cp, C, threads, s));
 
   int st_host = 0;

@@ -26,6 +26,11 @@
 // Modes: EXPV writes rho*(t_i) (FP32: Kahan-compensated, compensation in a
 // global scratch buffer; FP64: plain), LOGLIK accumulates only the observed
 // groups in shared memory and finishes with sum_g c_g log(a_g).
+//
+// FP32 chains run the compensated jump of chain_common.cuh: every state
+// carries its rounding residual (a third tile, single-buffered: only the
+// state's owner touches it) and, every p.renorm jumps, adds back the defect
+// of its exit coefficient (a fourth tile, formed once in the prologue).
 #include <cooperative_groups.h>
 
 #include "chain_common.cuh"
@@ -83,7 +88,7 @@ __host__ __device__ inline int tile_elems(int kind, int M, int P, int N, int sla
 }
 
 struct Smem {
-  size_t buf1, tx, tPL, ttail, tL, tK, twoff, twb, torig, pw, ring, red, memloc, gptr, mptr, gloc, gtime, acc_s,
+  size_t buf1, lo, cb, tx, tPL, ttail, tL, tK, twoff, twb, torig, pw, ring, red, memloc, gptr, mptr, gloc, gtime, acc_s,
       acc_c, total;
 };
 
@@ -92,6 +97,11 @@ __host__ __device__ inline Smem smem_layout(size_t elt, int tile, int nt, int G,
   size_t bufbytes = align_up((size_t)tile * elt, 16);
   s.buf1 = bufbytes;
   size_t o = 2 * bufbytes;
+  // FP32: residual and defect of every state, tile-shaped.
+  s.lo = o;
+  if (elt == 4) o += bufbytes;
+  s.cb = o;
+  if (elt == 4) o += bufbytes;
   s.tx = o; o += 8 * (size_t)nt;
   s.tPL = o; o += 8 * (size_t)nt;
   s.ttail = o; o += 8 * (size_t)nt;
@@ -128,6 +138,46 @@ __host__ __device__ inline Smem smem_layout(size_t elt, int tile, int nt, int G,
   return s;
 }
 
+// Exit defect of the state in tile row `row`, column `col` for the compensated
+// FP32 chain (see chain_common.cuh): the exit coefficient the update applies
+// minus the sum of the outflow coefficients its neighbours apply.  Birth-death
+// and mRNA/protein use the shared forms (their chains also run in the
+// register-resident kernels); the two-state and autoregulatory models form it
+// in FP64 from the FP32 coefficients of the update below.
+template <int KIND, typename T>
+__device__ float exit_defect(const Coef<T>& co, int row, int col, int M, int P) {
+  if (KIND == MJP_BD1D) return bd_defect(co, col, M);
+  if (KIND == MJP_MRNA_PROT2D) return mrna_defect(mrna_col(co, col, M), (float)co.d, row);
+  const float fm = (float)col;
+  if (KIND == MJP_TWOSTATE) {
+    const float bm = __fmul_rn((float)co.b, fm);
+    const float ain = col + 1 < M ? (float)co.a : 0.0f;
+    if (row == 0) {  // active: birth, death, deactivation
+      const float e = __fadd_rn(__fadd_rn(bm, ain), (float)co.d);
+      return (float)((((double)e - (double)bm) - (double)ain) - (double)co.d);
+    }
+    const float e = __fadd_rn((float)co.c, bm);  // inactive: activation, death
+    return (float)(((double)e - (double)co.c) - (double)bm);
+  }
+  // Autoregulatory network, tile row 2 q + sigma (Pm = P / 2 protein counts).
+  const int q = row >> 1, Pm = P / 2;
+  const float fq = (float)q;
+  const bool qtop = q + 1 >= Pm;
+  const float a_gm = __fmul_rn((float)co.c, fm);                // gamma_R m (to m-1)
+  const float a_tx = col + 1 < M ? (float)co.a : 0.0f;          // beta_R (to m+1, active)
+  const float tr = qtop ? 0.0f : __fmul_rn((float)co.b, fm);    // beta_P m (to q+1)
+  const float pd = __fmul_rn((float)co.d, fq);                  // gamma_P q (to q-1)
+  const float decay = __fadd_rn(pd, a_gm);
+  if ((row & 1) == 0) {
+    const float bind = __fmul_rn((float)co.f, fq);              // lambda_ina q (to q-1, inactive)
+    const float e = __fadd_rn(__fadd_rn(__fadd_rn(decay, a_tx), tr), bind);
+    return (float)(((((double)e - (double)a_tx) - (double)a_gm) - (double)tr) - (double)pd - (double)bind);
+  }
+  const float unb = qtop ? 0.0f : (float)co.e;                  // lambda_act (to q+1, active)
+  const float e = __fadd_rn(__fadd_rn(decay, tr), unb);
+  return (float)(((((double)e - (double)a_gm) - (double)tr) - (double)pd) - (double)unb);
+}
+
 template <typename T, int KIND, bool LL>
 __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -154,6 +204,9 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   const unsigned buf_off[2] = {0u, (unsigned)L.buf1};
   T* const buf0 = reinterpret_cast<T*>(smem);
   T* const buf1 = reinterpret_cast<T*>(smem + L.buf1);
+  constexpr bool kComp = sizeof(T) == 4;  // compensated FP32 chain
+  float* const lo_t = reinterpret_cast<float*>(smem + L.lo);  // residual of each state (FP32)
+  float* const cb_t = reinterpret_cast<float*>(smem + L.cb);  // p.renorm x exit defect (FP32)
   double* t_x = reinterpret_cast<double*>(smem + L.tx);
   double* t_PL = reinterpret_cast<double*>(smem + L.tPL);
   double* t_tail = reinterpret_cast<double*>(smem + L.ttail);
@@ -229,14 +282,18 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   for (int j = tid; j < tile; j += nthr) {
     buf0[j] = (T)0;
     buf1[j] = (T)0;
+    if (kComp) {
+      lo_t[j] = 0.0f;
+      cb_t[j] = 0.0f;
+    }
   }
   __syncthreads();
-  T msum = (T)0;
   for (int j = tid; j < g.W * g.H; j += nthr) {
     int r = j / g.W, c = j - r * g.W;
+    const int li = KIND == MJP_BD1D ? c + 1 : elem2d(g, r, c);
     T v = rho0_at(gidx(g.p0 + r, g.m0 + c));
-    buf0[KIND == MJP_BD1D ? c + 1 : elem2d(g, r, c)] = v;
-    msum += v;
+    buf0[li] = v;
+    if (kComp && p.renorm > 0) cb_t[li] = (float)p.renorm * exit_defect<KIND>(co, g.p0 + r, g.m0 + c, M, P);
   }
   // Halo of rho0 from global memory (later jumps receive it by push): the
   // row below a 2-D slab is the odd half of the bottom pad pair, the row above
@@ -279,25 +336,8 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     for (int i = warp; i < nt; i += nwarps)
       for (int q = (int)p.gptr[i] + lane; q < (int)p.gptr[i + 1]; q += 32) gtime[q] = (short)i;
   }
-  const bool rn = p.renorm > 0;
-  double mass0 = 1.0;
-  if (rn) {
-    double v = (double)msum;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if (lane == 0) red[warp] = v;
-  }
   if (C > 1) cluster.sync();
   else __syncthreads();
-  auto cluster_total = [&](const double* r0) {
-    double tot = 0.0;
-    for (int r = 0; r < C; ++r) {
-      const double* rr = (C == 1) ? r0 : cluster.map_shared_rank(r0, r);
-      for (int w = 0; w < nwarps; ++w) tot += rr[w];
-    }
-    return tot;
-  };
-  if (rn) mass0 = cluster_total(red);
   // Does any window lack a stored copy of its weights (arena overflow)?
   bool mine_rec = false;
   for (int i = tid; i < nt; i += nthr) mine_rec |= t_woff[i] < 0;
@@ -347,7 +387,7 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   // LOGLIK: acc_g += w_i f sum_{s in g} rho_k[s] over this CTA's states.
   // The groups of the active times [l, h] are one contiguous index range
   // (groups are stored time by time), so threads take groups directly.
-  auto group_accumulate = [&](const T* cur, int l, int h, const T* wts, T f) {
+  auto group_accumulate = [&](const T* cur, int l, int h, const T* wts) {
     if (h < l) return;
     const int ga = s_gptr[l], gb = s_gptr[h + 1];
     for (int gq = ga + acc_id; gq < gb; gq += acc_stride) {
@@ -366,7 +406,7 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
         }
       }
       if (!any) continue;
-      const T w = f_mul(wts[gtime[gq]], f);
+      const T w = wts[gtime[gq]];
       {
         if (sizeof(T) == 4) {
           float y = __fsub_rn(__fmul_rn((float)w, (float)v), acc_c[gq]);
@@ -430,7 +470,8 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     const T cr = f_mul(co.b, (T)(mc + 1));
     c_l = v_make(co.a, (T)0);
     c_r = v_make(cr, cr);
-    c_dg = v_make(f_sub(one, f_add(f_add(bm, mc + 1 < M ? co.a : (T)0), co.d)), f_sub(one, f_add(co.c, bm)));
+    const T ex = f_add(f_add(bm, mc + 1 < M ? co.a : (T)0), co.d), ey = f_add(co.c, bm);
+    c_dg = kComp ? v_make(-ex, -ey) : v_make(f_sub(one, ex), f_sub(one, ey));  // 1 - e (FP32: -e)
     c_sw = v_make(co.c, co.d);
   } else if (KIND == MJP_AUTOREG) {
     const T cr = f_mul(co.c, (T)(mc + 1));                 // gamma_R (m+1) from m+1
@@ -440,18 +481,18 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     const T fm = (T)mc;
     const T cr = f_mul(co.b, (T)(mc + 1));                 // gamma_m (m+1) from m+1
     cd = f_mul(co.c, fm);                                  // k_p m from p-1
-    const T d0 = f_sub(one, f_add(f_add(f_mul(co.b, fm), mc + 1 < M ? co.a : (T)0), cd));
+    const T e0 = f_add(f_add(f_mul(co.b, fm), mc + 1 < M ? co.a : (T)0), cd);
+    const T d0 = kComp ? -e0 : f_sub(one, e0);
     c_l = v_make(co.a, co.a);                              // k_m from m-1
     c_r = v_make(cr, cr);
     c_d = v_make(cd, cd);
-    c_dg = v_make(d0, d0);                                 // 1 - e without gamma_p p
+    c_dg = v_make(d0, d0);                                 // 1 - e without gamma_p p (FP32: -e)
     c_gp = v_make(co.d, co.d);                             // gamma_p
     c_ngp = v_make(-co.d, -co.d);
   }
   const T2 two2 = v_make((T)2, (T)2);
 
   // ---- the jump chain -----------------------------------------------------
-  bool renorm_prev = false;  // was rho_{k-1}'s mass reduced at jump k-1?
   for (int64_t k = 1; k <= Kmax + 1; ++k) {
     const int par = (int)((k - 1) & 1);
     const T* src = reinterpret_cast<const T*>(smem + buf_off[par]);
@@ -464,11 +505,8 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     int clo = lo, chi = hi;
     advance(k, clo, chi);
     const bool jump = k <= Kmax;
-    T f = one;  // renormalisation factor carried by rho_{k-1}
-    if (renorm_prev) {
-      double tot = cluster_total(red + (int)((k - 1) & 1) * 33);
-      f = (T)(tot > 0.0 ? mass0 / tot : 1.0);
-    }
+    // FP32: the exit defects are added back after jumps that are multiples of p.renorm.
+    const bool dfix = kComp && p.renorm > 0 && jump && (k % p.renorm) == 0;
     if (wwarp) {
       // Weights of jump k + lead from the planner's arena, copied straight
       // into the ring (cp.async, one group per jump) ...
@@ -489,22 +527,26 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
         }
       cp_async_wait<kWeightLead>();  // jump k's copy (issued lead jumps ago) has landed
     }
-    if (LL && acc_me) group_accumulate(src, plo, phi, wprev, f);
-    T part = (T)0;
+    if (LL && acc_me) group_accumulate(src, plo, phi, wprev);
     if (KIND == MJP_BD1D) {
       for (int m = wwarp ? g.m1 : g.m0 + tx; m < g.m1; m += TX) {
         const int li = m - g.m0 + 1;
         const T cur = src[li];
-        if (!LL) expv_accumulate(rn ? f_mul(cur, f) : cur, m, k - 1, plo, phi, wprev);
+        if (!LL) expv_accumulate(cur, m, k - 1, plo, phi, wprev);
         if (jump) {
           const T fm = (T)m;
           const T e = f_add(f_mul(co.b, fm), m + 1 < M ? co.a : (T)0);
-          T y = f_mul(f_sub(one, e), cur);
-          y = f_fma(co.a, src[li - 1], y);
-          y = f_fma(f_mul(co.b, f_add(fm, one)), src[li + 1], y);
-          if (rn) {
-            y = f_mul(y, f);
-            part += y;
+          const T cr = f_mul(co.b, f_add(fm, one));
+          T y;
+          if constexpr (kComp) {
+            float l = lo_t[li];
+            y = comp_jump(cur, l, co.a, src[li - 1], cr, src[li + 1], -e);
+            if (dfix) l = __fmaf_rn(cb_t[li], y, l);
+            lo_t[li] = l;
+          } else {
+            y = f_mul(f_sub(one, e), cur);
+            y = f_fma(co.a, src[li - 1], y);
+            y = f_fma(cr, src[li + 1], y);
           }
           dst[li] = y;
           if (m == g.m0 && push_dn[par ^ 1]) *push_dn[par ^ 1] = y;
@@ -521,23 +563,33 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
       T2 prev = sp[-W2];
       T2 cur = sp[0];
       T2 fpp = v_make((T)pp, (T)(pp + 1));
-      const T2 f2 = v_make(f, f);
       T2 y = v_make((T)0, (T)0);
+      float2* lp = kComp ? reinterpret_cast<float2*>(lo_t) + (ja + 1) * g.Wp + mc + 1 : nullptr;
+      const float2* cbp = kComp ? reinterpret_cast<const float2*>(cb_t) + (ja + 1) * g.Wp + mc + 1 : nullptr;
       // One pair-row: rows pp and pp+1 of column mc.  `top` marks the pair
       // that holds row P-1 (no protein birth out of it; row P absent).
       auto pair_row = [&](bool top) {
         const T2 next = sp[W2];
         const T2 left = sp[-1], right = sp[1];
         if (!LL) {
-          expv_accumulate(rn ? f_mul(cur.x, f) : cur.x, gidx(pp, mc), k - 1, plo, phi, wprev);
-          if (pp + 1 < g.p1)
-            expv_accumulate(rn ? f_mul(cur.y, f) : cur.y, gidx(pp + 1, mc), k - 1, plo, phi, wprev);
+          expv_accumulate(cur.x, gidx(pp, mc), k - 1, plo, phi, wprev);
+          if (pp + 1 < g.p1) expv_accumulate(cur.y, gidx(pp + 1, mc), k - 1, plo, phi, wprev);
         }
         if (jump) {
           if (KIND == MJP_TWOSTATE) {
-            const T2 t1 = v_fma(c_l, left, v_mul(c_dg, cur));
-            const T2 t2 = v_fma(c_sw, v_make(cur.y, cur.x), v_mul(c_r, right));
-            y = v_add(t1, t2);
+            if constexpr (kComp) {
+              float2 l = *lp;
+              float2 t = v_fma(c_l, left, l);
+              t = v_fma(c_r, right, t);
+              t = v_fma(c_sw, v_make(cur.y, cur.x), t);
+              t = v_fma(c_dg, cur, t);  // c_dg holds -e (compensated chain)
+              y = comp_finish(cur, t, l);
+              *lp = l;
+            } else {
+              const T2 t1 = v_fma(c_l, left, v_mul(c_dg, cur));
+              const T2 t2 = v_fma(c_sw, v_make(cur.y, cur.x), v_mul(c_r, right));
+              y = v_add(t1, t2);
+            }
           } else if (KIND == MJP_AUTOREG) {
             // Pair = (active, inactive) at protein count q: transcription from
             // m-1 (active only), R decay from m+1, translation from q-1, P
@@ -550,31 +602,67 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
             const T tr = qtop ? (T)0 : a_tl;                       // beta_P m, if q+1 exists
             const T e0 = f_add(f_add(f_add(decay, a_tx), tr), f_mul(co.f, fq));
             const T e1 = f_add(f_add(decay, tr), qtop ? (T)0 : co.e);
-            y.x = f_mul(f_sub(one, e0), cur.x);
-            y.y = f_mul(f_sub(one, e1), cur.y);
-            y.x = f_fma(co.a, left.x, y.x);
-            y = v_fma(c_r, right, y);
-            y = v_fma(v_make(a_tl, a_tl), prev, y);
             const T gq = f_mul(co.d, (T)(q + 1));
-            y = v_fma(v_make(gq, gq), next, y);
-            y.x = f_fma(co.e, prev.y, y.x);
-            y.y = f_fma(f_mul(co.f, (T)(q + 1)), next.x, y.y);
-          } else {
-            T2 dg = v_fma(c_ngp, fpp, c_dg);        // 1 - e_{m,p}
-            const T2 cup = v_fma(c_gp, fpp, c_gp);  // gamma_p (p+1) from p+1
-            if (top) {
-              if (pp == P - 1) dg.x = f_add(dg.x, cd);
-              else dg.y = f_add(dg.y, cd);
+            if constexpr (kComp) {
+              float2 l = *lp;
+              float2 t = l;
+              t.x = f_fma(co.a, left.x, t.x);
+              t = v_fma(c_r, right, t);
+              t = v_fma(v_make(a_tl, a_tl), prev, t);
+              t = v_fma(v_make(gq, gq), next, t);
+              t.x = f_fma(co.e, prev.y, t.x);
+              t.y = f_fma(f_mul(co.f, (T)(q + 1)), next.x, t.y);
+              t = v_fma(v_make(-e0, -e1), cur, t);
+              y = comp_finish(cur, t, l);
+              *lp = l;
+            } else {
+              y.x = f_mul(f_sub(one, e0), cur.x);
+              y.y = f_mul(f_sub(one, e1), cur.y);
+              y.x = f_fma(co.a, left.x, y.x);
+              y = v_fma(c_r, right, y);
+              y = v_fma(v_make(a_tl, a_tl), prev, y);
+              y = v_fma(v_make(gq, gq), next, y);
+              y.x = f_fma(co.e, prev.y, y.x);
+              y.y = f_fma(f_mul(co.f, (T)(q + 1)), next.x, y.y);
             }
-            y = v_fma(c_r, right, v_fma(c_l, left, v_mul(dg, cur)));
-            y.x = f_fma(cup.x, cur.y, f_fma(cd, prev.y, y.x));  // rows below / above
-            y.y = f_fma(cup.y, next.x, f_fma(cd, cur.x, y.y));
-            if (top && pp + 1 >= P) y.y = (T)0;     // row P does not exist
+          } else {
+            T2 dg = v_fma(c_ngp, fpp, c_dg);        // 1 - e_{m,p} (FP32: -e_{m,p})
+            const T2 cup = v_fma(c_gp, fpp, c_gp);  // gamma_p (p+1) from p+1
+            if constexpr (kComp) {
+              // Inflows from the left, right, below and above, the exit, and at
+              // row P-1 the protein birth k_p m that does not leave it.
+              float2 l = *lp;
+              float2 t = v_fma(c_l, left, l);
+              t = v_fma(c_r, right, t);
+              t.x = f_fma(cd, prev.y, t.x);
+              t.y = f_fma(cd, cur.x, t.y);
+              t.x = f_fma(cup.x, cur.y, t.x);
+              t.y = f_fma(cup.y, next.x, t.y);
+              t = v_fma(dg, cur, t);
+              if (top) {
+                if (pp == P - 1) t.x = f_fma(cd, cur.x, t.x);
+                else t.y = f_fma(cd, cur.y, t.y);
+              }
+              y = comp_finish(cur, t, l);
+              if (top && pp + 1 >= P) {  // row P does not exist
+                y.y = 0.0f;
+                l.y = 0.0f;
+              }
+              *lp = l;
+            } else {
+              if (top) {
+                if (pp == P - 1) dg.x = f_add(dg.x, cd);
+                else dg.y = f_add(dg.y, cd);
+              }
+              y = v_fma(c_r, right, v_fma(c_l, left, v_mul(dg, cur)));
+              y.x = f_fma(cup.x, cur.y, f_fma(cd, prev.y, y.x));  // rows below / above
+              y.y = f_fma(cup.y, next.x, f_fma(cd, cur.x, y.y));
+              if (top && pp + 1 >= P) y.y = (T)0;     // row P does not exist
+            }
             fpp = v_add(fpp, two2);
           }
-          if (rn) {
-            y = v_mul(y, f2);
-            part += y.x + y.y;
+          if constexpr (kComp) {
+            if (dfix) *lp = v_fma(*cbp, y, *lp);
           }
           *dp = y;
         }
@@ -582,6 +670,10 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
         cur = next;
         sp += W2;
         dp += W2;
+        if constexpr (kComp) {
+          lp += W2;
+          cbp += W2;
+        }
         pp += 2;
       };
       const bool has_top = (KIND == MJP_MRNA_PROT2D) && jb == g.Hp && g.p1 == P;
@@ -594,14 +686,6 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
         if (push_up[par ^ 1] && jb == g.Hp) reinterpret_cast<T2*>(push_up[par ^ 1])[mc + 1] = y;
       }
     }
-    const bool do_renorm = rn && jump && (k % p.renorm) == 0;
-    if (do_renorm) {
-      double v = (double)part;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-      if (lane == 0) red[(int)(k & 1) * 33 + warp] = v;
-    }
-    renorm_prev = do_renorm;
     if (C > 1) {
       cluster_arrive();
       cluster_wait();

@@ -13,10 +13,12 @@
 // 16 B to ~1.5 B per state and the FP32 pipe becomes the limit.
 //
 // Arithmetic per state is the same operation sequence, in the same order, as
-// the shared-memory kernel in stencil.cu (gather form of rho B with the
-// coefficients built from theta), so both kernels produce bit-identical
-// chains; observations with one member per group give bit-identical
-// log-likelihoods.  A cluster of C CTAs splits the rows; block edges that
+// the shared-memory kernel in stencil.cu (the compensated jump of
+// chain_common.cuh: delta form of rho B with the coefficients built from theta,
+// the rounding residual of every state carried in registers, and the exit
+// defects added back every p.renorm jumps), so both kernels produce
+// bit-identical chains; observations with one member per group give
+// bit-identical log-likelihoods.  A cluster of C CTAs splits the rows; block edges that
 // cross a CTA boundary are written into the neighbour CTA's halo slots
 // through distributed shared memory.
 //
@@ -38,10 +40,9 @@ namespace mjp {
 namespace {
 
 constexpr int kQC = 4;            // columns per thread block of states
-// Threads per CTA at most, T = 512 (one CTA per SM) or 256 (two CTAs of
-// different instances per SM, so that one computes while the other waits at
-// its barrier); <= 128 registers per thread either way.
-constexpr int kMaxNQ = 512;       // column quads (M <= 2048)
+// Threads per CTA at most: T = 384, one CTA per SM, so that a thread has 170
+// registers for its block of states, their residuals and the coefficients.
+constexpr int kT384 = 384;
 // Fixed strides of the edge arrays (per parity):
 //  - columns [2 sides][QR][T + 1] float2: the left (side 0) and right (side 1)
 //    column of block t, row pair r; entry T (kZero) is a zero slot;
@@ -142,8 +143,7 @@ __device__ int block_exclusive_scan(int v, int* wsum) {
 }
 
 template <int kQR, int kT>
-__global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainParams p, const int NQ,
-                                                                   const int RS) {
+__global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p, const int NQ, const int RS) {
   using G = EdgeGeo<kQR, kT>;
   constexpr int kZero = G::kZero;
   constexpr int kRows = 2 * kQR;  // rows of a thread's block
@@ -246,9 +246,9 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   else __syncthreads();
 
   // Column coefficients (rates into column m, scaled by 1/Omega): gamma_m
-  // (m+1) from m+1, k_p m from p-1, and 1 - e without the gamma_p p part, as
-  // pairs of the columns (c0, c2) and (c1, c3) that share a register pair.
-  const float one = 1.0f;
+  // (m+1) from m+1, k_p m from p-1, and the negated exit -e0 without the
+  // gamma_p p part, as pairs of the columns (c0, c2) and (c1, c3) that share a
+  // register pair.
   float crc[kQC], cdc[kQC], d0c[kQC];
   int colmask = 0;  // bit c: column m0 + c lies in the box
 #pragma unroll
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     const float fm = (float)m;
     crc[c] = f_mul(co.b, (float)(m + 1));
     cdc[c] = f_mul(co.c, fm);
-    d0c[c] = f_sub(one, f_add(f_add(f_mul(co.b, fm), m + 1 < M ? co.a : 0.0f), cdc[c]));
+    d0c[c] = -mrna_col(co, m, M).e0;
   }
   const float2 d0A = v_make(d0c[0], d0c[2]), d0B = v_make(d0c[1], d0c[3]);
   const float2 crA = v_make(crc[0], crc[2]), crB = v_make(crc[1], crc[3]);
@@ -298,6 +298,11 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     S[r][1] = v_make(v[1], v[3]);
   }
   S[NR][0] = S[NR][1] = v_make(0.0f, 0.0f);
+  // Residual of every state of the block (row r, pairs as in S), by row: it
+  // belongs to the state, not to a register slot, so it does not rotate.
+  float2 res[NR][2];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) res[r][0] = res[r][1] = v_make(0.0f, 0.0f);
   // The row arrays of the neighbouring CTAs: our first row is the row above
   // CTA rank-1 (its array 0), our last row the row below CTA rank+1 (array 1).
   unsigned char* nb_dn = nullptr;
@@ -470,36 +475,67 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
       }
       const float lin = (r & 1) ? lp.y : lp.x;
       const float rin = (r & 1) ? rp.y : rp.x;
-      float2 dA = v_fma(c_ngp, fp, d0A), dB = v_fma(c_ngp, fp, d0B);  // 1 - e_{m,p}
+      const float2 dA = v_fma(c_ngp, fp, d0A), dB = v_fma(c_ngp, fp, d0B);  // -e_{m,p}
+      const float2 cup = v_fma(c_gp, fp, c_gp);  // gamma_p (p+1) from p+1
+      // t = residual + inflows from the left, right, below and above + exit,
+      // and in row P-1 the protein birth k_p m that does not leave it.
+      float2 tA = res[r][0];
+      tA.x = f_fma(c_l, lin, tA.x);   // from m - 1: the left block's c3
+      tA.y = f_fma(c_l, B.x, tA.y);   // c1
+      tA = v_fma(crA, B, tA);         // from m + 1: (c1, c3)
+      tA = v_fma(cdA, bA, tA);
+      tA = v_fma(cup, aA, tA);
+      tA = v_fma(dA, A, tA);
+      float2 tB = v_fma(c_l2, A, res[r][1]);
+      tB.x = f_fma(crB.x, A.y, tB.x); // from m + 1: c2
+      tB.y = f_fma(crB.y, rin, tB.y); // the right block's c0
+      tB = v_fma(cdB, bB, tB);
+      tB = v_fma(cup, aB, tB);
+      tB = v_fma(dB, B, tB);
       if (EDGE && r == rtk) {
-        dA = v_add(dA, cdA);
-        dB = v_add(dB, cdB);
+        tA = v_fma(cdA, A, tA);
+        tB = v_fma(cdB, B, tB);
       }
       if (!EDGE && r == NR - 1) {
-        dA = v_add(dA, topA);
-        dB = v_add(dB, topB);
+        tA = v_fma(topA, A, tA);
+        tB = v_fma(topB, B, tB);
       }
-      const float2 cup = v_fma(c_gp, fp, c_gp);  // gamma_p (p+1) from p+1
-      float2 yA = v_mul(dA, A);
-      yA.x = f_fma(c_l, lin, yA.x);   // from m - 1: the left block's c3
-      yA.y = f_fma(c_l, B.x, yA.y);   // c1
-      yA = v_fma(crA, B, yA);         // from m + 1: (c1, c3)
-      yA = v_fma(cup, aA, v_fma(cdA, bA, yA));
-      float2 yB = v_fma(c_l2, A, v_mul(dB, B));
-      yB.x = f_fma(crB.x, A.y, yB.x); // from m + 1: c2
-      yB.y = f_fma(crB.y, rin, yB.y); // the right block's c0
-      yB = v_fma(cup, aB, v_fma(cdB, bB, yB));
+      float2 yA = comp_finish(A, tA, res[r][0]);
+      float2 yB = comp_finish(B, tB, res[r][1]);
       if (EDGE) {
-        if (rtk >= 0 && r > rtk) yA = yB = v_make(0.0f, 0.0f);  // rows beyond the box
-        if (padcols) {                                          // padding columns of the last quad
-          if (!(colmask & 2)) yB.x = 0.0f;
-          if (!(colmask & 4)) yA.y = 0.0f;
-          if (!(colmask & 8)) yB.y = 0.0f;
+        if (rtk >= 0 && r > rtk) {  // rows beyond the box
+          yA = yB = v_make(0.0f, 0.0f);
+          res[r][0] = res[r][1] = v_make(0.0f, 0.0f);
+        }
+        if (padcols) {              // padding columns of the last quad
+          if (!(colmask & 2)) yB.x = res[r][1].x = 0.0f;
+          if (!(colmask & 4)) yA.y = res[r][0].y = 0.0f;
+          if (!(colmask & 8)) yB.y = res[r][1].y = 0.0f;
         }
       }
       S[sn][0] = yA;
       S[sn][1] = yB;
       fp = v_add(fp, fstep);
+    }
+  };
+
+  // Exit-defect correction of rho_k (rotation ROT): every state adds
+  // p.renorm x its defect x its value to its residual (states outside the box
+  // hold zero and stay zero).
+  const float period = (float)p.renorm;
+  auto defect_fix = [&](auto ROTC) {
+    constexpr int ROT = decltype(ROTC)::value;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int pr = pb + r;
+      const int sl = rslot<NR>(r, ROT);
+      const float2 ya = S[sl][0], yb = S[sl][1];
+      const float b0 = __fmul_rn(period, mrna_defect(mrna_col(co, m0 + 0, M), co.d, pr));
+      const float b1 = __fmul_rn(period, mrna_defect(mrna_col(co, m0 + 1, M), co.d, pr));
+      const float b2 = __fmul_rn(period, mrna_defect(mrna_col(co, m0 + 2, M), co.d, pr));
+      const float b3 = __fmul_rn(period, mrna_defect(mrna_col(co, m0 + 3, M), co.d, pr));
+      res[r][0] = v_fma(v_make(b0, b2), ya, res[r][0]);
+      res[r][1] = v_fma(v_make(b1, b3), yb, res[r][1]);
     }
   };
 
@@ -524,8 +560,10 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     if (nb_dn || nb_up) fence_cluster();
     else fence_cta();
     cluster_arrive_relaxed();
-    // Work that touches no edge overlaps the barrier: observations of rho_k,
-    // the next chunk of weights, the recurrence one jump ahead.
+    // Work that touches no edge overlaps the barrier: the exit-defect
+    // correction of rho_k, observations of rho_k, the next chunk of weights,
+    // the recurrence one jump ahead.
+    if (owner && p.renorm > 0 && k % p.renorm == 0) defect_fix(std::integral_constant<int, ROT>{});
     advance(k, lo, hi);
     accumulate(k, lo, hi, std::integral_constant<int, ROT>{});
     if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
@@ -587,13 +625,12 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
 // box does not fit this kernel (then the shared-memory kernel runs).
 bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluster, int threads, RegPlan* out) {
   if (M < 1 || P < 1 || ntimes < 1) return false;
+  if (threads != 0) return false;  // the launch shape is this kernel's own
   const int NQ = (int)((M + kQC - 1) / kQC);
-  if (NQ > kMaxNQ) return false;
+  constexpr int T = kT384;
+  if (NQ > T) return false;
   // Fewest CTAs per instance first; for each, 8 rows per thread before 10.
-  // threads = 256 asks for two CTAs per SM (then the edge arrays are half as
-  // large and a CTA must fit half the shared memory).
-  const int T = threads == 256 ? 256 : 512;
-  const size_t smem_cap = T == 256 ? 113 * 1024 : 227 * 1024;
+  const size_t smem_cap = 227 * 1024;
   for (int C = 1; C <= max_cluster; ++C)
     for (int QR = 4; QR <= 5; ++QR) {
       const int rows_blk = 2 * QR;
@@ -602,9 +639,7 @@ bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluste
       if ((int64_t)(C - 1) * RS >= P) continue;  // the last CTA would be empty
       const int Tc = NQ * (RS / rows_blk);
       if (Tc > T) continue;
-      size_t edge;
-      if (T == 256) edge = 2 * (QR == 5 ? EdgeGeo<5, 256>::par_bytes : EdgeGeo<4, 256>::par_bytes);
-      else edge = 2 * (QR == 5 ? EdgeGeo<5, 512>::par_bytes : EdgeGeo<4, 512>::par_bytes);
+      const size_t edge = 2 * (QR == 5 ? EdgeGeo<5, T>::par_bytes : EdgeGeo<4, T>::par_bytes);
       const RegLayout L = reg_layout(edge, ntimes, nmem);
       if (L.total + 1024 > smem_cap) continue;  // leave room for static shared memory
       out->cluster = C;
@@ -652,8 +687,7 @@ cudaError_t launch_reg(const ChainParams& p, const RegPlan& rp, cudaStream_t s) 
 
 cudaError_t launch_chain_reg2d(const ChainParams& p, const RegPlan& rp, cudaStream_t s) {
   if (p.B <= 0) return cudaSuccess;
-  if (rp.tmax == 256) return rp.qr == 5 ? launch_reg<5, 256>(p, rp, s) : launch_reg<4, 256>(p, rp, s);
-  return rp.qr == 5 ? launch_reg<5, 512>(p, rp, s) : launch_reg<4, 512>(p, rp, s);
+  return rp.qr == 5 ? launch_reg<5, kT384>(p, rp, s) : launch_reg<4, kT384>(p, rp, s);
 }
 
 }  // namespace mjp

@@ -25,6 +25,10 @@
 // sequence in the same order, and the weighted accumulation is the same
 // Kahan (FP32) or plain (FP64) sum in jump order, with the same weights, so
 // both kernels give bit-identical outputs for every cluster shape and halo.
+// FP32 chains run the compensated jump of chain_common.cuh (each state carries
+// its rounding residual, and every p.renorm jumps the exact defect of its
+// exit coefficient is added back); the residuals travel with the values in
+// every halo exchange, so halo copies evolve exactly like their owners.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -44,18 +48,22 @@ constexpr int kChunk1 = 32;           // jumps of weights staged at a time
 constexpr int kStage1 = 2 * kChunk1;  // ring slots per time
 
 struct Reg1dLayout {
-  size_t wh, recv, tx, tPL, ttail, twb, pw, tL, tK, trec, torig, ring, acc_s, acc_c, total;
+  size_t wh, whl, recv, recvl, tx, tPL, ttail, twb, pw, tL, tK, trec, torig, ring, acc_s, acc_c, total;
 };
 
 // Shared memory of one CTA: the warps' halo runs [round parity][left, right]
 // [warp][pair], the cluster halo receive buffers [exchange parity][left,
-// right][h], the windows, the weight ring [time][kStage1], the accumulators
-// [time][pair][thread] (pairs of T; FP32 adds the Kahan compensations).
+// right][h] (FP32: each with a twin for the chain residuals), the windows, the
+// weight ring [time][kStage1], the accumulators [time][pair][thread] (pairs of
+// T; FP32 adds the Kahan compensations).
 __host__ __device__ inline Reg1dLayout reg1d_layout(size_t elt, int threads, int qp, int halo, int nt) {
   Reg1dLayout s;
   size_t o = 0;
+  const bool comp = elt == 4;  // FP32: compensated chain, residuals beside the values
   s.wh = o; o += align_up(elt * 2 * 4 * (size_t)(threads / 32) * qp, 16);
+  s.whl = o; if (comp) o += align_up(4 * 2 * 4 * (size_t)(threads / 32) * qp, 16);
   s.recv = o; o += align_up(elt * 4 * (size_t)(halo > 0 ? halo : 1), 16);
+  s.recvl = o; if (comp) o += align_up(4 * 4 * (size_t)(halo > 0 ? halo : 1), 16);
   s.tx = o; o += 8 * (size_t)nt;
   s.tPL = o; o += 8 * (size_t)nt;
   s.ttail = o; o += 8 * (size_t)nt;
@@ -133,8 +141,11 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
   const int64_t out_base = p.job_off ? p.job_off[job] : (int64_t)job * p.out_stride;
 
   const Reg1dLayout Ly = reg1d_layout(sizeof(T), nthr, QP, h, nt);
+  constexpr bool kComp = sizeof(T) == 4;                  // compensated FP32 chain
   T2* const wh = reinterpret_cast<T2*>(smem + Ly.wh);    // [2][2][nthr / 32][QP]
+  float2* const whl = reinterpret_cast<float2*>(smem + Ly.whl);  // residuals, same shape (FP32)
   T* const recv = reinterpret_cast<T*>(smem + Ly.recv);  // [2][2][h]
+  float* const recvl = reinterpret_cast<float*>(smem + Ly.recvl);  // residuals, same shape (FP32)
   double* t_x = reinterpret_cast<double*>(smem + Ly.tx);
   double* t_PL = reinterpret_cast<double*>(smem + Ly.tPL);
   double* t_tail = reinterpret_cast<double*>(smem + Ly.ttail);
@@ -173,36 +184,48 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
   if (Kmax64 >= (1LL << 30) && tid == 0 && rank == 0) set_status(p.status, kStatusKcap);
 
   // Coefficients of every held state n (rates into n, scaled by 1/Omega): the
-  // diagonal 1 - e_n and the death rate gamma (n+1) from n+1, both zero outside
-  // the segment or the box, and the latter zero at n = N - 1 too (what is held
-  // beyond the box is not kept at zero, so it must not be read).  Values
-  // entering a lane's run from outside its warp's window are stale by design
-  // (halo) except at the segment's left end, where the inflow coefficient of
-  // the first state is zero instead (the state left of it is void).
+  // diagonal 1 - e_n (FP64) or the negated exit -e_n (FP32, compensated jump)
+  // and the death rate gamma (n+1) from n+1, both zero outside the segment or
+  // the box, and the latter zero at n = N - 1 too (what is held beyond the box
+  // is not kept at zero, so it must not be read).  Values entering a lane's run
+  // from outside its warp's window are stale by design (halo) except at the
+  // segment's left end, where the inflow coefficient of the first state is zero
+  // instead (the state left of it is void).  FP32 also keeps, per state, the
+  // residual (zero at the start) and p.renorm times the defect of its exit,
+  // e_n - (beta + gamma n) with the outflow coefficients as the neighbours
+  // apply them (bd_defect).
   const T one = (T)1;
   const T* rho0 = reinterpret_cast<const T*>(p.rho0);
   const int64_t s0 = p.job_s0 ? p.job_s0[job] : -1;
   // r[QP] is a spare pair: the pairs rotate through all QP + 1 slots (below);
-  // at a round's end pair j is back in r[j].
+  // at a round's end pair j is back in r[j].  res[j] and cb[j] belong to pair
+  // j wherever its value sits.
   T2 r[QP + 1], dg[QP], up[QP];
+  float2 res[QP], cb[QP];
   r[QP] = v_make((T)0, (T)0);
 #pragma unroll
   for (int j = 0; j < QP; ++j) {
     T dv[2], uv[2], rv[2];
+    float bv[2];
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
       const int x = xw + y0 + hh * QP + j;
       const int n = xb + x;
       const bool in = wact && x >= 0 && x < ext && n >= 0 && n < N;
       const T fm = (T)n;
-      const T e = f_add(f_mul(co.b, fm), n + 1 < N ? co.a : (T)0);
-      dv[hh] = in ? f_sub(one, e) : (T)0;
+      const T bn = f_mul(co.b, fm);
+      const T ain = n + 1 < N ? co.a : (T)0;
+      const T e = f_add(bn, ain);
+      dv[hh] = in ? (kComp ? -e : f_sub(one, e)) : (T)0;
       uv[hh] = (in && n + 1 < N) ? f_mul(co.b, f_add(fm, one)) : (T)0;
       rv[hh] = !in ? (T)0 : (s0 >= 0 ? (T)(n == s0 ? 1 : 0) : rho0[n]);
+      bv[hh] = (kComp && in && p.renorm > 0) ? (float)p.renorm * bd_defect(co, n, N) : 0.0f;
     }
     dg[j] = v_make(dv[0], dv[1]);
     up[j] = v_make(uv[0], uv[1]);
     r[j] = v_make(rv[0], rv[1]);
+    res[j] = make_float2(0.0f, 0.0f);
+    cb[j] = make_float2(bv[0], bv[1]);
   }
   const T2 a2 = v_make(co.a, co.a);
   const T2 a2first = v_make(warp == 0 && lane == 0 ? (T)0 : co.a, co.a);  // pair 0's inflow from the left
@@ -213,9 +236,17 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
   // them; recv[ep][side][q], side 0 = left halo (from rank - 1), 1 = right.
   T* rmtL = nullptr;
   T* rmtR = nullptr;
+  float* rmtLl = nullptr;
+  float* rmtRl = nullptr;
   if (C > 1) {
-    if (rank > 0) rmtL = cluster.map_shared_rank(recv, rank - 1);
-    if (rank + 1 < C) rmtR = cluster.map_shared_rank(recv, rank + 1);
+    if (rank > 0) {
+      rmtL = cluster.map_shared_rank(recv, rank - 1);
+      if (kComp) rmtLl = cluster.map_shared_rank(recvl, rank - 1);
+    }
+    if (rank + 1 < C) {
+      rmtR = cluster.map_shared_rank(recv, rank + 1);
+      if (kComp) rmtRl = cluster.map_shared_rank(recvl, rank + 1);
+    }
   }
   const int xo0 = xw + max(sw, y0), xo1 = xw + min(sw + Wo, y0 + R);  // segment range this lane owns
   const bool cl_send = C > 1 && wact && xo0 < xo1 &&
@@ -231,9 +262,16 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
         for (int hh = 0; hh < 2; ++hh) {
           const int y = y0 + hh * QP + j, x = xw + y;
           const T v = hh ? r[j].y : r[j].x;
+          const float vl = hh ? res[j].y : res[j].x;
           if (!owned_y(y)) continue;
-          if (rmtL && x >= h && x < 2 * h) rmtL[(ep * 2 + 1) * h + (x - h)] = v;
-          if (rmtR && x >= own && x < own + h) rmtR[(ep * 2 + 0) * h + (x - own)] = v;
+          if (rmtL && x >= h && x < 2 * h) {
+            rmtL[(ep * 2 + 1) * h + (x - h)] = v;
+            if (kComp) rmtLl[(ep * 2 + 1) * h + (x - h)] = vl;
+          }
+          if (rmtR && x >= own && x < own + h) {
+            rmtR[(ep * 2 + 0) * h + (x - own)] = v;
+            if (kComp) rmtRl[(ep * 2 + 0) * h + (x - own)] = vl;
+          }
         }
       fence_cluster();
     }
@@ -243,16 +281,30 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
 #pragma unroll
       for (int j = 0; j < QP; ++j) {
         T v0 = r[j].x, v1 = r[j].y;
+        float l0 = res[j].x, l1 = res[j].y;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           const int y = y0 + hh * QP + j, x = xw + y;
           T v = hh ? v1 : v0;
-          if (owned_y(y) && rank > 0 && x < h) v = recv[(ep * 2 + 0) * h + x];
-          if (owned_y(y) && rank + 1 < C && x >= own + h && x < own + 2 * h) v = recv[(ep * 2 + 1) * h + (x - own - h)];
-          if (hh) v1 = v;
-          else v0 = v;
+          float l = hh ? l1 : l0;
+          if (owned_y(y) && rank > 0 && x < h) {
+            v = recv[(ep * 2 + 0) * h + x];
+            if (kComp) l = recvl[(ep * 2 + 0) * h + x];
+          }
+          if (owned_y(y) && rank + 1 < C && x >= own + h && x < own + 2 * h) {
+            v = recv[(ep * 2 + 1) * h + (x - own - h)];
+            if (kComp) l = recvl[(ep * 2 + 1) * h + (x - own - h)];
+          }
+          if (hh) {
+            v1 = v;
+            l1 = l;
+          } else {
+            v0 = v;
+            l0 = l;
+          }
         }
         r[j] = v_make(v0, v1);
+        res[j] = make_float2(l0, l1);
       }
     }
   };
@@ -263,15 +315,21 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
   // left halo of warp w.
   auto warp_exchange = [&](int rp) {
     if (wact && ((lane == 1 && warp > 0) || (lane == 30 && warp + 1 < nwu))) {
-      T2* dst = wh + ((rp * 2 + (lane == 1 ? 1 : 0)) * NW + (lane == 1 ? warp - 1 : warp + 1)) * QP;
+      const int off = ((rp * 2 + (lane == 1 ? 1 : 0)) * NW + (lane == 1 ? warp - 1 : warp + 1)) * QP;
 #pragma unroll
-      for (int j = 0; j < QP; ++j) dst[j] = r[j];
+      for (int j = 0; j < QP; ++j) {
+        wh[off + j] = r[j];
+        if (kComp) whl[off + j] = res[j];
+      }
     }
     __syncthreads();
     if (wact && ((lane == 0 && warp > 0) || (lane == 31 && warp + 1 < nwu))) {
-      const T2* src = wh + ((rp * 2 + (lane == 0 ? 0 : 1)) * NW + warp) * QP;
+      const int off = ((rp * 2 + (lane == 0 ? 0 : 1)) * NW + warp) * QP;
 #pragma unroll
-      for (int j = 0; j < QP; ++j) r[j] = src[j];
+      for (int j = 0; j < QP; ++j) {
+        r[j] = wh[off + j];
+        if (kComp) res[j] = whl[off + j];
+      }
     }
   };
 
@@ -396,8 +454,24 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
       const T2 cur = r[(j + O) % P1];
       const T2 left = j == 0 ? left0 : r[(j - 1 + O) % P1];
       const T2 right = (j + 1 < QP) ? r[(j + 1 + O) % P1] : v_make(first_y, rin);
-      r[j == 0 ? (O + QP) % P1 : (j - 1 + O) % P1] =
-          v_fma(up[j], right, v_fma(j == 0 ? a2first : a2, left, v_mul(dg[j], cur)));
+      const T2 al = j == 0 ? a2first : a2;
+      T2 y;
+      if constexpr (kComp) {
+        y = comp_jump(cur, res[j], al, left, up[j], right, dg[j]);
+      } else {
+        y = v_fma(up[j], right, v_fma(al, left, v_mul(dg[j], cur)));
+      }
+      r[j == 0 ? (O + QP) % P1 : (j - 1 + O) % P1] = y;
+    }
+  };
+  // Defect correction of the compensated chain after jump k_e (pairs at home);
+  // the period is a multiple of the round length P1.
+  auto defect = [&](int k_e) {
+    if constexpr (kComp) {
+      if (p.renorm > 0 && k_e % p.renorm == 0) {
+#pragma unroll
+        for (int j = 0; j < QP; ++j) res[j] = __ffma2_rn(cb[j], r[j], res[j]);
+      }
     }
   };
   auto jump_plain = [&](auto OC) {
@@ -443,6 +517,7 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
   for (int g = 0; g < ngroups; ++g) {
     if (wact) RotSeq<P1, 0, P1>::run(jump_plain);
     else k += P1;
+    defect(k - 1);
     round_end(k - 1);
   }
 
@@ -462,6 +537,7 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
     RotSeq<P1, 0, P1>::run(jump_acc);
     const int k_e = k - 1;
     if (k_e >= Kmax) break;
+    defect(k_e);
     if ((k_e + P1) % kChunk1 == 0) cp_async_wait<0>();
     rec_round(k_e + 1, min(Kmax, k_e + P1));
     round_end(k_e);
@@ -504,11 +580,12 @@ cudaError_t launch_reg1d_typed(const ChainParams& p, const Reg1dPlan& rp, cudaSt
 }
 
 // State pairs per lane (QP, QP + 1 = 8 jumps per round) and the largest CTA
-// of each precision: the registers hold 3 pairs (state, diagonal, death
-// coefficient) per pair of states, 42 registers at FP32 and 84 at FP64; 512
-// threads leave 128 registers per thread (FP32), 256 threads 255 (FP64,
-// whose slow FP64 pipe needs few warps but many independent operations).
-constexpr int kQP32 = 7, kMaxT32 = 512;
+// of each precision: the registers hold per pair of states the values, the
+// exit and death coefficients and, in FP32, the residuals and defects (70
+// registers at FP32, 84 at FP64); 384 threads leave 170 registers per thread
+// (FP32), 256 threads 255 (FP64, whose slow FP64 pipe needs few warps but many
+// independent operations).
+constexpr int kQP32 = 7, kMaxT32 = 384;
 constexpr int kQP64 = 7, kMaxT64 = 256;
 // One pair per thread spreads a small chain over more warps: the latency of a
 // single solve drops (GB300's FP64 pipe issues a warp's FP64 instruction over

@@ -78,7 +78,8 @@ def test_full_uneven_batch(prec):
     b.check()
     res = b.split(out.double().cpu().numpy())
     mass = np.array([r.sum() for r in res])
-    assert np.abs(mass - 1.0).max() <= (1e-11 if prec == 2 else 2e-3)
+    # FP32: the compensated chain conserves mass to ~u sqrt(K) (K up to 3.6e5).
+    assert np.abs(mass - 1.0).max() <= (1e-11 if prec == 2 else 1e-5)
     assert min(r.min() for r in res) >= 0.0
     # Sampled instances against the oracle: the smallest, the largest state
     # space and several of moderate cost.

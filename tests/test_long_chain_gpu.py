@@ -1,0 +1,146 @@
+"""FP32 chains at the full chain lengths the configurations run, against the
+FP64 oracle element by element.
+
+* mRNA/protein 200 x 200 box, 20 log-spaced times in [0.1, 50]: the shared
+  chain runs K = 69,089 jumps (Algorithm 2's K at t = 50); expv_series at every
+  time within 1e-6 of the oracle, and the register-resident log-likelihood of
+  jittered theta (K from ~56,000 to ~82,000) within the derived tolerance.
+* The heaviest instances of the uneven birth-death batch (K from 2.6e5 to
+  3.6e5 jumps, N up to 19,811 states) through the batch path, within 1e-6.
+* The exit-defect correction (MJP_OPT_RENORM_PERIOD, restoring the unit
+  column sums of B of Eq. B_def) switched off: the error is reported and is
+  larger than with the correction.
+
+The oracle runs take ~40 s each on one core; they run on host threads
+(ctypes releases the GIL) beside each other.
+"""
+import concurrent.futures as cf
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-6  # max |GPU - oracle| on transient distributions, FP32 chain
+# Log-likelihood, per observation (x total count).  The compensated chain keeps
+# the relative error of every state ~ u sqrt(K) x (the share of t that is
+# rounded, ~0.1), i.e. ~5e-7 at K ~ 8e4 (u = 6e-8); the Kahan-compensated
+# weighted sum adds ~u.  An observed probability with relative error r gives a
+# log error r: the tests allow 5e-6 per observation, ten times that.
+LL_PER_OBS = 5e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2312_05647_gb300 import build as lib_build
+    lib_build.build()
+    torch.cuda.set_device(0)
+
+
+_POOL = cf.ThreadPoolExecutor(max_workers=12)
+
+
+@pytest.fixture(scope="module")
+def mrna_oracle():
+    cfg = synth.mrna_protein()
+    csr = oracle.build_model(cfg["kind"], cfg["dims"], cfg["theta"])
+    return _POOL.submit(oracle.expv, csr, cfg["rho0"], cfg["times"])
+
+
+def _gpu_expv(kind, dims, theta, rho0, times, opts=None):
+    import torch
+    import paper_2312_05647_gb300 as mjp
+    m = mjp.Model(kind, dims, theta, mjp.FP32)
+    for k, v in (opts or {}).items():
+        m.set_option(k, v)
+    r = torch.tensor(rho0, dtype=torch.float32, device="cuda")
+    out, info = m.expv(r, times, info=True)
+    m.check()
+    return out.double().cpu().numpy(), info
+
+
+def test_mrna_protein_all_times_match_oracle(mrna_oracle):
+    cfg = synth.mrna_protein()
+    g, gi = _gpu_expv(cfg["kind"], cfg["dims"], cfg["theta"], cfg["rho0"], cfg["times"])
+    r, ri = mrna_oracle.result()
+    assert list(gi["K"]) == list(ri["K"]) and gi["K"].max() == 69089
+    err = np.abs(g - r).max(axis=1)
+    print("mRNA/protein FP32 max |GPU - oracle| per time:", ", ".join(f"{e:.2e}" for e in err))
+    assert err.max() <= FP32_TOL, err
+    assert g.min() >= 0.0
+    assert np.abs(g.sum(axis=1) - 1.0).max() <= 1e-6
+
+
+def test_defect_correction_off_is_reported_and_worse(mrna_oracle):
+    import paper_2312_05647_gb300 as mjp
+    cfg = synth.mrna_protein()
+    times = cfg["times"][[12, 16, 19]]
+    on, _ = _gpu_expv(cfg["kind"], cfg["dims"], cfg["theta"], cfg["rho0"], times)
+    off, _ = _gpu_expv(cfg["kind"], cfg["dims"], cfg["theta"], cfg["rho0"], times,
+                       opts={mjp.OPT_RENORM_PERIOD: 0})
+    r, _ = mrna_oracle.result()
+    r = r[[12, 16, 19]]
+    e_on, e_off = np.abs(on - r).max(), np.abs(off - r).max()
+    print(f"exit-defect correction on: {e_on:.2e}, off: {e_off:.2e}; mass drift off "
+          f"{np.abs(off.sum(axis=1) - 1).max():.2e}")
+    assert e_on <= FP32_TOL
+    assert e_off > e_on
+
+
+def test_mrna_protein_loglik_full_length():
+    import paper_2312_05647_gb300 as mjp
+    cfg = synth.mrna_protein()
+    snaps = synth.gillespie_snapshots(cfg["kind"], cfg["dims"], cfg["theta"], cfg["times"], 100, synth.rng(2, 0))
+    obs = synth.snapshot_obs(cfg["kind"], cfg["dims"], snaps)
+    thetas = synth.jitter(cfg["theta"], 3, 0.2, synth.rng(2, 77))
+    futs = [_POOL.submit(oracle.loglik, oracle.build_model(cfg["kind"], cfg["dims"], th), cfg["rho0"],
+                         cfg["times"], obs) for th in thetas]
+    m = mjp.Model(cfg["kind"], cfg["dims"], cfg["theta"], mjp.FP32)
+    o = mjp.Obs(40000, cfg["times"], obs, cfg["rho0"])
+    ll = mjp.loglik(m, o, thetas)  # default path: the register-resident chain
+    m.check()
+    m.set_option(mjp.OPT_CHAIN, 1)
+    ll_smem = mjp.loglik(m, o, thetas)
+    # Both kernels run the same compensated chain; only the final FP64 sum over
+    # the groups is taken in a thread-count dependent order.
+    np.testing.assert_allclose(ll, ll_smem, rtol=1e-13, atol=0)
+    nobs = sum(c.sum() for _, c in obs)
+    diffs = [abs(ll[b] - f.result()) for b, f in enumerate(futs)]
+    print("mRNA/protein FP32 loglik |GPU - oracle| per theta:", ", ".join(f"{d:.2e}" for d in diffs),
+          f"over {nobs:.0f} observations")
+    assert max(diffs) <= LL_PER_OBS * nobs
+
+
+def _heaviest(n):
+    b = synth.bd_batch()
+    N, th, t = b["N"], b["theta"], b["t"]
+    lam, mu = th[:, 0], th[:, 1]
+    om = 1.1 * np.maximum(lam + mu * (N - 2), mu * (N - 1))
+    x = om * t
+    K = np.floor(x + 6 * np.sqrt(x)) + 1
+    return np.argsort(-K)[:n], b
+
+
+def _oracle_bd(N, th, t):
+    r0 = np.zeros(int(N))
+    r0[0] = 1.0
+    out, _ = oracle.expv(oracle.build_model(oracle.BD1D, [int(N)], th), r0, [t])
+    return out[0]
+
+
+def test_uneven_batch_heaviest_instances_fp32():
+    import paper_2312_05647_gb300 as mjp
+    idx, b = _heaviest(8)
+    N, th, t = b["N"][idx], b["theta"][idx], b["t"][idx]
+    futs = [_POOL.submit(_oracle_bd, N[j], th[j], t[j]) for j in range(len(idx))]
+    bt = mjp.Batch(N, th, t, precision=mjp.FP32)
+    out = bt.run(bt.empty_out())
+    bt.check()
+    res = bt.split(out.double())
+    errs = [float(np.abs(res[j].cpu().numpy() - futs[j].result()).max()) for j in range(len(idx))]
+    print("uneven batch, heaviest instances: N", list(N), "max |GPU - oracle|:", ", ".join(f"{e:.2e}" for e in errs))
+    assert max(errs) <= FP32_TOL

@@ -74,7 +74,7 @@ def test_batch_bitwise_over_clusters_and_halos(prec):
 
 @pytest.mark.parametrize("prec", [1, 2])
 def test_batch_instances_that_need_a_cluster(prec):
-    # FP32 CTAs hold 6,720 states, FP64 CTAs 3,360: these need up to 3 and 6 CTAs.
+    # FP32 CTAs hold 5,040 states, FP64 CTAs 3,360: these need up to 4 and 6 CTAs.
     N = np.array([20000, 12000, 9000, 8193, 4097, 300], dtype=np.int64)
     th = np.stack([N / 5.0, np.full(len(N), 1.0)], 1)
     t = np.array([0.02, 0.03, 0.01, 0.02, 0.05, 0.5])
@@ -85,6 +85,26 @@ def test_batch_instances_that_need_a_cluster(prec):
     res = b.split(got.astype(np.float64))
     for j in range(len(N)):
         assert np.abs(res[j] - _oracle_bd(N[j], th[j], t[j], s0[j])).max() <= TOL[prec], j
+
+
+@pytest.mark.parametrize("period", [0, 8, 64])
+def test_defect_period_bitwise_across_kernels(period):
+    # The exit-defect correction is local to a state, so every kernel and
+    # cluster shape applies it identically, at any period or switched off.
+    import paper_2312_05647_gb300 as mjp
+    N, th, t, s0 = _small_batch(48, 17)
+    outs = []
+    for chain, cluster in ((1, 0), (2, 0), (2, 3)):
+        b = mjp.Batch(N, th, t, s0=s0, precision=1)
+        b.set_option(mjp.OPT_RENORM_PERIOD, period)
+        b.set_option(mjp.OPT_CHAIN, chain)
+        if cluster:
+            b.set_option(mjp.OPT_CLUSTER, cluster)
+        out = b.run(b.empty_out())
+        b.check()
+        outs.append(out.cpu().numpy())
+    np.testing.assert_array_equal(outs[1], outs[0])
+    np.testing.assert_array_equal(outs[2], outs[0])
 
 
 def test_batch_tune_keeps_results():
@@ -158,9 +178,10 @@ def test_register_chain_refusals():
     import paper_2312_05647_gb300 as mjp
     from paper_2312_05647_gb300.capi import MJPError
     cfg = synth.bd_small()
-    for opt, val in ((mjp.OPT_RENORM_PERIOD, 64), (mjp.OPT_THREADS, 128)):
-        with pytest.raises(MJPError):
-            _model_expv(64, cfg["theta"], 1, cfg["rho0"], [1.0], chain=2, opts={opt: val})
+    with pytest.raises(MJPError):
+        _model_expv(64, cfg["theta"], 1, cfg["rho0"], [1.0], chain=2, opts={mjp.OPT_THREADS: 128})
+    with pytest.raises(MJPError):  # the defect-correction period is a multiple of 8
+        _model_expv(64, cfg["theta"], 1, cfg["rho0"], [1.0], chain=2, opts={mjp.OPT_RENORM_PERIOD: 12})
     b = mjp.Batch(np.array([10]), np.array([[1.0, 1.0]]), np.array([0.5]))
     with pytest.raises(MJPError):
         b.set_option(mjp.OPT_HALO, 0)
