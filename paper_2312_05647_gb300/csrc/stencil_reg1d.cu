@@ -203,6 +203,13 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
   T2 r[QP + 1], dg[QP], up[QP];
   float2 res[QP], cb[QP];
   r[QP] = v_make((T)0, (T)0);
+  // States held outside the segment or the box receive inflow from their left
+  // neighbour (the birth coefficient is shared by the run) and hold nothing
+  // the chain needs; they are reset to zero at every round end so that they
+  // stay finite (0 x inf would otherwise reach the box, and a stale halo
+  // state could read an infinity).  Bit 2 j + c: pair j, component c lies
+  // outside.
+  unsigned outmask = 0;
 #pragma unroll
   for (int j = 0; j < QP; ++j) {
     T dv[2], uv[2], rv[2];
@@ -212,6 +219,7 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
       const int x = xw + y0 + hh * QP + j;
       const int n = xb + x;
       const bool in = wact && x >= 0 && x < ext && n >= 0 && n < N;
+      if (!in) outmask |= 1u << (2 * j + hh);
       const T fm = (T)n;
       const T bn = f_mul(co.b, fm);
       const T ain = n + 1 < N ? co.a : (T)0;
@@ -464,6 +472,22 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
       r[j == 0 ? (O + QP) % P1 : (j - 1 + O) % P1] = y;
     }
   };
+  // Reset of the states beyond the box (pairs at home).
+  auto scrub = [&]() {
+    if (outmask) {
+#pragma unroll
+      for (int j = 0; j < QP; ++j) {
+        if (outmask & (1u << (2 * j))) {
+          r[j].x = (T)0;
+          res[j].x = 0.0f;
+        }
+        if (outmask & (2u << (2 * j))) {
+          r[j].y = (T)0;
+          res[j].y = 0.0f;
+        }
+      }
+    }
+  };
   // Defect correction of the compensated chain after jump k_e (pairs at home);
   // the period is a multiple of the round length P1.
   auto defect = [&](int k_e) {
@@ -518,6 +542,7 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
     if (wact) RotSeq<P1, 0, P1>::run(jump_plain);
     else k += P1;
     defect(k - 1);
+    scrub();
     round_end(k - 1);
   }
 
@@ -538,6 +563,7 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
     const int k_e = k - 1;
     if (k_e >= Kmax) break;
     defect(k_e);
+    scrub();
     if ((k_e + P1) % kChunk1 == 0) cp_async_wait<0>();
     rec_round(k_e + 1, min(Kmax, k_e + P1));
     round_end(k_e);
