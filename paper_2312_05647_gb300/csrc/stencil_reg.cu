@@ -14,13 +14,22 @@
 //
 // Arithmetic per state is the same operation sequence, in the same order, as
 // the shared-memory kernel in stencil.cu (the compensated jump of
-// chain_common.cuh: delta form of rho B with the coefficients built from theta,
-// the rounding residual of every state carried in registers, and the exit
+// chain_common.cuh: delta form of rho B with the coefficients built from
+// theta, each state's rounding residual carried into the next jump, the exit
 // defects added back every p.renorm jumps), so both kernels produce
 // bit-identical chains; observations with one member per group give
-// bit-identical log-likelihoods.  A cluster of C CTAs splits the rows; block edges that
-// cross a CTA boundary are written into the neighbour CTA's halo slots
-// through distributed shared memory.
+// bit-identical log-likelihoods.  A cluster of C CTAs splits the rows; block
+// edges that cross a CTA boundary are written into the neighbour CTA's halo
+// slots through distributed shared memory.
+//
+// The residuals live in tensor memory (TMEM, 256 KB per SM, otherwise idle in
+// this kernel): the registers of a 512-thread CTA hold the 40 values of a
+// block and the coefficients, not 40 residuals as well.  Each warp owns its
+// 32 TMEM lanes (the quadrant warp % 4 may address) and 4 columns per row of
+// its blocks; a row's four residuals are read with one tcgen05.ld before the
+// row's update and written back with one tcgen05.st after it.  The CTA holds
+// one 256-column allocation from start to end (at least 116 KB of dynamic
+// shared memory keep it alone on its SM, so the allocation never waits).
 //
 // Every neighbour read and edge write uses a per-thread base plus a
 // compile-time offset (the edge arrays have fixed strides), and the jump
@@ -28,6 +37,7 @@
 // the arithmetic of the states.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "chain_common.cuh"
@@ -40,9 +50,11 @@ namespace mjp {
 namespace {
 
 constexpr int kQC = 4;            // columns per thread block of states
-// Threads per CTA at most: T = 384, one CTA per SM, so that a thread has 170
-// registers for its block of states, their residuals and the coefficients.
-constexpr int kT384 = 384;
+// Threads per CTA at most: T = 512, one CTA per SM, <= 128 registers per thread.
+constexpr int kT = 512;
+constexpr int kMaxNQ = 512;       // column quads (M <= 2048)
+constexpr unsigned kTmemCols = 256;  // TMEM columns per CTA (4 warps per lane quadrant x 4 x 10 rows <= 160)
+constexpr size_t kMinSmem = 116 * 1024;  // one CTA per SM (its TMEM allocation never waits)
 // Fixed strides of the edge arrays (per parity):
 //  - columns [2 sides][QR][T + 1] float2: the left (side 0) and right (side 1)
 //    column of block t, row pair r; entry T (kZero) is a zero slot;
@@ -93,17 +105,24 @@ __host__ __device__ inline RegLayout reg_layout(size_t edge_bytes, int nt, int n
   return s;
 }
 
-// Register value of observation slot r * 4 + c (row r, column c; columns
-// c0, c2 in pair 0 and c1, c3 in pair 1 of the row), by a tree of selections
-// (no local-memory array).
+// Register slot of row r of a block at rotation ROT: 0 = home (row r in slot
+// r), 1 = shifted (row r in slot r - 1, row 0 in the spare slot NR).
 template <int NR>
-__device__ __forceinline__ float pick(const float2 (&S)[NR][2], int slot) {
+__host__ __device__ constexpr int rslot(int r, int rot) {
+  return rot == 0 ? r : (r == 0 ? NR : r - 1);
+}
+
+// Register value of observation slot r * 4 + c (row r, column c; columns
+// c0, c2 in pair 0 and c1, c3 in pair 1 of the row) at rotation ROT, by a tree
+// of selections (no local-memory array).
+template <int NR, int ROT>
+__device__ __forceinline__ float pick(const float2 (&S)[NR + 1][2], int slot) {
   const bool c1 = slot & 1, c2 = slot & 2;
   const int r = slot >> 2;
   float v = 0.0f;
 #pragma unroll
   for (int q = 0; q < NR; ++q) {
-    const float2 a = S[q][0], b = S[q][1];
+    const float2 a = S[rslot<NR>(q, ROT)][0], b = S[rslot<NR>(q, ROT)][1];
     const float x = c2 ? (c1 ? b.y : a.y) : (c1 ? b.x : a.x);
     v = (r == q) ? x : v;
   }
@@ -117,6 +136,37 @@ __device__ __forceinline__ int opaque(int v) {
   asm volatile("" : "+r"(v));
   return v;
 }
+
+// Tensor-memory access (tcgen05, sm_100 family): allocation by one warp,
+// 32-lane x 4-column loads and stores of 32-bit values, and the waits that
+// order them.  Addresses are (lane << 16) | column.
+__device__ __forceinline__ void tmem_alloc(unsigned* slot, unsigned ncols) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(slot);
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(a), "r"(ncols) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Four residuals of one row: (c0, c2) and (c1, c3), the layout of the state pairs.
+__device__ __forceinline__ void tmem_ld4(unsigned taddr, float2& a, float2& b) {
+  unsigned r0, r1, r2, r3;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(taddr) : "memory");
+  // The loaded registers are defined only after the wait: tie them to it.
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3) :: "memory");
+  a = make_float2(__uint_as_float(r0), __uint_as_float(r1));
+  b = make_float2(__uint_as_float(r2), __uint_as_float(r3));
+}
+__device__ __forceinline__ void tmem_st4(unsigned taddr, float2 a, float2 b) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(__float_as_uint(a.x)), "r"(__float_as_uint(a.y)), "r"(__float_as_uint(b.x)),
+               "r"(__float_as_uint(b.y))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Exclusive prefix sum of v over the block (blockDim <= 1024).
 __device__ int block_exclusive_scan(int v, int* wsum) {
@@ -135,13 +185,14 @@ __device__ int block_exclusive_scan(int v, int* wsum) {
   return off + x - v;
 }
 
-template <int kQR, int kT>
+template <int kQR>
 __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p, const int NQ, const int RS) {
   using G = EdgeGeo<kQR, kT>;
   constexpr int kZero = G::kZero;
   constexpr int kRows = 2 * kQR;  // rows of a thread's block
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int wsum[32];
+  __shared__ unsigned tmem_base;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
@@ -196,7 +247,13 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
   // The planner caps K (MJP_OPT_K_CAP, default 2^26); the loop counts in 32 bits.
   const int Kmax = Kmax64 < (1LL << 30) ? (int)Kmax64 : 0;
   if (Kmax64 >= (1LL << 30) && tid == 0 && rank == 0) set_status(p.status, kStatusKcap);
+  if (warp == 0) tmem_alloc(&tmem_base, kTmemCols);
+  tmem_fence_before();
   __syncthreads();
+  tmem_fence_after();
+  // This thread's residuals: lane 32 (warp % 4) + lane, columns
+  // (warp / 4) 4 NR + 4 r .. + 3 for row r of its block.
+  const unsigned tres = tmem_base + ((32u * (unsigned)(warp & 3)) << 16) + (unsigned)(warp >> 2) * 8u * kQR;
 
   // Observation entries: (member q, register slot, time) of the states this
   // thread holds, in member order (= time order).  Two passes: count, then
@@ -241,23 +298,26 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
   // Column coefficients (rates into column m, scaled by 1/Omega): gamma_m
   // (m+1) from m+1, k_p m from p-1, and the negated exit -e0 without the
   // gamma_p p part, as pairs of the columns (c0, c2) and (c1, c3) that share a
-  // register pair.
+  // register pair.  Threads without a block run the same instructions (the
+  // tensor-memory accesses are warp-wide) with every coefficient zero, so
+  // their values stay zero.
   float crc[kQC], cdc[kQC], d0c[kQC];
   int colmask = 0;  // bit c: column m0 + c lies in the box
+  const float own = owner ? 1.0f : 0.0f;
 #pragma unroll
   for (int c = 0; c < kQC; ++c) {
     const int m = m0 + c;
     if (m < M) colmask |= 1 << c;
     const float fm = (float)m;
-    crc[c] = f_mul(co.b, (float)(m + 1));
-    cdc[c] = f_mul(co.c, fm);
-    d0c[c] = -mrna_col(co, m, M).e0;
+    crc[c] = owner ? f_mul(co.b, (float)(m + 1)) : 0.0f;
+    cdc[c] = owner ? f_mul(co.c, fm) : 0.0f;
+    d0c[c] = owner ? -mrna_col(co, m, M).e0 : 0.0f;
   }
   const float2 d0A = v_make(d0c[0], d0c[2]), d0B = v_make(d0c[1], d0c[3]);
   const float2 crA = v_make(crc[0], crc[2]), crB = v_make(crc[1], crc[3]);
   const float2 cdA = v_make(cdc[0], cdc[2]), cdB = v_make(cdc[1], cdc[3]);
-  const float c_l = co.a;
-  const float2 c_l2 = v_make(co.a, co.a), c_gp = v_make(co.d, co.d), c_ngp = v_make(-co.d, -co.d);
+  const float c_l = own * co.a, c_d = own * co.d;
+  const float2 c_l2 = v_make(c_l, c_l), c_gp = v_make(c_d, c_d), c_ngp = v_make(-c_d, -c_d);
   const bool padcols = colmask != (1 << kQC) - 1;
   // Row of this block that holds row P-1 (-1 if none).
   const int rtop = (P - 1 >= pb && P - 1 < pb + kRows) ? P - 1 - pb : -1;
@@ -272,9 +332,12 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
   unsigned char* const E0 = smem + L.edge;
 
   // rho0 into registers, its edges into parity 0.  Row r of the block is
-  // S[r][0] = (c0, c2), S[r][1] = (c1, c3), updated in place every jump.
+  // S[r][0] = (c0, c2), S[r][1] = (c1, c3); S[kRows] is a spare row: a jump
+  // writes row r's new values over row r-1's old ones (ascending) or row r+1's
+  // (descending), so the rows shift by one slot and back every two jumps and
+  // no register is copied.
   constexpr int NR = kRows;
-  float2 S[NR][2];
+  float2 S[NR + 1][2];
   const float* rho0 = reinterpret_cast<const float*>(p.rho0);
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
@@ -287,11 +350,10 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
     S[r][0] = v_make(v[0], v[2]);
     S[r][1] = v_make(v[1], v[3]);
   }
-  // Residual of every state of the block (same layout), zero at the start;
-  // between the two halves of a jump it holds the partial update t.
-  float2 res[NR][2];
+  S[NR][0] = S[NR][1] = v_make(0.0f, 0.0f);
+  // Residuals start at zero.
 #pragma unroll
-  for (int r = 0; r < NR; ++r) res[r][0] = res[r][1] = v_make(0.0f, 0.0f);
+  for (int r = 0; r < NR; ++r) tmem_st4(tres + 4u * r, v_make(0.0f, 0.0f), v_make(0.0f, 0.0f));
   // The row arrays of the neighbouring CTAs: our first row is the row above
   // CTA rank-1 (its array 0), our last row the row below CTA rank+1 (array 1).
   unsigned char* nb_dn = nullptr;
@@ -303,36 +365,39 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
   }
   // Edges of the block: the left (c0) and right (c3) columns per row pair,
   // the first and last rows as (c0, c2, c1, c3).
-  auto publish = [&](int par) {
+  auto publish = [&](int par, auto ROTC) {
+    constexpr int ROT = decltype(ROTC)::value;
     unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
 #pragma unroll
     for (int r = 0; r < kQR; ++r) {
+      const int s0 = rslot<NR>(2 * r, ROT), s1 = rslot<NR>(2 * r + 1, ROT);
       float* cl = reinterpret_cast<float*>(Ep + G::col(0, r) + oT8);
       float* cr = reinterpret_cast<float*>(Ep + G::col(1, r) + oT8);
-      cl[0] = S[2 * r][0].x;
-      cl[1] = S[2 * r + 1][0].x;
-      cr[0] = S[2 * r][1].y;
-      cr[1] = S[2 * r + 1][1].y;
+      cl[0] = S[s0][0].x;
+      cl[1] = S[s1][0].x;
+      cr[0] = S[s0][1].y;
+      cr[1] = S[s1][1].y;
     }
+    const int sf = rslot<NR>(0, ROT), sl = rslot<NR>(NR - 1, ROT);
     float2* fr = reinterpret_cast<float2*>(Ep + G::row(0) + oT16);
     float2* lr = reinterpret_cast<float2*>(Ep + G::row(1) + oT16);
-    fr[0] = S[0][0];
-    fr[1] = S[0][1];
-    lr[0] = S[NR - 1][0];
-    lr[1] = S[NR - 1][1];
+    fr[0] = S[sf][0];
+    fr[1] = S[sf][1];
+    lr[0] = S[sl][0];
+    lr[1] = S[sl][1];
     const size_t po = par ? G::par_bytes : 0;
     if (nb_dn) {
       float2* d = reinterpret_cast<float2*>(nb_dn + po);
-      d[0] = S[0][0];
-      d[1] = S[0][1];
+      d[0] = S[sf][0];
+      d[1] = S[sf][1];
     }
     if (nb_up) {
       float2* d = reinterpret_cast<float2*>(nb_up + po);
-      d[0] = S[NR - 1][0];
-      d[1] = S[NR - 1][1];
+      d[0] = S[sl][0];
+      d[1] = S[sl][1];
     }
   };
-  if (owner) publish(0);
+  publish(0, std::integral_constant<int, 0>{});
   if (C > 1) cluster.sync();
   else __syncthreads();
 
@@ -363,7 +428,8 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
 
   // Observations of rho_k for the active times [l, h] of jump k (Kahan, FP32).
   int ecur = ebeg;
-  auto accumulate = [&](int k, int l, int h) {
+  auto accumulate = [&](int k, int l, int h, auto ROTC) {
+    constexpr int ROT = decltype(ROTC)::value;
     if (!owner || l > h) return;
     const int sk = k & (kStage - 1);
     while (ecur < eend && (ent[ecur].y >> 6) < l) ++ecur;
@@ -371,7 +437,7 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
       const int2 en = ent[e];
       const int ti = en.y >> 6;
       if (ti > h) break;
-      const float v = pick<NR>(S, en.y & 63);
+      const float v = pick<NR, ROT>(S, en.y & 63);
       const float w = ring[ti * kStage + sk];
       const float y = __fsub_rn(__fmul_rn(w, v), acc_c[en.x]);
       const float s0 = acc_s[en.x];
@@ -397,165 +463,161 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
   };
   if (wwarp && any_rec && Kmax >= 1) rec_step(1);
   __syncthreads();
-  accumulate(0, lo, hi);  // rho_0 with the weights of jump 0
+  accumulate(0, lo, hi, std::integral_constant<int, 0>{});  // rho_0 with the weights of jump 0
 
-  // One jump, rho_{k-1} -> rho_k, in two halves around the cluster barrier.
-  // The terms of a state's update t are added in one order in every kernel
-  // that runs the compensated mRNA/protein chain: the residual, the exit
-  // -e rho (e = e0 + gamma_p p), in row P-1 the protein birth k_p m rho that
-  // does not leave it, then the inflows from below (k_p m rho(p-1)), above
-  // (gamma_p (p+1) rho(p+1)), left (k_m rho(m-1)) and right (gamma_m (m+1)
-  // rho(m+1)); then y = rho + t and the new residual.  In that order, every
-  // term that reads another thread's values comes after all terms of the
-  // same state that do not: the first half (PRE) forms, for every state, t up
-  // to its first such term from the thread's own registers and leaves it in
-  // res; the second half (POST), after the barrier, reads the neighbours'
-  // edges, adds the remaining terms and finishes every state in place.
-  //  - interior rows: PRE does everything but c0's left and right inflows
-  //    and c3's right inflow;
-  //  - the first row: PRE does the residual, exit and P-1 terms (its below
-  //    is the neighbouring block's last row);
-  //  - the last row: PRE adds its below too (the row below is updated in
-  //    place before POST reaches the last row).
-  // Row P-1 without branches when it is a block's last row: every thread
-  // adds topA / topB x rho in its last row, k_p m (both columns of the pair)
-  // in the block holding P-1 and zero elsewhere (adding +0 changes no
-  // value); the row above it is the zero slot.  Warps with a thread whose
-  // block holds P-1 elsewhere, rows beyond the box or padding columns run the
-  // EDGE variant with explicit checks (warp-uniform, so no warp runs both).
+  // One jump of the block: rho_{k-1} at rotation DIR (0: home, rows
+  // ascending; 1: shifted, rows descending) -> rho_k at rotation 1 - DIR.
+  // Per state, in the shared-memory kernel's order: (1 - e) rho + k_m rho(m-1)
+  // + gamma_m (m+1) rho(m+1) + k_p m rho(p-1) + gamma_p (p+1) rho(p+1); the row
+  // holding P-1 adds k_p m back to 1 - e (no protein birth out of it), rows
+  // beyond it and padding columns stay zero.
+  // Row P-1 (no protein birth out of it: 1 - e gains k_p m back) is handled
+  // without branches when it is a block's last row: every thread adds topA /
+  // topB to the diagonal of its last row, k_p m (both columns of the pair) in
+  // the block holding P-1 and zero elsewhere (adding +0 changes no value); the
+  // row above it is the zero slot.  Warps with a thread whose block holds P-1
+  // elsewhere, rows beyond the box or padding columns run the EDGE update with
+  // explicit checks (warp-uniform, so no warp runs both).
   const bool edge_t = padcols || (rtop >= 0 && rtop != NR - 1);
   const bool edge_w = __any_sync(kFull, edge_t);
   const float2 topA = rtop == NR - 1 ? cdA : v_make(0.0f, 0.0f);
   const float2 topB = rtop == NR - 1 ? cdB : v_make(0.0f, 0.0f);
-  auto pre = [&](auto EDGEC) {
+  auto update = [&](int par, auto DIRC, auto EDGEC) {
+    constexpr int DIR = decltype(DIRC)::value;
     constexpr bool EDGE = decltype(EDGEC)::value;
+    const unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
     const int rtk = EDGE ? opaque(rtop) : -1;
-    float2 fp;  // row index as a float pair, stepped exactly (integers below 2^24)
+    tmem_wait_st();  // the last jump's residual stores are complete
+    // Row index as a float pair, stepped exactly (integers below 2^24).
+    float2 fp;
     {
-      const float f0 = (float)opaque(pb);
+      const float f0 = (float)opaque(pb + (DIR == 0 ? 0 : NR - 1));
       fp = v_make(f0, f0);
     }
+    const float2 fstep = DIR == 0 ? v_make(1.0f, 1.0f) : v_make(-1.0f, -1.0f);
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const float2 A = S[r][0], B = S[r][1];
-      float2 tA = v_fma(v_fma(c_ngp, fp, d0A), A, res[r][0]);  // residual + exit
-      float2 tB = v_fma(v_fma(c_ngp, fp, d0B), B, res[r][1]);
-      if (EDGE && r == rtk) {
-        tA = v_fma(cdA, A, tA);
-        tB = v_fma(cdB, B, tB);
-      }
-      if (!EDGE && r == NR - 1) {
-        tA = v_fma(topA, A, tA);
-        tB = v_fma(topB, B, tB);
-      }
-      if (r > 0) {  // below: own registers
-        tA = v_fma(cdA, S[r - 1][0], tA);
-        tB = v_fma(cdB, S[r - 1][1], tB);
-      }
-      if (r > 0 && r < NR - 1) {
-        const float2 cup = v_fma(c_gp, fp, c_gp);  // gamma_p (p+1) from p+1
-        tA = v_fma(cup, S[r + 1][0], tA);
-        tB = v_fma(cup, S[r + 1][1], tB);
-        tA.y = f_fma(c_l, B.x, tA.y);     // c2: from m-1 (c1), from m+1 (c3)
-        tA.y = f_fma(crA.y, B.y, tA.y);
-        tB = v_fma(c_l2, A, tB);          // c1 and c3 from m-1 (c0, c2)
-        tB.x = f_fma(crB.x, A.y, tB.x);   // c1 from m+1 (c2)
-      }
-      res[r][0] = tA;
-      res[r][1] = tB;
-      fp = v_add(fp, v_make(1.0f, 1.0f));
-    }
-  };
-  auto post = [&](int par, auto EDGEC) {
-    constexpr bool EDGE = decltype(EDGEC)::value;
-    const int rtk = EDGE ? opaque(rtop) : -1;
-    const unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      // The left block's c3 and the right block's c0 of this row pair.
+    for (int i = 0; i < NR; ++i) {
+      const int r = DIR == 0 ? i : NR - 1 - i;
+      const int so = rslot<NR>(r, DIR);                                  // old row r
+      const int sn = DIR == 0 ? (r == 0 ? NR : r - 1) : r;               // its new value
+      // The left block's c3 and the right block's c0 of this row pair, read at
+      // its first row in this jump's order.
       float2 lp, rp;
-      if ((r & 1) == 0) {
+      if ((i & 1) == 0) {
         lp = *reinterpret_cast<const float2*>(Ep + G::col(1, r >> 1) + oL);
         rp = *reinterpret_cast<const float2*>(Ep + G::col(0, r >> 1) + oR);
       }
+      const float2 A = S[so][0], B = S[so][1];
+      float2 bA, bB, aA, aB;  // rows p-1 and p+1: registers, or the row below / above the block
+      if (r == 0) {
+        const float2* e = reinterpret_cast<const float2*>(Ep + G::row(1) + oB);
+        bA = e[0];
+        bB = e[1];
+      } else {
+        bA = S[rslot<NR>(r - 1, DIR)][0];
+        bB = S[rslot<NR>(r - 1, DIR)][1];
+      }
+      if (r + 1 == NR) {
+        const float2* e = reinterpret_cast<const float2*>(Ep + G::row(0) + oA);
+        aA = e[0];
+        aB = e[1];
+      } else {
+        aA = S[rslot<NR>(r + 1, DIR)][0];
+        aB = S[rslot<NR>(r + 1, DIR)][1];
+      }
       const float lin = (r & 1) ? lp.y : lp.x;
       const float rin = (r & 1) ? rp.y : rp.x;
-      const float2 A = S[r][0], B = S[r][1];
-      float2 tA = res[r][0], tB = res[r][1];
-      if (r == 0 || r == NR - 1) {
-        const float f0 = (float)opaque(pb + r);
-        const float2 fp = v_make(f0, f0);
-        if (r == 0) {  // below: the row under the block; above: own
-          const float2* e = reinterpret_cast<const float2*>(Ep + G::row(1) + oB);
-          tA = v_fma(cdA, e[0], tA);
-          tB = v_fma(cdB, e[1], tB);
-          const float2 cup = v_fma(c_gp, fp, c_gp);
-          tA = v_fma(cup, S[1][0], tA);
-          tB = v_fma(cup, S[1][1], tB);
-        } else {       // above: the row over the block
-          const float2* e = reinterpret_cast<const float2*>(Ep + G::row(0) + oA);
-          const float2 cup = v_fma(c_gp, fp, c_gp);
-          tA = v_fma(cup, e[0], tA);
-          tB = v_fma(cup, e[1], tB);
-        }
-        tA.x = f_fma(c_l, lin, tA.x);     // from m-1: the left block's c3, c1
-        tA.y = f_fma(c_l, B.x, tA.y);
-        tA = v_fma(crA, B, tA);           // from m+1: (c1, c3)
-        tB = v_fma(c_l2, A, tB);          // from m-1: (c0, c2)
-        tB.x = f_fma(crB.x, A.y, tB.x);   // from m+1: c2, the right block's c0
-        tB.y = f_fma(crB.y, rin, tB.y);
-      } else {
-        tA.x = f_fma(c_l, lin, tA.x);     // c0 from m-1 (left block's c3), m+1 (c1)
-        tA.x = f_fma(crA.x, B.x, tA.x);
-        tB.y = f_fma(crB.y, rin, tB.y);   // c3 from m+1 (right block's c0)
-      }
-      float2 yA = comp_finish(A, tA, res[r][0]);
-      float2 yB = comp_finish(B, tB, res[r][1]);
+      float2 rA, rB;  // residuals of row r
+      tmem_ld4(tres + 4u * r, rA, rB);
+      const float2 dA = v_fma(c_ngp, fp, d0A), dB = v_fma(c_ngp, fp, d0B);  // -e_{m,p}
+      const float2 cup = v_fma(c_gp, fp, c_gp);  // gamma_p (p+1) from p+1
+      // t = residual + inflows from the left, right, below and above + exit,
+      // and in row P-1 the protein birth k_p m that does not leave it.
+      float2 tA = rA;
+      tA.x = f_fma(c_l, lin, tA.x);   // from m - 1: the left block's c3
+      tA.y = f_fma(c_l, B.x, tA.y);   // c1
+      tA = v_fma(crA, B, tA);         // from m + 1: (c1, c3)
+      tA = v_fma(cdA, bA, tA);
+      tA = v_fma(cup, aA, tA);
+      tA = v_fma(dA, A, tA);
+      float2 tB = v_fma(c_l2, A, rB);
+      tB.x = f_fma(crB.x, A.y, tB.x); // from m + 1: c2
+      tB.y = f_fma(crB.y, rin, tB.y); // the right block's c0
+      tB = v_fma(cdB, bB, tB);
+      tB = v_fma(cup, aB, tB);
+      tB = v_fma(dB, B, tB);
+      // (Selections, not branches: the warp stays converged for the
+      // tensor-memory store below.)
+      const float2 z2 = v_make(0.0f, 0.0f);
       if (EDGE) {
-        if (rtk >= 0 && r > rtk) {  // rows beyond the box
-          yA = yB = v_make(0.0f, 0.0f);
-          res[r][0] = res[r][1] = v_make(0.0f, 0.0f);
-        }
-        if (padcols) {              // padding columns of the last quad
-          if (!(colmask & 2)) yB.x = res[r][1].x = 0.0f;
-          if (!(colmask & 4)) yA.y = res[r][0].y = 0.0f;
-          if (!(colmask & 8)) yB.y = res[r][1].y = 0.0f;
-        }
+        tA = v_fma(r == rtk ? cdA : z2, A, tA);
+        tB = v_fma(r == rtk ? cdB : z2, B, tB);
+      } else if (r == NR - 1) {
+        tA = v_fma(topA, A, tA);
+        tB = v_fma(topB, B, tB);
       }
-      S[r][0] = yA;
-      S[r][1] = yB;
+      float2 yA = comp_finish(A, tA, rA);
+      float2 yB = comp_finish(B, tB, rB);
+      if (EDGE) {
+        const bool beyond = rtk >= 0 && r > rtk;  // rows beyond the box
+        yA = beyond ? z2 : yA;
+        yB = beyond ? z2 : yB;
+        rA = beyond ? z2 : rA;
+        rB = beyond ? z2 : rB;
+        // Padding columns of the last quad: c1 (bit 1), c2 (bit 2), c3 (bit 3).
+        const bool p1c = !(colmask & 2), p2c = !(colmask & 4), p3c = !(colmask & 8);
+        yB.x = p1c ? 0.0f : yB.x;
+        rB.x = p1c ? 0.0f : rB.x;
+        yA.y = p2c ? 0.0f : yA.y;
+        rA.y = p2c ? 0.0f : rA.y;
+        yB.y = p3c ? 0.0f : yB.y;
+        rB.y = p3c ? 0.0f : rB.y;
+      }
+      tmem_st4(tres + 4u * r, rA, rB);
+      S[sn][0] = yA;
+      S[sn][1] = yB;
+      fp = v_add(fp, fstep);
     }
   };
 
-  // Exit-defect correction of rho_k: every state adds p.renorm x its defect
-  // x its value to its residual (states outside the box hold zero and stay
-  // zero).
+  // Exit-defect correction of rho_k (rotation ROT): every state adds p.renorm
+  // x its defect x its value to its residual (zero coefficients and values
+  // outside the box keep those residuals zero).
   const float period = (float)p.renorm;
-  auto defect_fix = [&]() {
-#pragma unroll
+  auto defect_fix = [&](auto ROTC) {
+    constexpr int ROT = decltype(ROTC)::value;
+    tmem_wait_st();
+#pragma unroll 1
     for (int r = 0; r < NR; ++r) {
       const int pr = pb + r;
-      const float b0 = __fmul_rn(period, mrna_defect(mrna_col(co, m0 + 0, M), co.d, pr));
-      const float b1 = __fmul_rn(period, mrna_defect(mrna_col(co, m0 + 1, M), co.d, pr));
-      const float b2 = __fmul_rn(period, mrna_defect(mrna_col(co, m0 + 2, M), co.d, pr));
-      const float b3 = __fmul_rn(period, mrna_defect(mrna_col(co, m0 + 3, M), co.d, pr));
-      res[r][0] = v_fma(v_make(b0, b2), S[r][0], res[r][0]);
-      res[r][1] = v_fma(v_make(b1, b3), S[r][1], res[r][1]);
+      float2 rA, rB;
+      tmem_ld4(tres + 4u * r, rA, rB);
+      float b[kQC];
+#pragma unroll
+      for (int c = 0; c < kQC; ++c) b[c] = own * __fmul_rn(period, mrna_defect(mrna_col(co, m0 + c, M), co.d, pr));
+      // Row r sits in register slot r (home) or r - 1 (shifted); pick it by rotation.
+      float2 ya = v_make(0.0f, 0.0f), yb = ya;
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+        if (q == r) {
+          ya = S[rslot<NR>(q, ROT)][0];
+          yb = S[rslot<NR>(q, ROT)][1];
+        }
+      rA = v_fma(v_make(b[0], b[2]), ya, rA);
+      rB = v_fma(v_make(b[1], b[3]), yb, rB);
+      tmem_st4(tres + 4u * r, rA, rB);
     }
   };
 
   // ---- the jump chain -------------------------------------------------------
-  if (owner && Kmax >= 1) {
-    if (edge_w) pre(std::true_type{});
-    else pre(std::false_type{});
-  }
-  for (int k = 1; k <= Kmax; ++k) {
+  int k = 1;
+  auto step = [&](auto DIRC) {
+    constexpr int DIR = decltype(DIRC)::value;
+    constexpr int ROT = 1 - DIR;  // rotation of rho_k
     const int par = (k - 1) & 1;
-    if (owner) {
-      if (edge_w) post(par, std::true_type{});
-      else post(par, std::false_type{});
-      publish(par ^ 1);
-    }
+    if (edge_w) update(par, DIRC, std::true_type{});
+    else update(par, DIRC, std::false_type{});
+    publish(par ^ 1, std::integral_constant<int, ROT>{});
     // Chunk c (jumps [c kChunk, (c+1) kChunk)) is staged at jump (c-1) kChunk + 1,
     // after the last read of the slots it reuses (chunk c-2's, read up to jump
     // (c-1) kChunk - 1), and waited for at jump c kChunk - 1, before the barrier
@@ -568,18 +630,21 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
     cluster_arrive_relaxed();
     // Work that touches no edge overlaps the barrier: the exit-defect
     // correction and the observations of rho_k, the next chunk of weights,
-    // the recurrence one jump ahead, and the first half of jump k + 1.
-    if (owner && p.renorm > 0 && k % p.renorm == 0) defect_fix();
+    // the recurrence one jump ahead.
+    if (p.renorm > 0 && k % p.renorm == 0) defect_fix(std::integral_constant<int, ROT>{});
     advance(k, lo, hi);
-    accumulate(k, lo, hi);
+    accumulate(k, lo, hi, std::integral_constant<int, ROT>{});
     if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
     if (wwarp && any_rec && k + 1 <= Kmax) rec_step(k + 1);
-    if (owner && k < Kmax) {
-      if (edge_w) pre(std::true_type{});
-      else pre(std::false_type{});
-    }
     cluster_wait();
+    ++k;
+  };
+  while (k + 1 <= Kmax) {
+    step(std::integral_constant<int, 0>{});
+    step(std::integral_constant<int, 1>{});
   }
+  if (k <= Kmax) step(std::integral_constant<int, 0>{});
+  // rho_Kmax may be left at rotation 1; only the accumulators are read below.
   cp_async_wait<0>();
 
   // ---- epilogue: sum_g c_g log(a_g) over the cluster's accumulators ---------
@@ -619,7 +684,14 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
     }
     if (bad) set_status(p.status, kStatusNumeric);
   }
-  if (C > 1) cluster.sync();  // keep every CTA's accumulators alive until rank 0 is done
+  // Keep every CTA's accumulators alive until rank 0 is done, and every
+  // residual store complete before the tensor memory is released.
+  tmem_wait_st();
+  tmem_fence_before();
+  if (C > 1) cluster.sync();
+  else __syncthreads();
+  tmem_fence_after();
+  if (warp == 0) tmem_dealloc(tmem_base, kTmemCols);
 }
 
 }  // namespace
@@ -630,8 +702,7 @@ bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluste
   if (M < 1 || P < 1 || ntimes < 1) return false;
   if (threads != 0) return false;  // the launch shape is this kernel's own
   const int NQ = (int)((M + kQC - 1) / kQC);
-  constexpr int T = kT384;
-  if (NQ > T) return false;
+  if (NQ > kMaxNQ) return false;
   // Fewest CTAs per instance first; for each, 8 rows per thread before 10.
   const size_t smem_cap = 227 * 1024;
   for (int C = 1; C <= max_cluster; ++C)
@@ -641,27 +712,27 @@ bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluste
       const int RS = (int)((rows + rows_blk - 1) / rows_blk) * rows_blk;
       if ((int64_t)(C - 1) * RS >= P) continue;  // the last CTA would be empty
       const int Tc = NQ * (RS / rows_blk);
-      if (Tc > T) continue;
-      const size_t edge = 2 * (QR == 5 ? EdgeGeo<5, T>::par_bytes : EdgeGeo<4, T>::par_bytes);
+      if (Tc > kT) continue;
+      const size_t edge = 2 * (QR == 5 ? EdgeGeo<5, kT>::par_bytes : EdgeGeo<4, kT>::par_bytes);
       const RegLayout L = reg_layout(edge, ntimes, nmem);
       if (L.total + 1024 > smem_cap) continue;  // leave room for static shared memory
       out->cluster = C;
       out->rows = RS;
       out->nq = NQ;
       out->qr = QR;
-      out->tmax = T;
+      out->tmax = kT;
       out->threads = ((Tc + 31) / 32) * 32;
-      out->smem = L.total;
+      out->smem = std::max(L.total, kMinSmem);
       return true;
     }
   return false;
 }
 
-template <int QR, int T>
+template <int QR>
 cudaError_t launch_reg(const ChainParams& p, const RegPlan& rp, cudaStream_t s) {
   static int smem_set = 0;
   static bool nonportable = false;
-  auto kern = chain_reg2d_kernel<QR, T>;
+  auto kern = chain_reg2d_kernel<QR>;
   cudaError_t e;
   if ((int)rp.smem > smem_set) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rp.smem);
@@ -690,7 +761,7 @@ cudaError_t launch_reg(const ChainParams& p, const RegPlan& rp, cudaStream_t s) 
 
 cudaError_t launch_chain_reg2d(const ChainParams& p, const RegPlan& rp, cudaStream_t s) {
   if (p.B <= 0) return cudaSuccess;
-  return rp.qr == 5 ? launch_reg<5, kT384>(p, rp, s) : launch_reg<4, kT384>(p, rp, s);
+  return rp.qr == 5 ? launch_reg<5>(p, rp, s) : launch_reg<4>(p, rp, s);
 }
 
 }  // namespace mjp
