@@ -311,16 +311,35 @@ void expv_batch_destroy(mjp_batch* b);
  * of 16 MiB inside the library, which every GPU that loads the library keeps
  * until the process exits; larger requests fail with MJP_ERR_ARG and a
  * message giving the size needed.  The first call on a device looks up that
- * array's device address (once per device, with the device current), so make
- * it before any stream capture.  All calls share the array and it keeps the
- * last call's contents (the call resets what must start at zero): calls that
- * overlap on the GPU -- on different streams, threads or devices sharing a
- * process -- race, so order them.  The call synchronises `stream` and reports
- * device-side errors (MJP_ERR_KCAP, MJP_ERR_NUMERIC) itself.
+ * array's device address (once per device, with the device current).  All
+ * calls share the array and it keeps the last call's contents (the call resets
+ * what must start at zero): calls that overlap on the GPU -- on different
+ * streams, threads or devices sharing a process -- race, so order them.  The
+ * call copies from host stack memory, synchronises `stream` and reports
+ * device-side errors (MJP_ERR_KCAP, MJP_ERR_NUMERIC) itself; it must not be
+ * called while `stream` is capturing a graph (MJP_ERR_UNSUPPORTED).  Models of
+ * more than 2^31 - 1 states are MJP_ERR_ARG; a launch shape the GPU cannot
+ * hold is MJP_ERR_UNSUPPORTED.
  * Errors: MJP_ERR_ARG, MJP_ERR_UNSUPPORTED, MJP_ERR_KCAP, MJP_ERR_NUMERIC, MJP_ERR_CUDA.
  */
 int expv_series_static(int kind, const int64_t* dims, int ndims, const double* theta, int ntheta,
                        const float* rho0, const double* times, int ntimes, float* out, void* stream);
+
+/*
+ * Measured on-chip peaks of the current device, for roofline denominators (the
+ * paper has no counterpart; the benchmark reports the chain kernels against
+ * them).  MJP_PEAK_FP32_FMA: packed FP32 fused multiply-adds from independent
+ * chains on two 512-thread CTAs per SM, in TFLOP/s (2 flops per lane and
+ * instruction); MJP_PEAK_SMEM: 16-byte shared-memory loads and stores of
+ * consecutive vectors (no bank conflicts) on the same grid, in GB/s counting
+ * read plus written bytes.  `iters` loop iterations per thread (a few hundred
+ * thousand give ~10 ms); best of three timed launches with CUDA events on
+ * `stream` after one untimed launch.  Allocates and frees a small device
+ * buffer.  Errors: MJP_ERR_ARG, MJP_ERR_ALLOC, MJP_ERR_CUDA.
+ */
+#define MJP_PEAK_FP32_FMA 1
+#define MJP_PEAK_SMEM 2
+int mjp_measure_peak(int which, int iters, double* result, void* stream);
 
 /*
  * Synchronise `stream` and report device-side errors recorded by earlier

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import capi
 from .capi import (AUTOREG, BD1D, CSR, FP32, FP64, METHOD_KRYLOV, METHOD_RK4, METHOD_RMJP, MRNA_PROT2D, OPT_ARENA,
-                   OPT_CHAIN, OPT_CLUSTER, OPT_HALO, OPT_K_CAP, OPT_KAPPA, OPT_METHOD, OPT_PROFILE, OPT_RENORM_PERIOD, OPT_THREADS, PTR_DEVICE, PTR_HOST, TRUNC_PAPER, TRUNC_TOL, TWOSTATE,
+                   OPT_CHAIN, OPT_CLUSTER, OPT_HALO, OPT_K_CAP, OPT_KAPPA, OPT_METHOD, OPT_PROFILE, OPT_RENORM_PERIOD, OPT_THREADS, PEAK_FP32_FMA, PEAK_SMEM, PTR_DEVICE, PTR_HOST, TRUNC_PAPER, TRUNC_TOL, TWOSTATE,
                    MJPError)
 
 __all__ = ["Model", "Obs", "Batch", "loglik", "BD1D", "TWOSTATE", "MRNA_PROT2D", "AUTOREG", "CSR", "FP32", "FP64",
@@ -205,6 +205,14 @@ def loglik(model: Model, obs: Obs, theta, trunc: int = TRUNC_PAPER, tol: float =
     capi.check(L.loglik(model._h, obs._h, ctypes.c_void_p(th.ctypes.data), B, ctypes.c_void_p(res.ctypes.data),
                         PTR_HOST, int(trunc), float(tol), _stream_ptr(stream)))
     return res
+
+
+def measure_peak(which: int, iters: int = 200000, stream=None) -> float:
+    """Measured on-chip peak of the current device: PEAK_FP32_FMA (TFLOP/s)
+    or PEAK_SMEM (GB/s, read + write); see mjp_measure_peak."""
+    v = ctypes.c_double()
+    capi.check(capi.lib().mjp_measure_peak(int(which), int(iters), ctypes.byref(v), _stream_ptr(stream)))
+    return v.value
 
 
 class Batch:

@@ -24,6 +24,7 @@ PTR_HOST, PTR_DEVICE = 0, 1
 OPT_RENORM_PERIOD, OPT_K_CAP, OPT_THREADS, OPT_CLUSTER, OPT_PROFILE, OPT_ARENA, OPT_CHAIN, OPT_HALO = 1, 2, 3, 4, 5, 6, 7, 8
 OPT_METHOD, OPT_KAPPA = 9, 10
 METHOD_RMJP, METHOD_RK4, METHOD_KRYLOV = 0, 1, 2
+PEAK_FP32_FMA, PEAK_SMEM = 1, 2
 
 # Every entry point of include/mjp.h: name -> (restype, argtypes).
 _vp = ctypes.c_void_p
@@ -91,6 +92,7 @@ SIGNATURES = {
     "expv_batch_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64]),
     "jmjp_state_probs": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _i64p, _i64p, _i32p, _f64p, _vp]),
     "expv_batch_destroy": (None, [_vp]),
+    "mjp_measure_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _f64p, _vp]),
     "expv_series_static": (ctypes.c_int, [ctypes.c_int, _i64p, ctypes.c_int, _f64p, ctypes.c_int, _vp, _f64p,
                                           ctypes.c_int, _vp, _vp]),
     # include/mjp_surrogate.h

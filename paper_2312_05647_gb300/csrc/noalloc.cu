@@ -46,14 +46,19 @@ extern "C" int expv_series_static(int kind, const int64_t* dims, int ndims, cons
   if (ntimes < 1 || ntimes > kMaxTimes) return fail(MJP_ERR_ARG, "ntimes must be in [1, 256]");
   int64_t M, P, N;
   int want_theta;
-  if (kind == MJP_BD1D && ndims == 1 && dims[0] >= 1) {
+  // Each dimension is checked before any product, so N cannot wrap; the
+  // chain kernels index states in 32 bits.
+  constexpr int64_t kMaxN = ((int64_t)1 << 31) - 1;
+  if (kind == MJP_BD1D && ndims == 1 && dims[0] >= 1 && dims[0] <= kMaxN) {
     M = dims[0]; P = 1; N = M; want_theta = 2;
-  } else if (kind == MJP_TWOSTATE && ndims == 1 && dims[0] >= 2) {
+  } else if (kind == MJP_TWOSTATE && ndims == 1 && dims[0] >= 2 && dims[0] <= kMaxN / 2) {
     M = dims[0]; P = 2; N = 2 * M; want_theta = 4;
-  } else if (kind == MJP_MRNA_PROT2D && ndims == 2 && dims[0] >= 2 && dims[1] >= 1) {
+  } else if (kind == MJP_MRNA_PROT2D && ndims == 2 && dims[0] >= 2 && dims[1] >= 1 && dims[0] <= kMaxN &&
+             dims[1] <= kMaxN / dims[0]) {
     M = dims[0]; P = dims[1]; N = M * P; want_theta = 4;
   } else {
-    return fail(MJP_ERR_ARG, "kind/dims must describe a stencil model (BD1D, TWOSTATE or MRNA_PROT2D)");
+    return fail(MJP_ERR_ARG, "kind/dims must describe a stencil model (BD1D, TWOSTATE or MRNA_PROT2D) of at most "
+                             "2^31 - 1 states");
   }
   if (ntheta != want_theta) return fail(MJP_ERR_ARG, "wrong number of parameters for this kind");
   for (int q = 0; q < ntheta; ++q)
@@ -75,6 +80,15 @@ extern "C" int expv_series_static(int kind, const int64_t* dims, int ndims, cons
              "its static scratch holds %zu bytes",
              need, kStaticScratchBytes);
     return fail(MJP_ERR_ARG, msg);
+  }
+
+  // The call copies from stack memory and synchronises `stream`, neither of
+  // which a stream capture accepts: refuse to run while `stream` captures.
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MJP_CUDA(cudaStreamIsCapturing((cudaStream_t)stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(MJP_ERR_UNSUPPORTED, "expv_series_static cannot run while its stream is capturing a graph");
   }
 
   // One-time set-up per device, with that device current.
@@ -118,6 +132,10 @@ extern "C" int expv_series_static(int kind, const int64_t* dims, int ndims, cons
   int64_t t = (W >= 992 ? 992 : W * groups);
   t = (t + 31) / 32 * 32 + 32;
   const int threads = (int)(t < 64 ? 64 : (t > 1024 ? 1024 : t));
+  // The cluster must fit the GPU at all (the same check as expv_series).
+  const size_t smem = chain_stencil_smem(kind, MJP_FP32, 0, M, P, slab, ntimes, 0, 0);
+  if (chain_stencil_max_cluster_blocks(kind, MJP_FP32, 0, C, threads, smem) <= 0)
+    return fail(MJP_ERR_UNSUPPORTED, "stencil chain configuration cannot be made resident");
 
   // Times in ascending order with their caller rows (no heap: fixed arrays).
   double st[kMaxTimes];
