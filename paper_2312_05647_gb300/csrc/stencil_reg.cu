@@ -160,6 +160,19 @@ __device__ __forceinline__ void tmem_ld4(unsigned taddr, float2& a, float2& b) {
   a = make_float2(__uint_as_float(r0), __uint_as_float(r1));
   b = make_float2(__uint_as_float(r2), __uint_as_float(r3));
 }
+// Split form: issue the load of a row, wait for it later (one load in flight).
+struct Tmem4 {
+  unsigned r0, r1, r2, r3;
+};
+__device__ __forceinline__ void tmem_ld4_issue(unsigned taddr, Tmem4& v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.r0), "=r"(v.r1), "=r"(v.r2), "=r"(v.r3) : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_ld4_wait(Tmem4& v, float2& a, float2& b) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(v.r0), "+r"(v.r1), "+r"(v.r2), "+r"(v.r3) :: "memory");
+  a = make_float2(__uint_as_float(v.r0), __uint_as_float(v.r1));
+  b = make_float2(__uint_as_float(v.r2), __uint_as_float(v.r3));
+}
 __device__ __forceinline__ void tmem_st4(unsigned taddr, float2 a, float2 b) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
                "r"(__float_as_uint(a.x)), "r"(__float_as_uint(a.y)), "r"(__float_as_uint(b.x)),
@@ -488,6 +501,10 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
     const unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
     const int rtk = EDGE ? opaque(rtop) : -1;
     tmem_wait_st();  // the last jump's residual stores are complete
+    // The residuals of the next row in this jump's order are loaded while the
+    // current row is computed.
+    Tmem4 pre;
+    tmem_ld4_issue(tres + 4u * (DIR == 0 ? 0 : NR - 1), pre);
     // Row index as a float pair, stepped exactly (integers below 2^24).
     float2 fp;
     {
@@ -528,7 +545,8 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
       const float lin = (r & 1) ? lp.y : lp.x;
       const float rin = (r & 1) ? rp.y : rp.x;
       float2 rA, rB;  // residuals of row r
-      tmem_ld4(tres + 4u * r, rA, rB);
+      tmem_ld4_wait(pre, rA, rB);
+      if (i + 1 < NR) tmem_ld4_issue(tres + 4u * (DIR == 0 ? r + 1 : r - 1), pre);
       const float2 dA = v_fma(c_ngp, fp, d0A), dB = v_fma(c_ngp, fp, d0B);  // -e_{m,p}
       const float2 cup = v_fma(c_gp, fp, c_gp);  // gamma_p (p+1) from p+1
       // t = residual + inflows from the left, right, below and above + exit,
