@@ -26,10 +26,10 @@
 // this kernel): the registers of a 512-thread CTA hold the 40 values of a
 // block and the coefficients, not 40 residuals as well.  Each warp owns its
 // 32 TMEM lanes (the quadrant warp % 4 may address) and 4 columns per row of
-// its blocks; a row's four residuals are read with one tcgen05.ld before the
-// row's update and written back with one tcgen05.st after it.  The CTA holds
-// one 256-column allocation from start to end (at least 116 KB of dynamic
-// shared memory keep it alone on its SM, so the allocation never waits).
+// its blocks; a row's four residuals are read with one tcgen05.ld (issued
+// while the previous row is computed) and written back with one tcgen05.st.
+// The CTA holds one allocation from start to end, sized so that all CTAs the
+// register file admits on one SM fit its TMEM (no allocation ever waits).
 //
 // Every neighbour read and edge write uses a per-thread base plus a
 // compile-time offset (the edge arrays have fixed strides), and the jump
@@ -50,11 +50,19 @@ namespace mjp {
 namespace {
 
 constexpr int kQC = 4;            // columns per thread block of states
-// Threads per CTA at most: T = 512, one CTA per SM, <= 128 registers per thread.
-constexpr int kT = 512;
+// Threads per CTA at most, T = 512 (one CTA per SM) or 256 (two CTAs of
+// different instances per SM, so that one computes while the other waits at
+// its barrier); <= 128 registers per thread either way, so the register file
+// itself admits one (T = 512) or two (T = 256) CTAs per SM.
 constexpr int kMaxNQ = 512;       // column quads (M <= 2048)
-constexpr unsigned kTmemCols = 256;  // TMEM columns per CTA (4 warps per lane quadrant x 4 x 10 rows <= 160)
-constexpr size_t kMinSmem = 116 * 1024;  // one CTA per SM (its TMEM allocation never waits)
+// TMEM columns per CTA: T / 128 warps share each lane quadrant, 4 columns per
+// row of their blocks (<= 10 rows): 160 -> 256 columns at T = 512, 80 -> 128
+// at T = 256, so the CTAs an SM can hold never exceed its 512 columns and an
+// allocation never waits.
+template <int T>
+constexpr unsigned tmem_cols() {
+  return T == 512 ? 256u : 128u;
+}
 // Fixed strides of the edge arrays (per parity):
 //  - columns [2 sides][QR][T + 1] float2: the left (side 0) and right (side 1)
 //    column of block t, row pair r; entry T (kZero) is a zero slot;
@@ -198,8 +206,8 @@ __device__ int block_exclusive_scan(int v, int* wsum) {
   return off + x - v;
 }
 
-template <int kQR>
-__global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p, const int NQ, const int RS) {
+template <int kQR, int kT>
+__global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainParams p, const int NQ, const int RS) {
   using G = EdgeGeo<kQR, kT>;
   constexpr int kZero = G::kZero;
   constexpr int kRows = 2 * kQR;  // rows of a thread's block
@@ -260,7 +268,7 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
   // The planner caps K (MJP_OPT_K_CAP, default 2^26); the loop counts in 32 bits.
   const int Kmax = Kmax64 < (1LL << 30) ? (int)Kmax64 : 0;
   if (Kmax64 >= (1LL << 30) && tid == 0 && rank == 0) set_status(p.status, kStatusKcap);
-  if (warp == 0) tmem_alloc(&tmem_base, kTmemCols);
+  if (warp == 0) tmem_alloc(&tmem_base, tmem_cols<kT>());
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
@@ -709,7 +717,7 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
   if (C > 1) cluster.sync();
   else __syncthreads();
   tmem_fence_after();
-  if (warp == 0) tmem_dealloc(tmem_base, kTmemCols);
+  if (warp == 0) tmem_dealloc(tmem_base, tmem_cols<kT>());
 }
 
 }  // namespace
@@ -718,11 +726,14 @@ __global__ void __launch_bounds__(kT, 1) chain_reg2d_kernel(const ChainParams p,
 // box does not fit this kernel (then the shared-memory kernel runs).
 bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluster, int threads, RegPlan* out) {
   if (M < 1 || P < 1 || ntimes < 1) return false;
-  if (threads != 0) return false;  // the launch shape is this kernel's own
+  if (threads != 0 && threads != 256) return false;
   const int NQ = (int)((M + kQC - 1) / kQC);
   if (NQ > kMaxNQ) return false;
   // Fewest CTAs per instance first; for each, 8 rows per thread before 10.
-  const size_t smem_cap = 227 * 1024;
+  // threads = 256 asks for two CTAs per SM (then the edge arrays are half as
+  // large and a CTA must fit half the shared memory).
+  const int T = threads == 256 ? 256 : 512;
+  const size_t smem_cap = T == 256 ? 113 * 1024 : 227 * 1024;
   for (int C = 1; C <= max_cluster; ++C)
     for (int QR = 4; QR <= 5; ++QR) {
       const int rows_blk = 2 * QR;
@@ -730,27 +741,29 @@ bool chain_reg2d_plan(int64_t M, int64_t P, int ntimes, int nmem, int max_cluste
       const int RS = (int)((rows + rows_blk - 1) / rows_blk) * rows_blk;
       if ((int64_t)(C - 1) * RS >= P) continue;  // the last CTA would be empty
       const int Tc = NQ * (RS / rows_blk);
-      if (Tc > kT) continue;
-      const size_t edge = 2 * (QR == 5 ? EdgeGeo<5, kT>::par_bytes : EdgeGeo<4, kT>::par_bytes);
+      if (Tc > T) continue;
+      size_t edge;
+      if (T == 256) edge = 2 * (QR == 5 ? EdgeGeo<5, 256>::par_bytes : EdgeGeo<4, 256>::par_bytes);
+      else edge = 2 * (QR == 5 ? EdgeGeo<5, 512>::par_bytes : EdgeGeo<4, 512>::par_bytes);
       const RegLayout L = reg_layout(edge, ntimes, nmem);
       if (L.total + 1024 > smem_cap) continue;  // leave room for static shared memory
       out->cluster = C;
       out->rows = RS;
       out->nq = NQ;
       out->qr = QR;
-      out->tmax = kT;
+      out->tmax = T;
       out->threads = ((Tc + 31) / 32) * 32;
-      out->smem = std::max(L.total, kMinSmem);
+      out->smem = L.total;
       return true;
     }
   return false;
 }
 
-template <int QR>
+template <int QR, int T>
 cudaError_t launch_reg(const ChainParams& p, const RegPlan& rp, cudaStream_t s) {
   static int smem_set = 0;
   static bool nonportable = false;
-  auto kern = chain_reg2d_kernel<QR>;
+  auto kern = chain_reg2d_kernel<QR, T>;
   cudaError_t e;
   if ((int)rp.smem > smem_set) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rp.smem);
@@ -779,7 +792,8 @@ cudaError_t launch_reg(const ChainParams& p, const RegPlan& rp, cudaStream_t s) 
 
 cudaError_t launch_chain_reg2d(const ChainParams& p, const RegPlan& rp, cudaStream_t s) {
   if (p.B <= 0) return cudaSuccess;
-  return rp.qr == 5 ? launch_reg<5>(p, rp, s) : launch_reg<4>(p, rp, s);
+  if (rp.tmax == 256) return rp.qr == 5 ? launch_reg<5, 256>(p, rp, s) : launch_reg<4, 256>(p, rp, s);
+  return rp.qr == 5 ? launch_reg<5, 512>(p, rp, s) : launch_reg<4, 512>(p, rp, s);
 }
 
 }  // namespace mjp

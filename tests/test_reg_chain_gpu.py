@@ -60,16 +60,26 @@ def test_register_chain_is_bitwise_equal_to_shared_memory_chain(dims, theta):
     np.testing.assert_array_equal(a, b)
 
 
-def test_register_chain_refuses_forced_thread_counts():
-    # The register-resident chain has one launch shape (384-thread CTAs);
-    # OPT_CHAIN = 2 with a forced thread count is refused.
+@pytest.mark.parametrize("dims,theta", [((200, 200), (20.0, 1.0, 5.0, 0.1)), ((136, 401), (12.0, 1.0, 2.0, 0.15))])
+def test_register_chain_two_ctas_per_sm_variant_is_bitwise_equal(dims, theta):
+    # OPT_THREADS = 256 selects 256-thread CTAs (two per SM, more CTAs per cluster).
+    times = np.array([0.05, 0.2, 0.6])
+    obs, rho0 = _case(dims, theta, times, 30, seed=sum(dims) + 1)
+    thetas = synth.jitter(theta, 2, 0.2, synth.rng(2, 17))
+    a = _loglik(dims, theta, thetas, times, obs, rho0, 1)
+    b = _loglik(dims, theta, thetas, times, obs, rho0, 2, threads=256)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_register_chain_refuses_other_thread_counts():
+    # The register-resident chain runs 512- or 256-thread CTAs only.
     import paper_2312_05647_gb300 as mjp
     from paper_2312_05647_gb300.capi import MJPError
     dims, theta = (37, 53), (10.0, 1.0, 1.5, 0.4)
     times = np.array([0.05, 0.2])
     obs, rho0 = _case(dims, theta, times, 10, seed=5)
     with pytest.raises(MJPError):
-        _loglik(dims, theta, np.array([theta]), times, obs, rho0, 2, threads=256)
+        _loglik(dims, theta, np.array([theta]), times, obs, rho0, 2, threads=128)
 
 
 @pytest.mark.parametrize("dims,theta", [((37, 53), (10.0, 1.0, 1.5, 0.4)), ((200, 200), (20.0, 1.0, 5.0, 0.1))])
