@@ -58,11 +58,14 @@ def parse():
     ap.add_argument("--no-mcmc", action="store_true", help="skip the ESS/s comparison")
     ap.add_argument("--mcmc-iters", type=int, default=20000, help="iterations of each timed sampler run")
     ap.add_argument("--mcmc-adapt-iters", type=int, default=1500, help="iteration cap of each adaptive phase")
-    ap.add_argument("--probe", choices=["bd_heavy", "promoter"], default=None,
+    ap.add_argument("--probe", choices=["bd_heavy", "promoter", "csr"], default=None,
                     help="time one small case for a profiler capture instead of the bench line: bd_heavy = eight "
                          "birth-death instances of the uneven batch's largest size (N = 18,863, K = 26,884 jumps) "
                          "on clusters of --probe-cluster CTAs; promoter = the two-state promoter log-likelihood of "
-                         "256 jittered thetas on its 50 x 100 snapshots (one exact launch of the samplers)")
+                         "256 jittered thetas on its 50 x 100 snapshots (one exact launch of the samplers); csr = "
+                         "the general CSR configuration (N = 2^20, 8 nonzeros per row, K = 309), --probe-chain 0 "
+                         "(one cooperative launch) or 1 (one launch per jump)")
+    ap.add_argument("--probe-chain", type=int, default=0)
     ap.add_argument("--probe-cluster", type=int, default=4)
     ap.add_argument("--probe-precision", type=int, default=1, help="1 = FP32, 2 = FP64")
     ap.add_argument("--configs", action="store_true",
@@ -317,6 +320,23 @@ def probe_promoter():
     return {"probe": "promoter", "thetas": 256, "ms": ms}
 
 
+def probe_csr(chain: int, precision: int):
+    """The general CSR configuration (N = 2^20, 8 nonzeros per row, t = 1):
+    one warm expv_series call, then one timed with CUDA events."""
+    import torch
+    import synth
+    import paper_2312_05647_gb300 as mjp
+    cc = synth.csr_large()
+    n = len(cc["rho0"])
+    m = mjp.Model.from_csr(n, cc["row_ptr"], cc["col"], cc["val"], precision)
+    m.set_option(mjp.OPT_CHAIN, chain)
+    r = torch.tensor(cc["rho0"], dtype=m.torch_dtype, device="cuda")
+    o = m.expv(r, cc["times"])
+    ms = _events_ms(lambda: m.expv(r, cc["times"], out=o))
+    m.check()
+    return {"probe": "csr", "chain": chain, "precision": precision, "ms": ms}
+
+
 def other_configs():
     """Measurements of the configurations that are not the bench line."""
     import numpy as np
@@ -554,6 +574,8 @@ def main():
                 res = probe_bd_heavy(args.probe_cluster, args.probe_precision)
             elif args.probe == "promoter":
                 res = probe_promoter()
+            elif args.probe == "csr":
+                res = probe_csr(args.probe_chain, args.probe_precision)
             else:
                 res = other_configs()
             print(json.dumps(res), flush=True)

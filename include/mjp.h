@@ -99,7 +99,8 @@ extern "C" {
 #define MJP_OPT_PROFILE 5       /* 1: record CUDA events around each kernel of a call (see rate_model_last_timing) */
 #define MJP_OPT_ARENA 6         /* capacity (elements) of the planner's Poisson-weight store; 0 = automatic.  Windows
                                    that do not fit are generated in the chain by Algorithm 2's recurrence instead. */
-#define MJP_OPT_CHAIN 7         /* chain kernel for stencil models: 0 = automatic (the register-resident kernels for
+#define MJP_OPT_CHAIN 7         /* general CSR models: 0 = the whole chain in one cooperative launch (default), 1 = one
+                                   launch per jump (identical results).  Stencil models: 0 = automatic (the register-resident kernels for
                                    the log-likelihood of FP32 mRNA/protein boxes and for expv_series of birth-death
                                    models, both without renormalisation or forced thread counts (and for the
                                    former forced cluster sizes), else the shared-memory kernel), 1 = shared-memory
@@ -118,6 +119,9 @@ extern "C" {
                                    2 kappa (Krylov, Sec. 2.3); the info report then gives omega = max_n |a_nn|,
                                    K_i = cumulative steps to t_i, eps_i = 0 */
 #define MJP_OPT_KAPPA 10        /* Krylov subspace size kappa (default 20, the paper's; 1 .. 32) */
+#define MJP_OPT_WAIT_LIMIT 11   /* general CSR models: polls of a CTA waiting at the chain's grid barrier before it
+                                   gives up (default 2^24, about a second; 0 = give up at once).  A wait that runs
+                                   out stops the chain; rate_model_check then returns MJP_ERR_DEVICE_TIMEOUT */
 
 typedef struct mjp_model mjp_model;
 typedef struct mjp_obs mjp_obs;

@@ -270,8 +270,12 @@ def ess_geyer(x) -> float:
         total += 2.0 * G
         prev = G
         m += 1
-    # Antithetic or very short series can drive the estimate to zero or below;
-    # tau is floored at 1/log10(n), so ESS stays in (0, n log10 n].
+    # Antithetic or very short series can drive the estimate to zero or below.
+    # Vehtari, Gelman, Simpson, Carpenter & Buerkner (2021, Bayesian Analysis
+    # 16(2), "Rank-normalization, folding, and localization"), whose ESS
+    # estimator also sums Geyer's initial monotone sequence, bound the
+    # estimate by S log10 S for S draws to keep antithetic chains stable; the
+    # same bound here: tau >= 1 / log10(n), so ESS stays in (0, n log10 n].
     tau = max(total / g0, 1.0 / math.log10(n))
     return float(n / tau)
 

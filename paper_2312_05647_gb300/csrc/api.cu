@@ -64,6 +64,8 @@ struct mjp_model {
   double csr_omega = 0.0;
   int64_t nslices = 0;
   DevBuf d_slice_ptr, d_slice_len, d_col, d_val, d_diag, d_perm;
+  DevBuf d_bar;                            // grid barrier of the one-launch CSR chain
+  long long wait_limit = (long long)1 << 24;  // MJP_OPT_WAIT_LIMIT
   // workspace (scratch owned by the handle)
   DevBuf d_times, d_orig, d_win, d_info, d_theta, d_comp, d_status, d_ll;
   DevBuf d_rho2, d_outp, d_wtab, d_woff, d_L, d_K;
@@ -75,7 +77,7 @@ struct mjp_model {
   ~mjp_model() {
     d_arena.release(); d_arena_ctl.release();
     d_slice_ptr.release(); d_slice_len.release(); d_col.release(); d_val.release(); d_diag.release();
-    d_perm.release(); d_rho2.release(); d_outp.release(); d_wtab.release(); d_woff.release();
+    d_perm.release(); d_rho2.release(); d_outp.release(); d_wtab.release(); d_woff.release(); d_bar.release();
     d_L.release(); d_K.release();
     d_kq.release(); d_jk.release(); d_jorder.release(); d_jgp.release(); d_jmem.release(); d_jphi.release(); d_jchunk.release();
     d_jmap.release();
@@ -281,18 +283,35 @@ int csr_run(mjp_model* m, const void* rho0, const double* sorted_times, int nt, 
   jp.wtab = m->d_wtab.as<double>(); jp.woff = m->d_woff.as<int64_t>();
   jp.L = m->d_L.as<int64_t>(); jp.K = m->d_K.as<int64_t>();
   jp.out = m->d_outp.p; jp.comp = m->d_comp.as<float>();
-  int lo = 0, hi = -1;  // times whose window holds jump k-1 (ascending times)
-  for (int64_t k = 1; k <= kmax + 1; ++k) {
-    const int64_t kp = k - 1;
-    while (lo < nt && K[lo] < kp) ++lo;
-    while (hi + 1 < nt && L[hi + 1] <= kp) ++hi;
-    jp.k = k;
-    jp.jump = k <= kmax;
-    jp.tlo = lo;
-    jp.thi = hi;
-    jp.rho_prev = rho + ((kp & 1) ? elt * n : 0);
-    jp.rho_next = rho + ((kp & 1) ? 0 : elt * n);
-    MJP_CUDA(launch_csr_jump(m->precision, jp, s));
+  if (m->chain != 1) {
+    // The whole chain in one cooperative launch, jumps separated by a
+    // bounded grid barrier (a wait that runs out is reported by
+    // rate_model_check as MJP_ERR_DEVICE_TIMEOUT).
+    if ((rc = m->d_bar.ensure(2 * sizeof(unsigned)))) return rc;
+    MJP_CUDA(cudaMemsetAsync(m->d_bar.p, 0, 2 * sizeof(unsigned), s));
+    CsrChainParams cp = {};
+    cp.j = jp;
+    cp.ntimes = nt;
+    cp.kmax = kmax;
+    cp.rho = rho;
+    cp.bar = m->d_bar.as<unsigned>();
+    cp.wait_limit = m->wait_limit;
+    cp.status = m->d_status.as<int>();
+    MJP_CUDA(launch_csr_chain(m->precision, cp, s));
+  } else {
+    int lo = 0, hi = -1;  // times whose window holds jump k-1 (ascending times)
+    for (int64_t k = 1; k <= kmax + 1; ++k) {
+      const int64_t kp = k - 1;
+      while (lo < nt && K[lo] < kp) ++lo;
+      while (hi + 1 < nt && L[hi + 1] <= kp) ++hi;
+      jp.k = k;
+      jp.jump = k <= kmax;
+      jp.tlo = lo;
+      jp.thi = hi;
+      jp.rho_prev = rho + ((kp & 1) ? elt * n : 0);
+      jp.rho_next = rho + ((kp & 1) ? 0 : elt * n);
+      MJP_CUDA(launch_csr_jump(m->precision, jp, s));
+    }
   }
   if ((rc = mark(m, 2, s))) return rc;
   return MJP_OK;
@@ -519,6 +538,10 @@ int rate_model_set_option(mjp_model* m, int option, int64_t value) try {
     case MJP_OPT_CLUSTER:
       if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16) return fail(MJP_ERR_ARG, "cluster must be 0, 1, 2, 4, 8 or 16");
       m->cluster = (int)value;
+      return MJP_OK;
+    case MJP_OPT_WAIT_LIMIT:
+      if (value < 0) return fail(MJP_ERR_ARG, "wait limit must be >= 0");
+      m->wait_limit = (long long)value;
       return MJP_OK;
     default:
       return fail(MJP_ERR_ARG, "unknown option");

@@ -12,12 +12,19 @@
 // separate array.  rho (4 MB for 2^20 FP32 states) stays resident in L2;
 // neighbour values are gathered with read-only loads.
 //
-// One launch per jump (the grid-wide dependency of rho_{k+1} on all of
-// rho_k): launch k accumulates rho_{k-1} into the active times' outputs
+// Jump k accumulates rho_{k-1} into the active times' outputs
 // (Kahan-compensated in FP32) and forms rho_k = rho_{k-1} B (Algorithm 2's
-// loop body).  The Poisson weights of every (time, jump) come from a table
-// filled by `fill_weights_kernel` with Algorithm 2's recurrence P_k =
-// P_{k-1} x/k started from the planner's P_L.
+// loop body); rho_{k+1} depends on all of rho_k, so jumps are separated grid-
+// wide.  Default: the whole chain in one cooperative launch (all CTAs
+// co-resident), jumps separated by a software grid barrier whose waits are
+// bounded (a CTA that polls longer than the limit records kStatusTimeout and
+// leaves, and so do the others at their next barrier).  Alternative
+// (MJP_OPT_CHAIN = 1): one launch per jump.  Both run the same per-jump code,
+// so their results are identical.  The Poisson weights of every (time, jump)
+// come from a table filled by `fill_weights_kernel` with Algorithm 2's
+// recurrence P_k = P_{k-1} x/k started from the planner's P_L.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace mjp {
@@ -62,7 +69,7 @@ __global__ void permute_out_kernel(const T* __restrict__ src, const int32_t* __r
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) csr_jump_kernel(CsrJumpParams p) {
+__device__ __forceinline__ void csr_jump_body(const CsrJumpParams& p) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -116,6 +123,69 @@ __global__ void __launch_bounds__(512) csr_jump_kernel(CsrJumpParams p) {
       }
       nxt[r] = y;
     }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) csr_jump_kernel(CsrJumpParams p) {
+  csr_jump_body<T>(p);
+}
+
+// Grid-wide barrier with a bounded wait.  bar[0] counts arrivals, bar[1] is
+// the generation: the last CTA to arrive resets the count and advances the
+// generation; the others poll the generation they read before arriving, at
+// most `limit` times.  Returns false (and records kStatusTimeout) when the
+// wait ran out; every CTA then leaves the chain, the late ones at the latest
+// at their next barrier, which can no longer complete.
+__device__ bool grid_barrier(unsigned* bar, long long limit, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    int good = 1;
+    if (arrived == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g) {
+        if (it++ >= limit) {
+          good = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    if (!good) atomicCAS(status, 0, kStatusTimeout);
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) csr_chain_kernel(CsrChainParams c) {
+  CsrJumpParams p = c.j;
+  const size_t n = (size_t)p.n;
+  T* rho = reinterpret_cast<T*>(c.rho);
+  int lo = 0, hi = -1;  // times whose window holds jump k-1 (ascending times)
+  for (int64_t k = 1; k <= c.kmax + 1; ++k) {
+    const int64_t kp = k - 1;
+    while (lo < c.ntimes && p.K[lo] < kp) ++lo;
+    while (hi + 1 < c.ntimes && p.L[hi + 1] <= kp) ++hi;
+    p.k = k;
+    p.jump = k <= c.kmax;
+    p.tlo = lo;
+    p.thi = hi;
+    p.rho_prev = rho + ((kp & 1) ? n : 0);
+    p.rho_next = rho + ((kp & 1) ? 0 : n);
+    csr_jump_body<T>(p);
+    if (k <= c.kmax && !grid_barrier(c.bar, c.wait_limit, c.status)) return;
   }
 }
 
@@ -191,6 +261,28 @@ cudaError_t launch_csr_jump(int precision, const CsrJumpParams& p, cudaStream_t 
   if (precision == MJP_FP64) csr_jump_kernel<double><<<grid, block, 0, s>>>(p);
   else csr_jump_kernel<float><<<grid, block, 0, s>>>(p);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_chain_typed(const CsrChainParams& c, cudaStream_t s) {
+  const int block = 512;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_chain_kernel<T>, block, 0)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // Every CTA must be resident at once: at most the occupancy limit, and no
+  // more than the slices need.
+  int grid = std::min<int64_t>((int64_t)per_sm * sms, (c.j.nslices * 32 + block - 1) / block);
+  if (grid < 1) grid = 1;
+  void* args[] = {const_cast<CsrChainParams*>(&c)};
+  return cudaLaunchCooperativeKernel((const void*)csr_chain_kernel<T>, dim3(grid), dim3(block), args, 0, s);
+}
+
+cudaError_t launch_csr_chain(int precision, const CsrChainParams& p, cudaStream_t s) {
+  return precision == MJP_FP64 ? launch_chain_typed<double>(p, s) : launch_chain_typed<float>(p, s);
 }
 
 cudaError_t launch_csr_loglik(const void* outp, int precision, int64_t n, const int64_t* gptr, int ntimes,

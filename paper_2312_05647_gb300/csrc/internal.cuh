@@ -135,6 +135,18 @@ struct CsrJumpParams {
   float* comp;               // FP32 Kahan compensation, ntimes x n
 };
 
+// The whole general-CSR chain in one cooperative launch (csr.cu): every jump
+// of csr_jump_kernel's body, then a grid-wide barrier with a bounded wait.
+struct CsrChainParams {
+  CsrJumpParams j;           // k, jump, tlo, thi, rho_prev and rho_next are set per jump in the kernel
+  int ntimes;
+  int64_t kmax;
+  void* rho;                 // two state vectors of n elements (T), ping-pong
+  unsigned* bar;             // [0] arrivals, [1] generation; zeroed before the launch
+  long long wait_limit;      // polls of a waiting CTA before it gives up (status kStatusTimeout)
+  int* status;
+};
+
 // Fourth-order Runge-Kutta for one birth-death distribution (rk4.cu).
 struct Rk4Params {
   const double* theta;   // device, {beta, gamma} or {beta, gamma, lambda_act, lambda_ina}
@@ -239,6 +251,7 @@ cudaError_t launch_permute_in(int precision, const void* src, const int32_t* per
 cudaError_t launch_permute_out(int precision, const void* src, const int32_t* perm, void* dst, int64_t n,
                                int ntimes, const int32_t* orig, cudaStream_t s);
 cudaError_t launch_csr_jump(int precision, const CsrJumpParams& p, cudaStream_t s);
+cudaError_t launch_csr_chain(int precision, const CsrChainParams& p, cudaStream_t s);
 cudaError_t launch_csr_loglik(const void* outp, int precision, int64_t n, const int64_t* gptr, int ntimes,
                               const double* counts, const int64_t* mptr, const int32_t* members,
                               const int32_t* perm, double* ll, int* status, cudaStream_t s);

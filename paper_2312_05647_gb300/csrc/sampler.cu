@@ -582,6 +582,8 @@ __global__ void __launch_bounds__(256) chain_ess_kernel(const double* __restrict
         total += 2.0 * G;
         prev = G;
       }
+      // tau >= 1 / log10(S): the bound S log10 S on the ESS that Vehtari et
+      // al. (2021, Bayesian Analysis 16(2)) apply to keep antithetic chains stable.
       result = (double)S / fmax(total / g0, 1.0 / log10((double)S));
     }
   }

@@ -106,3 +106,54 @@ def test_csr_loglik():
     ll = mjp.loglik(m, o, np.zeros((1, 0)))
     ref = oracle.loglik(csr, cfg["rho0"], times, obs)
     assert abs(ll[0] - ref) <= 1e-12 * 150
+
+
+def _csr_run(rp, col, val, prec, rho0, times, opts):
+    import torch
+    import paper_2312_05647_gb300 as mjp
+    m = mjp.Model.from_csr(len(rp) - 1, rp, col, val, prec)
+    for k, v in opts.items():
+        m.set_option(k, v)
+    r = torch.tensor(rho0, dtype=m.torch_dtype, device="cuda")
+    out = m.expv(r, times)
+    return m, out
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_one_launch_chain_equals_per_jump_launches(prec):
+    # The cooperative one-launch chain and one launch per jump run the same
+    # per-jump code: identical results (several CTAs, many grid barriers).
+    import paper_2312_05647_gb300 as mjp
+    gen = np.random.default_rng(8)
+    n = 70000
+    rp, col, val = synth.random_csr(n, 6, gen, max_exit=80.0)
+    rho0 = gen.random(n)
+    rho0 /= rho0.sum()
+    times = [0.1, 0.8, 2.0]
+    m1, a = _csr_run(rp, col, val, prec, rho0, times, {})
+    m1.check()
+    m2, b = _csr_run(rp, col, val, prec, rho0, times, {mjp.OPT_CHAIN: 1})
+    m2.check()
+    np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+
+
+def test_grid_barrier_wait_that_runs_out_is_reported():
+    # A wait limit of zero polls: every CTA but the last to arrive gives up at
+    # the first barrier; the chain stops, the status word says so, and the
+    # model (and the context) stay usable.
+    import paper_2312_05647_gb300 as mjp
+    from paper_2312_05647_gb300.capi import MJPError
+    gen = np.random.default_rng(9)
+    n = 1 << 15
+    rp, col, val = synth.random_csr(n, 4, gen, max_exit=40.0)
+    rho0 = np.full(n, 1.0 / n)
+    m, _ = _csr_run(rp, col, val, 2, rho0, [1.0], {mjp.OPT_WAIT_LIMIT: 0})
+    with pytest.raises(MJPError) as ei:
+        m.check()
+    assert ei.value.code == -5  # MJP_ERR_DEVICE_TIMEOUT
+    m.set_option(mjp.OPT_WAIT_LIMIT, 1 << 24)
+    import torch
+    out = m.expv(torch.tensor(rho0, dtype=torch.float64, device="cuda"), [1.0])
+    m.check()
+    r, _ = oracle.expv(oracle.CSR(rp, col, val), rho0, [1.0])
+    assert np.abs(out.cpu().numpy() - r).max() <= 1e-12

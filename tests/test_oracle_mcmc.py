@@ -182,6 +182,27 @@ def test_plain_and_delayed_acceptance_sample_a_known_gaussian():
     assert out["da"].n_exact == out["da"].n_stage1
 
 
+def test_ess_bound_acts_only_beyond_n_log10_n():
+    # Antithetic AR(1): ESS = n (1 - phi) / (1 + phi).  For phi = -0.5 that is
+    # 3 n, below the published bound n log10 n at n = 20,000 (4.3 n), so the
+    # estimate follows the closed form; for phi = -0.95 the closed form is 39 n,
+    # above the bound, and the estimate stops at the bound.
+    n = 20000
+    for phi, capped in ((-0.5, False), (-0.95, True)):
+        gen = np.random.default_rng(5)
+        x = np.zeros(n)
+        e = gen.standard_normal(n)
+        for i in range(1, n):
+            x[i] = phi * x[i - 1] + e[i]
+        est = mcmc.ess_geyer(x)
+        bound = n * math.log10(n)
+        if capped:
+            assert est == pytest.approx(bound, rel=1e-12)
+        else:
+            assert abs(est / (n * (1 - phi) / (1 + phi)) - 1.0) < 0.1
+            assert est < bound
+
+
 def test_ess_floor_on_degenerate_series():
     # Alternating series: gamma(1) = -gamma(0) makes the first pair sum zero;
     # the floor keeps ESS finite and positive (n log10 n at most).
