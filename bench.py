@@ -64,7 +64,7 @@ def parse():
                          "on clusters of --probe-cluster CTAs; promoter = the two-state promoter log-likelihood of "
                          "256 jittered thetas on its 50 x 100 snapshots (one exact launch of the samplers); csr = "
                          "the general CSR configuration (N = 2^20, 8 nonzeros per row, K = 309), --probe-chain 0 "
-                         "(one cooperative launch) or 1 (one launch per jump)")
+                         "(one launch per jump) or 2 (one cooperative launch)")
     ap.add_argument("--probe-chain", type=int, default=0)
     ap.add_argument("--probe-cluster", type=int, default=4)
     ap.add_argument("--probe-precision", type=int, default=1, help="1 = FP32, 2 = FP64")
@@ -493,7 +493,11 @@ def other_configs():
         # read, rho written); the window's accumulation is counted separately.
         per_jump = nnz * (vb + 4 + vb) + n * 3 * vb
         res["csr_2p20"][name] = {"ms": ms, "K": Kc, "bytes_per_jump": per_jump,
-                                 "achieved_gbs": per_jump * Kc / (ms / 1e3) / 1e9}
+                                 "achieved_gbs": per_jump * Kc / (ms / 1e3) / 1e9,
+                                 "gathers_per_s_G": nnz * Kc / (ms / 1e3) / 1e9}
+    # The gathers of rho are random 4-byte reads of an L2-resident vector:
+    # their measured peak rate is the roofline of the CSR chain.
+    res["csr_2p20"]["l2_gather_peak_G_per_s"] = mjp.measure_peak(mjp.PEAK_L2_GATHER, 2000)
     return res
 
 

@@ -99,8 +99,9 @@ extern "C" {
 #define MJP_OPT_PROFILE 5       /* 1: record CUDA events around each kernel of a call (see rate_model_last_timing) */
 #define MJP_OPT_ARENA 6         /* capacity (elements) of the planner's Poisson-weight store; 0 = automatic.  Windows
                                    that do not fit are generated in the chain by Algorithm 2's recurrence instead. */
-#define MJP_OPT_CHAIN 7         /* general CSR models: 0 = the whole chain in one cooperative launch (default), 1 = one
-                                   launch per jump (identical results).  Stencil models: 0 = automatic (the register-resident kernels for
+#define MJP_OPT_CHAIN 7         /* general CSR models: 0 or 1 = one launch per jump (default), 2 = the whole chain in
+                                   one cooperative launch with a bounded grid barrier per jump (identical results;
+                                   see MJP_OPT_WAIT_LIMIT).  Stencil models: 0 = automatic (the register-resident kernels for
                                    the log-likelihood of FP32 mRNA/protein boxes and for expv_series of birth-death
                                    models, both without renormalisation or forced thread counts (and for the
                                    former forced cluster sizes), else the shared-memory kernel), 1 = shared-memory
@@ -119,7 +120,7 @@ extern "C" {
                                    2 kappa (Krylov, Sec. 2.3); the info report then gives omega = max_n |a_nn|,
                                    K_i = cumulative steps to t_i, eps_i = 0 */
 #define MJP_OPT_KAPPA 10        /* Krylov subspace size kappa (default 20, the paper's; 1 .. 32) */
-#define MJP_OPT_WAIT_LIMIT 11   /* general CSR models: polls of a CTA waiting at the chain's grid barrier before it
+#define MJP_OPT_WAIT_LIMIT 11   /* general CSR models, MJP_OPT_CHAIN = 2: polls of a CTA waiting at the grid barrier before it
                                    gives up (default 2^24, about a second; 0 = give up at once).  A wait that runs
                                    out stops the chain; rate_model_check then returns MJP_ERR_DEVICE_TIMEOUT */
 
@@ -343,6 +344,7 @@ int expv_series_static(int kind, const int64_t* dims, int ndims, const double* t
  */
 #define MJP_PEAK_FP32_FMA 1
 #define MJP_PEAK_SMEM 2
+#define MJP_PEAK_L2_GATHER 3 /* 4-byte loads at random positions of an L2-resident 4 MB array, in G loads/s */
 int mjp_measure_peak(int which, int iters, double* result, void* stream);
 
 /*

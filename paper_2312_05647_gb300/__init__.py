@@ -14,7 +14,7 @@ import numpy as np
 
 from . import capi
 from .capi import (AUTOREG, BD1D, CSR, FP32, FP64, METHOD_KRYLOV, METHOD_RK4, METHOD_RMJP, MRNA_PROT2D, OPT_ARENA,
-                   OPT_CHAIN, OPT_CLUSTER, OPT_HALO, OPT_K_CAP, OPT_KAPPA, OPT_METHOD, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_RENORM_PERIOD, OPT_THREADS, PEAK_FP32_FMA, PEAK_SMEM, PTR_DEVICE, PTR_HOST, TRUNC_PAPER, TRUNC_TOL, TWOSTATE,
+                   OPT_CHAIN, OPT_CLUSTER, OPT_HALO, OPT_K_CAP, OPT_KAPPA, OPT_METHOD, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_RENORM_PERIOD, OPT_THREADS, PEAK_FP32_FMA, PEAK_L2_GATHER, PEAK_SMEM, PTR_DEVICE, PTR_HOST, TRUNC_PAPER, TRUNC_TOL, TWOSTATE,
                    MJPError)
 
 __all__ = ["Model", "Obs", "Batch", "loglik", "BD1D", "TWOSTATE", "MRNA_PROT2D", "AUTOREG", "CSR", "FP32", "FP64",

@@ -24,7 +24,7 @@ PTR_HOST, PTR_DEVICE = 0, 1
 OPT_RENORM_PERIOD, OPT_K_CAP, OPT_THREADS, OPT_CLUSTER, OPT_PROFILE, OPT_ARENA, OPT_CHAIN, OPT_HALO = 1, 2, 3, 4, 5, 6, 7, 8
 OPT_METHOD, OPT_KAPPA, OPT_WAIT_LIMIT = 9, 10, 11
 METHOD_RMJP, METHOD_RK4, METHOD_KRYLOV = 0, 1, 2
-PEAK_FP32_FMA, PEAK_SMEM = 1, 2
+PEAK_FP32_FMA, PEAK_SMEM, PEAK_L2_GATHER = 1, 2, 3
 
 # Every entry point of include/mjp.h: name -> (restype, argtypes).
 _vp = ctypes.c_void_p

@@ -283,10 +283,12 @@ int csr_run(mjp_model* m, const void* rho0, const double* sorted_times, int nt, 
   jp.wtab = m->d_wtab.as<double>(); jp.woff = m->d_woff.as<int64_t>();
   jp.L = m->d_L.as<int64_t>(); jp.K = m->d_K.as<int64_t>();
   jp.out = m->d_outp.p; jp.comp = m->d_comp.as<float>();
-  if (m->chain != 1) {
+  if (m->chain == 2) {
     // The whole chain in one cooperative launch, jumps separated by a
     // bounded grid barrier (a wait that runs out is reported by
-    // rate_model_check as MJP_ERR_DEVICE_TIMEOUT).
+    // rate_model_check as MJP_ERR_DEVICE_TIMEOUT).  Measured slower than
+    // one launch per jump at N = 2^20 (12.6 against 11.4 ms for 309 jumps,
+    // FP32): the barrier costs more than the gap between launches.
     if ((rc = m->d_bar.ensure(2 * sizeof(unsigned)))) return rc;
     MJP_CUDA(cudaMemsetAsync(m->d_bar.p, 0, 2 * sizeof(unsigned), s));
     CsrChainParams cp = {};

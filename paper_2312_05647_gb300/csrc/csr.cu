@@ -15,12 +15,12 @@
 // Jump k accumulates rho_{k-1} into the active times' outputs
 // (Kahan-compensated in FP32) and forms rho_k = rho_{k-1} B (Algorithm 2's
 // loop body); rho_{k+1} depends on all of rho_k, so jumps are separated grid-
-// wide.  Default: the whole chain in one cooperative launch (all CTAs
-// co-resident), jumps separated by a software grid barrier whose waits are
-// bounded (a CTA that polls longer than the limit records kStatusTimeout and
-// leaves, and so do the others at their next barrier).  Alternative
-// (MJP_OPT_CHAIN = 1): one launch per jump.  Both run the same per-jump code,
-// so their results are identical.  The Poisson weights of every (time, jump)
+// wide.  Default: one launch per jump.  Alternative (MJP_OPT_CHAIN = 2): the
+// whole chain in one cooperative launch (all CTAs co-resident), jumps
+// separated by a software grid barrier whose waits are bounded (a CTA that
+// polls longer than the limit records kStatusTimeout and leaves, and so do
+// the others at their next barrier).  Both run the same per-jump code, so
+// their results are identical.  The Poisson weights of every (time, jump)
 // come from a table filled by `fill_weights_kernel` with Algorithm 2's
 // recurrence P_k = P_{k-1} x/k started from the planner's P_L.
 #include <algorithm>
@@ -116,7 +116,22 @@ __device__ __forceinline__ void csr_jump_body(const CsrJumpParams& p) {
       T y = mul_t(diag[r], v);
       const int64_t base = p.slice_ptr[s] + lane;
       const int width = p.slice_len[s];
-      for (int j = 0; j < width; ++j) {
+      // Entries four at a time: the index and value loads of the group, then
+      // its four gathers, so each lane has several independent loads in flight
+      // (the same multiply-adds in the same order as one at a time).
+      int j = 0;
+      for (; j + 4 <= width; j += 4) {
+        const int64_t e = base + (int64_t)j * 32;
+        const int32_t c0 = __ldg(p.col + e), c1 = __ldg(p.col + e + 32), c2 = __ldg(p.col + e + 64),
+                      c3 = __ldg(p.col + e + 96);
+        const T a0 = __ldg(val + e), a1 = __ldg(val + e + 32), a2 = __ldg(val + e + 64), a3 = __ldg(val + e + 96);
+        const T g0 = __ldg(cur + c0), g1 = __ldg(cur + c1), g2 = __ldg(cur + c2), g3 = __ldg(cur + c3);
+        y = fma_t(a0, g0, y);
+        y = fma_t(a1, g1, y);
+        y = fma_t(a2, g2, y);
+        y = fma_t(a3, g3, y);
+      }
+      for (; j < width; ++j) {
         const int64_t e = base + (int64_t)j * 32;
         const int32_t c = __ldg(p.col + e);
         y = fma_t(__ldg(val + e), __ldg(cur + c), y);
@@ -157,7 +172,7 @@ __device__ bool grid_barrier(unsigned* bar, long long limit, int* status) {
           good = 0;
           break;
         }
-        __nanosleep(100);
+        __nanosleep(20);
       }
     }
     __threadfence();
@@ -169,7 +184,7 @@ __device__ bool grid_barrier(unsigned* bar, long long limit, int* status) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) csr_chain_kernel(CsrChainParams c) {
+__global__ void __launch_bounds__(1024) csr_chain_kernel(CsrChainParams c) {
   CsrJumpParams p = c.j;
   const size_t n = (size_t)p.n;
   T* rho = reinterpret_cast<T*>(c.rho);
@@ -265,7 +280,8 @@ cudaError_t launch_csr_jump(int precision, const CsrJumpParams& p, cudaStream_t 
 
 template <typename T>
 cudaError_t launch_chain_typed(const CsrChainParams& c, cudaStream_t s) {
-  const int block = 512;
+  // 1024-thread CTAs: the fewer CTAs meet at each grid barrier, the shorter it is.
+  const int block = 1024;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

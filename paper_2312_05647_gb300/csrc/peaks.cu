@@ -51,11 +51,34 @@ __global__ void __launch_bounds__(512) peak_smem_kernel(float* sink, int iters) 
   if (acc.x == -1.0f) sink[blockIdx.x * blockDim.x + t] = acc.x;
 }
 
+// Every thread gathers 4-byte values at pseudo-random positions of an
+// L2-resident 4 MB array (a linear congruential sequence per thread; eight
+// loads per iteration, independent of each other's values): the random-access
+// rate of the L2 that the general-CSR chain's gathers of rho meet.
+__global__ void __launch_bounds__(512) peak_gather_kernel(const float* __restrict__ a, unsigned mask, float* sink,
+                                                          int iters) {
+  unsigned h = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u + 12345u;
+  float acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      h = h * 1664525u + 1013904223u;
+      acc[j] += __ldg(a + ((h >> 7) & mask));
+    }
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += acc[j];
+  if (s == -1.0f) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 
 extern "C" int mjp_measure_peak(int which, int iters, double* result, void* stream) try {
   using namespace mjp;
-  if (!result || iters < 1 || (which != MJP_PEAK_FP32_FMA && which != MJP_PEAK_SMEM))
+  if (!result || iters < 1 || (which != MJP_PEAK_FP32_FMA && which != MJP_PEAK_SMEM && which != MJP_PEAK_L2_GATHER))
     return fail(MJP_ERR_ARG, "mjp_measure_peak: unknown quantity, iters < 1 or NULL result");
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0, sms = 0;
@@ -69,10 +92,20 @@ extern "C" int mjp_measure_peak(int which, int iters, double* result, void* stre
   DevBuf& sink = sk.b;
   int rc = sink.ensure(sizeof(float) * (size_t)blocks * threads);
   if (rc) return rc;
+  constexpr unsigned kGatherN = 1u << 20;  // 4 MB of FP32, as rho of the 2^20-state CSR configuration
+  struct Arr {
+    DevBuf b;
+    ~Arr() { b.release(); }
+  } ar;
+  if (which == MJP_PEAK_L2_GATHER) {
+    if ((rc = ar.b.ensure(sizeof(float) * kGatherN))) return rc;
+    MJP_CUDA(cudaMemsetAsync(ar.b.p, 0, sizeof(float) * kGatherN, s));
+  }
   const size_t smem = (which == MJP_PEAK_SMEM) ? 2 * threads * sizeof(float4) : 0;
   auto launch = [&]() -> cudaError_t {
     if (which == MJP_PEAK_FP32_FMA) peak_fma_kernel<<<blocks, threads, 0, s>>>(sink.as<float>(), iters);
-    else peak_smem_kernel<<<blocks, threads, smem, s>>>(sink.as<float>(), iters);
+    else if (which == MJP_PEAK_SMEM) peak_smem_kernel<<<blocks, threads, smem, s>>>(sink.as<float>(), iters);
+    else peak_gather_kernel<<<blocks, threads, 0, s>>>(ar.b.as<float>(), kGatherN - 1, sink.as<float>(), iters);
     return cudaGetLastError();
   };
   MJP_CUDA(launch());  // warm-up (clocks, instruction cache)
@@ -93,7 +126,8 @@ extern "C" int mjp_measure_peak(int which, int iters, double* result, void* stre
   cudaEventDestroy(e1);
   const double work = (double)blocks * threads * iters;
   if (which == MJP_PEAK_FP32_FMA) *result = work * kFmaChains * 4.0 / (best * 1e-3) / 1e12;  // TFLOP/s
-  else *result = work * 32.0 / (best * 1e-3) / 1e9;                                        // GB/s, read + write
+  else if (which == MJP_PEAK_SMEM) *result = work * 32.0 / (best * 1e-3) / 1e9;            // GB/s, read + write
+  else *result = work * 8.0 / (best * 1e-3) / 1e9;                                          // G gathers/s
   return MJP_OK;
 } catch (...) {
   return ::mjp::exception_status();

@@ -130,9 +130,9 @@ def test_one_launch_chain_equals_per_jump_launches(prec):
     rho0 = gen.random(n)
     rho0 /= rho0.sum()
     times = [0.1, 0.8, 2.0]
-    m1, a = _csr_run(rp, col, val, prec, rho0, times, {})
+    m1, a = _csr_run(rp, col, val, prec, rho0, times, {mjp.OPT_CHAIN: 2})
     m1.check()
-    m2, b = _csr_run(rp, col, val, prec, rho0, times, {mjp.OPT_CHAIN: 1})
+    m2, b = _csr_run(rp, col, val, prec, rho0, times, {})
     m2.check()
     np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
 
@@ -147,7 +147,7 @@ def test_grid_barrier_wait_that_runs_out_is_reported():
     n = 1 << 15
     rp, col, val = synth.random_csr(n, 4, gen, max_exit=40.0)
     rho0 = np.full(n, 1.0 / n)
-    m, _ = _csr_run(rp, col, val, 2, rho0, [1.0], {mjp.OPT_WAIT_LIMIT: 0})
+    m, _ = _csr_run(rp, col, val, 2, rho0, [1.0], {mjp.OPT_CHAIN: 2, mjp.OPT_WAIT_LIMIT: 0})
     with pytest.raises(MJPError) as ei:
         m.check()
     assert ei.value.code == -5  # MJP_ERR_DEVICE_TIMEOUT
