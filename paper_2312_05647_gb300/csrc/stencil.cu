@@ -629,21 +629,21 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
             T2 dg = v_fma(c_ngp, fpp, c_dg);        // 1 - e_{m,p} (FP32: -e_{m,p})
             const T2 cup = v_fma(c_gp, fpp, c_gp);  // gamma_p (p+1) from p+1
             if constexpr (kComp) {
-              // In the order of the register-resident kernel: residual, exit,
-              // at row P-1 the protein birth k_p m that does not leave it, then
-              // the inflows from below, above, left and right.
+              // In the order of the register-resident kernel: residual, the
+              // inflows from the left, right, below and above, the exit, and at
+              // row P-1 the protein birth k_p m that does not leave it.
               float2 l = *lp;
-              float2 t = v_fma(dg, cur, l);
-              if (top) {
-                if (pp == P - 1) t.x = f_fma(cd, cur.x, t.x);
-                else t.y = f_fma(cd, cur.y, t.y);
-              }
+              float2 t = v_fma(c_l, left, l);
+              t = v_fma(c_r, right, t);
               t.x = f_fma(cd, prev.y, t.x);
               t.y = f_fma(cd, cur.x, t.y);
               t.x = f_fma(cup.x, cur.y, t.x);
               t.y = f_fma(cup.y, next.x, t.y);
-              t = v_fma(c_l, left, t);
-              t = v_fma(c_r, right, t);
+              t = v_fma(dg, cur, t);
+              if (top) {
+                if (pp == P - 1) t.x = f_fma(cd, cur.x, t.x);
+                else t.y = f_fma(cd, cur.y, t.y);
+              }
               y = comp_finish(cur, t, l);
               if (top && pp + 1 >= P) {  // row P does not exist
                 y.y = 0.0f;

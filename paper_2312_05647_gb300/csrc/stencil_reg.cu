@@ -113,17 +113,24 @@ __host__ __device__ inline RegLayout reg_layout(size_t edge_bytes, int nt, int n
   return s;
 }
 
-// Register value of observation slot r * 4 + c (row r, column c; columns
-// c0, c2 in pair 0 and c1, c3 in pair 1 of the row), by a tree of selections
-// (no local-memory array).
+// Register slot of row r of a block at rotation ROT: 0 = home (row r in slot
+// r), 1 = shifted (row r in slot r - 1, row 0 in the spare slot NR).
 template <int NR>
-__device__ __forceinline__ float pick(const float2 (&S)[NR][2], int slot) {
+__host__ __device__ constexpr int rslot(int r, int rot) {
+  return rot == 0 ? r : (r == 0 ? NR : r - 1);
+}
+
+// Register value of observation slot r * 4 + c (row r, column c; columns
+// c0, c2 in pair 0 and c1, c3 in pair 1 of the row) at rotation ROT, by a tree
+// of selections (no local-memory array).
+template <int NR, int ROT>
+__device__ __forceinline__ float pick(const float2 (&S)[NR + 1][2], int slot) {
   const bool c1 = slot & 1, c2 = slot & 2;
   const int r = slot >> 2;
   float v = 0.0f;
 #pragma unroll
   for (int q = 0; q < NR; ++q) {
-    const float2 a = S[q][0], b = S[q][1];
+    const float2 a = S[rslot<NR>(q, ROT)][0], b = S[rslot<NR>(q, ROT)][1];
     const float x = c2 ? (c1 ? b.y : a.y) : (c1 ? b.x : a.x);
     v = (r == q) ? x : v;
   }
@@ -346,9 +353,12 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   unsigned char* const E0 = smem + L.edge;
 
   // rho0 into registers, its edges into parity 0.  Row r of the block is
-  // S[r][0] = (c0, c2), S[r][1] = (c1, c3), updated in place every jump.
+  // S[r][0] = (c0, c2), S[r][1] = (c1, c3); S[kRows] is a spare row: a jump
+  // writes row r's new values over row r-1's old ones (ascending) or row r+1's
+  // (descending), so the rows shift by one slot and back every two jumps and
+  // no register is copied.
   constexpr int NR = kRows;
-  float2 S[NR][2];
+  float2 S[NR + 1][2];
   const float* rho0 = reinterpret_cast<const float*>(p.rho0);
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
@@ -361,6 +371,7 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     S[r][0] = v_make(v[0], v[2]);
     S[r][1] = v_make(v[1], v[3]);
   }
+  S[NR][0] = S[NR][1] = v_make(0.0f, 0.0f);
   // Residuals start at zero.
 #pragma unroll
   for (int r = 0; r < NR; ++r) tmem_st4(tres + 4u * r, v_make(0.0f, 0.0f), v_make(0.0f, 0.0f));
@@ -375,36 +386,39 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   }
   // Edges of the block: the left (c0) and right (c3) columns per row pair,
   // the first and last rows as (c0, c2, c1, c3).
-  auto publish = [&](int par) {
+  auto publish = [&](int par, auto ROTC) {
+    constexpr int ROT = decltype(ROTC)::value;
     unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
 #pragma unroll
     for (int r = 0; r < kQR; ++r) {
+      const int s0 = rslot<NR>(2 * r, ROT), s1 = rslot<NR>(2 * r + 1, ROT);
       float* cl = reinterpret_cast<float*>(Ep + G::col(0, r) + oT8);
       float* cr = reinterpret_cast<float*>(Ep + G::col(1, r) + oT8);
-      cl[0] = S[2 * r][0].x;
-      cl[1] = S[2 * r + 1][0].x;
-      cr[0] = S[2 * r][1].y;
-      cr[1] = S[2 * r + 1][1].y;
+      cl[0] = S[s0][0].x;
+      cl[1] = S[s1][0].x;
+      cr[0] = S[s0][1].y;
+      cr[1] = S[s1][1].y;
     }
+    const int sf = rslot<NR>(0, ROT), sl = rslot<NR>(NR - 1, ROT);
     float2* fr = reinterpret_cast<float2*>(Ep + G::row(0) + oT16);
     float2* lr = reinterpret_cast<float2*>(Ep + G::row(1) + oT16);
-    fr[0] = S[0][0];
-    fr[1] = S[0][1];
-    lr[0] = S[NR - 1][0];
-    lr[1] = S[NR - 1][1];
+    fr[0] = S[sf][0];
+    fr[1] = S[sf][1];
+    lr[0] = S[sl][0];
+    lr[1] = S[sl][1];
     const size_t po = par ? G::par_bytes : 0;
     if (nb_dn) {
       float2* d = reinterpret_cast<float2*>(nb_dn + po);
-      d[0] = S[0][0];
-      d[1] = S[0][1];
+      d[0] = S[sf][0];
+      d[1] = S[sf][1];
     }
     if (nb_up) {
       float2* d = reinterpret_cast<float2*>(nb_up + po);
-      d[0] = S[NR - 1][0];
-      d[1] = S[NR - 1][1];
+      d[0] = S[sl][0];
+      d[1] = S[sl][1];
     }
   };
-  publish(0);
+  publish(0, std::integral_constant<int, 0>{});
   if (C > 1) cluster.sync();
   else __syncthreads();
 
@@ -435,7 +449,8 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
 
   // Observations of rho_k for the active times [l, h] of jump k (Kahan, FP32).
   int ecur = ebeg;
-  auto accumulate = [&](int k, int l, int h) {
+  auto accumulate = [&](int k, int l, int h, auto ROTC) {
+    constexpr int ROT = decltype(ROTC)::value;
     if (!owner || l > h) return;
     const int sk = k & (kStage - 1);
     while (ecur < eend && (ent[ecur].y >> 6) < l) ++ecur;
@@ -443,7 +458,7 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
       const int2 en = ent[e];
       const int ti = en.y >> 6;
       if (ti > h) break;
-      const float v = pick<NR>(S, en.y & 63);
+      const float v = pick<NR, ROT>(S, en.y & 63);
       const float w = ring[ti * kStage + sk];
       const float y = __fsub_rn(__fmul_rn(w, v), acc_c[en.x]);
       const float s0 = acc_s[en.x];
@@ -469,61 +484,97 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   };
   if (wwarp && any_rec && Kmax >= 1) rec_step(1);
   __syncthreads();
-  accumulate(0, lo, hi);  // rho_0 with the weights of jump 0
+  accumulate(0, lo, hi, std::integral_constant<int, 0>{});  // rho_0 with the weights of jump 0
 
-  // One jump, rho_{k-1} -> rho_k, in two halves around the cluster barrier.
-  // The terms of a state's update t are added in one order in every kernel
-  // that runs the compensated mRNA/protein chain: the residual, the exit
-  // -e rho (e = e0 + gamma_p p), in row P-1 the protein birth k_p m rho that
-  // does not leave it, then the inflows from below (k_p m rho(p-1)), above
-  // (gamma_p (p+1) rho(p+1)), left (k_m rho(m-1)) and right (gamma_m (m+1)
-  // rho(m+1)); then y = rho + t and the new residual.  In that order, every
-  // term that reads another thread's values comes after all terms of the
-  // same state that do not: the first half (PRE, in the shadow of the
-  // previous jump's barrier) forms t up to its first such term from the
-  // thread's own registers and stores it over the residual in tensor memory;
-  // the second half (POST), after the barrier, loads it back, reads the
-  // neighbours' edges, adds the remaining terms and finishes every state in
-  // place (rows ascending).
-  //  - interior rows: PRE does everything but c0's left and right inflows
-  //    and c3's right inflow;
-  //  - the first row: PRE does the residual, exit and P-1 terms (its below
-  //    is the neighbouring block's last row; its above, still old, is read in
-  //    POST before row 1 is updated);
-  //  - the last row: PRE adds its below too (the row below is updated in
-  //    place before POST reaches the last row).
-  // Row P-1 without branches when it is a block's last row: every thread
-  // adds topA / topB x rho in its last row, k_p m (both columns of the pair)
-  // in the block holding P-1 and zero elsewhere (adding +0 changes no
-  // value); the row above it is the zero slot.  Warps with a thread whose
-  // block holds P-1 elsewhere, rows beyond the box or padding columns run the
-  // EDGE variant with selections (warp-uniform, so no warp runs both; no
-  // branch inside a warp, which stays converged for the tensor-memory
-  // accesses).
+  // One jump of the block: rho_{k-1} at rotation DIR (0: home, rows
+  // ascending; 1: shifted, rows descending) -> rho_k at rotation 1 - DIR.
+  // Per state, in the shared-memory kernel's order: (1 - e) rho + k_m rho(m-1)
+  // + gamma_m (m+1) rho(m+1) + k_p m rho(p-1) + gamma_p (p+1) rho(p+1); the row
+  // holding P-1 adds k_p m back to 1 - e (no protein birth out of it), rows
+  // beyond it and padding columns stay zero.
+  // Row P-1 (no protein birth out of it: 1 - e gains k_p m back) is handled
+  // without branches when it is a block's last row: every thread adds topA /
+  // topB to the diagonal of its last row, k_p m (both columns of the pair) in
+  // the block holding P-1 and zero elsewhere (adding +0 changes no value); the
+  // row above it is the zero slot.  Warps with a thread whose block holds P-1
+  // elsewhere, rows beyond the box or padding columns run the EDGE update with
+  // explicit checks (warp-uniform, so no warp runs both).
   const bool edge_t = padcols || (rtop >= 0 && rtop != NR - 1);
   const bool edge_w = __any_sync(kFull, edge_t);
   const float2 topA = rtop == NR - 1 ? cdA : v_make(0.0f, 0.0f);
   const float2 topB = rtop == NR - 1 ? cdB : v_make(0.0f, 0.0f);
-  const float2 z2 = v_make(0.0f, 0.0f);
-  auto pre = [&](auto EDGEC) {
+  auto update = [&](int par, auto DIRC, auto EDGEC) {
+    constexpr int DIR = decltype(DIRC)::value;
     constexpr bool EDGE = decltype(EDGEC)::value;
+    const unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
     const int rtk = EDGE ? opaque(rtop) : -1;
     tmem_wait_st();  // the last jump's residual stores are complete
-    Tmem4 nx;
-    tmem_ld4_issue(tres, nx);
-    float2 fp;  // row index as a float pair, stepped exactly (integers below 2^24)
+    // The residuals of the next row in this jump's order are loaded while the
+    // current row is computed.
+    Tmem4 pre;
+    tmem_ld4_issue(tres + 4u * (DIR == 0 ? 0 : NR - 1), pre);
+    // Row index as a float pair, stepped exactly (integers below 2^24).
+    float2 fp;
     {
-      const float f0 = (float)opaque(pb);
+      const float f0 = (float)opaque(pb + (DIR == 0 ? 0 : NR - 1));
       fp = v_make(f0, f0);
     }
+    const float2 fstep = DIR == 0 ? v_make(1.0f, 1.0f) : v_make(-1.0f, -1.0f);
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const float2 A = S[r][0], B = S[r][1];
-      float2 tA, tB;
-      tmem_ld4_wait(nx, tA, tB);
-      if (r + 1 < NR) tmem_ld4_issue(tres + 4u * (r + 1), nx);
-      tA = v_fma(v_fma(c_ngp, fp, d0A), A, tA);  // residual + exit
-      tB = v_fma(v_fma(c_ngp, fp, d0B), B, tB);
+    for (int i = 0; i < NR; ++i) {
+      const int r = DIR == 0 ? i : NR - 1 - i;
+      const int so = rslot<NR>(r, DIR);                                  // old row r
+      const int sn = DIR == 0 ? (r == 0 ? NR : r - 1) : r;               // its new value
+      // The left block's c3 and the right block's c0 of this row pair, read at
+      // its first row in this jump's order.
+      float2 lp, rp;
+      if ((i & 1) == 0) {
+        lp = *reinterpret_cast<const float2*>(Ep + G::col(1, r >> 1) + oL);
+        rp = *reinterpret_cast<const float2*>(Ep + G::col(0, r >> 1) + oR);
+      }
+      const float2 A = S[so][0], B = S[so][1];
+      float2 bA, bB, aA, aB;  // rows p-1 and p+1: registers, or the row below / above the block
+      if (r == 0) {
+        const float2* e = reinterpret_cast<const float2*>(Ep + G::row(1) + oB);
+        bA = e[0];
+        bB = e[1];
+      } else {
+        bA = S[rslot<NR>(r - 1, DIR)][0];
+        bB = S[rslot<NR>(r - 1, DIR)][1];
+      }
+      if (r + 1 == NR) {
+        const float2* e = reinterpret_cast<const float2*>(Ep + G::row(0) + oA);
+        aA = e[0];
+        aB = e[1];
+      } else {
+        aA = S[rslot<NR>(r + 1, DIR)][0];
+        aB = S[rslot<NR>(r + 1, DIR)][1];
+      }
+      const float lin = (r & 1) ? lp.y : lp.x;
+      const float rin = (r & 1) ? rp.y : rp.x;
+      float2 rA, rB;  // residuals of row r
+      tmem_ld4_wait(pre, rA, rB);
+      if (i + 1 < NR) tmem_ld4_issue(tres + 4u * (DIR == 0 ? r + 1 : r - 1), pre);
+      const float2 dA = v_fma(c_ngp, fp, d0A), dB = v_fma(c_ngp, fp, d0B);  // -e_{m,p}
+      const float2 cup = v_fma(c_gp, fp, c_gp);  // gamma_p (p+1) from p+1
+      // t = residual + inflows from the left, right, below and above + exit,
+      // and in row P-1 the protein birth k_p m that does not leave it.
+      float2 tA = rA;
+      tA.x = f_fma(c_l, lin, tA.x);   // from m - 1: the left block's c3
+      tA.y = f_fma(c_l, B.x, tA.y);   // c1
+      tA = v_fma(crA, B, tA);         // from m + 1: (c1, c3)
+      tA = v_fma(cdA, bA, tA);
+      tA = v_fma(cup, aA, tA);
+      tA = v_fma(dA, A, tA);
+      float2 tB = v_fma(c_l2, A, rB);
+      tB.x = f_fma(crB.x, A.y, tB.x); // from m + 1: c2
+      tB.y = f_fma(crB.y, rin, tB.y); // the right block's c0
+      tB = v_fma(cdB, bB, tB);
+      tB = v_fma(cup, aB, tB);
+      tB = v_fma(dB, B, tB);
+      // (Selections, not branches: the warp stays converged for the
+      // tensor-memory store below.)
+      const float2 z2 = v_make(0.0f, 0.0f);
       if (EDGE) {
         tA = v_fma(r == rtk ? cdA : z2, A, tA);
         tB = v_fma(r == rtk ? cdB : z2, B, tB);
@@ -531,98 +582,36 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
         tA = v_fma(topA, A, tA);
         tB = v_fma(topB, B, tB);
       }
-      if (r > 0) {  // below: own registers (still rho_{k-1})
-        tA = v_fma(cdA, S[r - 1][0], tA);
-        tB = v_fma(cdB, S[r - 1][1], tB);
-      }
-      if (r > 0 && r < NR - 1) {
-        const float2 cup = v_fma(c_gp, fp, c_gp);  // gamma_p (p+1) from p+1
-        tA = v_fma(cup, S[r + 1][0], tA);
-        tB = v_fma(cup, S[r + 1][1], tB);
-        tA.y = f_fma(c_l, B.x, tA.y);     // c2: from m-1 (c1), from m+1 (c3)
-        tA.y = f_fma(crA.y, B.y, tA.y);
-        tB = v_fma(c_l2, A, tB);          // c1 and c3 from m-1 (c0, c2)
-        tB.x = f_fma(crB.x, A.y, tB.x);   // c1 from m+1 (c2)
-      }
-      tmem_st4(tres + 4u * r, tA, tB);
-      fp = v_add(fp, v_make(1.0f, 1.0f));
-    }
-  };
-  auto post = [&](int par, auto EDGEC) {
-    constexpr bool EDGE = decltype(EDGEC)::value;
-    const int rtk = EDGE ? opaque(rtop) : -1;
-    const unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
-    tmem_wait_st();  // the partial sums of PRE are complete
-    Tmem4 nx;
-    tmem_ld4_issue(tres, nx);
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      // The left block's c3 and the right block's c0 of this row pair.
-      float2 lp, rp;
-      if ((r & 1) == 0) {
-        lp = *reinterpret_cast<const float2*>(Ep + G::col(1, r >> 1) + oL);
-        rp = *reinterpret_cast<const float2*>(Ep + G::col(0, r >> 1) + oR);
-      }
-      const float lin = (r & 1) ? lp.y : lp.x;
-      const float rin = (r & 1) ? rp.y : rp.x;
-      const float2 A = S[r][0], B = S[r][1];
-      float2 tA, tB;
-      tmem_ld4_wait(nx, tA, tB);
-      if (r + 1 < NR) tmem_ld4_issue(tres + 4u * (r + 1), nx);
-      if (r == 0 || r == NR - 1) {
-        const float f0 = (float)opaque(pb + r);
-        const float2 fp = v_make(f0, f0);
-        const float2 cup = v_fma(c_gp, fp, c_gp);
-        if (r == 0) {  // below: the row under the block; above: own, still old
-          const float2* e = reinterpret_cast<const float2*>(Ep + G::row(1) + oB);
-          tA = v_fma(cdA, e[0], tA);
-          tB = v_fma(cdB, e[1], tB);
-          tA = v_fma(cup, S[1][0], tA);
-          tB = v_fma(cup, S[1][1], tB);
-        } else {       // above: the row over the block
-          const float2* e = reinterpret_cast<const float2*>(Ep + G::row(0) + oA);
-          tA = v_fma(cup, e[0], tA);
-          tB = v_fma(cup, e[1], tB);
-        }
-        tA.x = f_fma(c_l, lin, tA.x);     // from m-1: the left block's c3, c1
-        tA.y = f_fma(c_l, B.x, tA.y);
-        tA = v_fma(crA, B, tA);           // from m+1: (c1, c3)
-        tB = v_fma(c_l2, A, tB);          // from m-1: (c0, c2)
-        tB.x = f_fma(crB.x, A.y, tB.x);   // from m+1: c2, the right block's c0
-        tB.y = f_fma(crB.y, rin, tB.y);
-      } else {
-        tA.x = f_fma(c_l, lin, tA.x);     // c0 from m-1 (left block's c3), m+1 (c1)
-        tA.x = f_fma(crA.x, B.x, tA.x);
-        tB.y = f_fma(crB.y, rin, tB.y);   // c3 from m+1 (right block's c0)
-      }
-      float2 yA = comp_finish(A, tA, tA);
-      float2 yB = comp_finish(B, tB, tB);  // tA, tB now hold the new residuals
+      float2 yA = comp_finish(A, tA, rA);
+      float2 yB = comp_finish(B, tB, rB);
       if (EDGE) {
         const bool beyond = rtk >= 0 && r > rtk;  // rows beyond the box
         yA = beyond ? z2 : yA;
         yB = beyond ? z2 : yB;
-        tA = beyond ? z2 : tA;
-        tB = beyond ? z2 : tB;
+        rA = beyond ? z2 : rA;
+        rB = beyond ? z2 : rB;
         // Padding columns of the last quad: c1 (bit 1), c2 (bit 2), c3 (bit 3).
         const bool p1c = !(colmask & 2), p2c = !(colmask & 4), p3c = !(colmask & 8);
         yB.x = p1c ? 0.0f : yB.x;
-        tB.x = p1c ? 0.0f : tB.x;
+        rB.x = p1c ? 0.0f : rB.x;
         yA.y = p2c ? 0.0f : yA.y;
-        tA.y = p2c ? 0.0f : tA.y;
+        rA.y = p2c ? 0.0f : rA.y;
         yB.y = p3c ? 0.0f : yB.y;
-        tB.y = p3c ? 0.0f : tB.y;
+        rB.y = p3c ? 0.0f : rB.y;
       }
-      tmem_st4(tres + 4u * r, tA, tB);
-      S[r][0] = yA;
-      S[r][1] = yB;
+      tmem_st4(tres + 4u * r, rA, rB);
+      S[sn][0] = yA;
+      S[sn][1] = yB;
+      fp = v_add(fp, fstep);
     }
   };
 
-  // Exit-defect correction of rho_k: every state adds p.renorm x its defect
-  // x its value to its residual (zero coefficients and values outside the box
-  // keep those residuals zero).
+  // Exit-defect correction of rho_k (rotation ROT): every state adds p.renorm
+  // x its defect x its value to its residual (zero coefficients and values
+  // outside the box keep those residuals zero).
   const float period = (float)p.renorm;
-  auto defect_fix = [&]() {
+  auto defect_fix = [&](auto ROTC) {
+    constexpr int ROT = decltype(ROTC)::value;
     tmem_wait_st();
 #pragma unroll 1
     for (int r = 0; r < NR; ++r) {
@@ -632,12 +621,13 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
       float b[kQC];
 #pragma unroll
       for (int c = 0; c < kQC; ++c) b[c] = own * __fmul_rn(period, mrna_defect(mrna_col(co, m0 + c, M), co.d, pr));
-      float2 ya = z2, yb = z2;  // row r of the block, picked without local memory
+      // Row r sits in register slot r (home) or r - 1 (shifted); pick it by rotation.
+      float2 ya = v_make(0.0f, 0.0f), yb = ya;
 #pragma unroll
       for (int q = 0; q < NR; ++q)
         if (q == r) {
-          ya = S[q][0];
-          yb = S[q][1];
+          ya = S[rslot<NR>(q, ROT)][0];
+          yb = S[rslot<NR>(q, ROT)][1];
         }
       rA = v_fma(v_make(b[0], b[2]), ya, rA);
       rB = v_fma(v_make(b[1], b[3]), yb, rB);
@@ -646,15 +636,14 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   };
 
   // ---- the jump chain -------------------------------------------------------
-  if (Kmax >= 1) {
-    if (edge_w) pre(std::true_type{});
-    else pre(std::false_type{});
-  }
-  for (int k = 1; k <= Kmax; ++k) {
+  int k = 1;
+  auto step = [&](auto DIRC) {
+    constexpr int DIR = decltype(DIRC)::value;
+    constexpr int ROT = 1 - DIR;  // rotation of rho_k
     const int par = (k - 1) & 1;
-    if (edge_w) post(par, std::true_type{});
-    else post(par, std::false_type{});
-    publish(par ^ 1);
+    if (edge_w) update(par, DIRC, std::true_type{});
+    else update(par, DIRC, std::false_type{});
+    publish(par ^ 1, std::integral_constant<int, ROT>{});
     // Chunk c (jumps [c kChunk, (c+1) kChunk)) is staged at jump (c-1) kChunk + 1,
     // after the last read of the slots it reuses (chunk c-2's, read up to jump
     // (c-1) kChunk - 1), and waited for at jump c kChunk - 1, before the barrier
@@ -667,18 +656,21 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     cluster_arrive_relaxed();
     // Work that touches no edge overlaps the barrier: the exit-defect
     // correction and the observations of rho_k, the next chunk of weights,
-    // the recurrence one jump ahead, and the first half of jump k + 1.
-    if (p.renorm > 0 && k % p.renorm == 0) defect_fix();
+    // the recurrence one jump ahead.
+    if (p.renorm > 0 && k % p.renorm == 0) defect_fix(std::integral_constant<int, ROT>{});
     advance(k, lo, hi);
-    accumulate(k, lo, hi);
+    accumulate(k, lo, hi, std::integral_constant<int, ROT>{});
     if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
     if (wwarp && any_rec && k + 1 <= Kmax) rec_step(k + 1);
-    if (k < Kmax) {
-      if (edge_w) pre(std::true_type{});
-      else pre(std::false_type{});
-    }
     cluster_wait();
+    ++k;
+  };
+  while (k + 1 <= Kmax) {
+    step(std::integral_constant<int, 0>{});
+    step(std::integral_constant<int, 1>{});
   }
+  if (k <= Kmax) step(std::integral_constant<int, 0>{});
+  // rho_Kmax may be left at rotation 1; only the accumulators are read below.
   cp_async_wait<0>();
 
   // ---- epilogue: sum_g c_g log(a_g) over the cluster's accumulators ---------
