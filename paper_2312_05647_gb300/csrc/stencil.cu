@@ -493,20 +493,28 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
   const T2 two2 = v_make((T)2, (T)2);
 
   // ---- the jump chain -----------------------------------------------------
+  // Ring slots of jumps k - 1, k and k + lead, and the jumps left until the
+  // next exit-defect correction, kept as counters (no 64-bit modulo per jump).
+  int sprev = 0, scur = 1 % kWeightRing, sfut = (1 + kWeightLead) % kWeightRing;
+  int dleft = p.renorm;
   for (int64_t k = 1; k <= Kmax + 1; ++k) {
     const int par = (int)((k - 1) & 1);
     const T* src = reinterpret_cast<const T*>(smem + buf_off[par]);
     T* dst = reinterpret_cast<T*>(smem + buf_off[par ^ 1]);
     const double* rprev = pw + par * nt;    // FP64 recurrence state, jump k-1
     double* rcur = pw + (par ^ 1) * nt;     // jump k
-    const T* wprev = ring + (int)((k - 1) % kWeightRing) * nt;  // weights of jump k-1
-    T* wcur = ring + (int)(k % kWeightRing) * nt;
+    const T* wprev = ring + sprev * nt;     // weights of jump k-1
+    T* wcur = ring + scur * nt;
     const int plo = lo, phi = hi;
     int clo = lo, chi = hi;
     advance(k, clo, chi);
     const bool jump = k <= Kmax;
     // FP32: the exit defects are added back after jumps that are multiples of p.renorm.
-    const bool dfix = kComp && p.renorm > 0 && jump && (k % p.renorm) == 0;
+    bool dfix = false;
+    if (kComp && p.renorm > 0 && --dleft == 0) {
+      dfix = jump;
+      dleft = p.renorm;
+    }
     if (wwarp) {
       // Weights of jump k + lead from the planner's arena, copied straight
       // into the ring (cp.async, one group per jump) ...
@@ -514,7 +522,7 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
       advance(kf, flo, fhi);
       if (kf <= Kmax)
         for (int i = flo + lane; i <= fhi; i += 32)
-          if (t_wb[i]) cp_async_elem(ring + (int)(kf % kWeightRing) * nt + i, t_wb[i] + kf);
+          if (t_wb[i]) cp_async_elem(ring + sfut * nt + i, t_wb[i] + kf);
       cp_async_commit();
       // ... and, for windows without a stored copy, Algorithm 2's recurrence
       // P_k = P_{k-1} x / k (the tail is added at k = K).
@@ -695,6 +703,9 @@ __global__ void __launch_bounds__(1024, 1) chain_kernel(ChainParams p) {
     }
     lo = clo;
     hi = chi;
+    sprev = scur;
+    scur = scur + 1 == kWeightRing ? 0 : scur + 1;
+    sfut = sfut + 1 == kWeightRing ? 0 : sfut + 1;
   }
 
   if (wwarp) cp_async_wait<0>();
