@@ -58,14 +58,16 @@ def parse():
     ap.add_argument("--no-mcmc", action="store_true", help="skip the ESS/s comparison")
     ap.add_argument("--mcmc-iters", type=int, default=20000, help="iterations of each timed sampler run")
     ap.add_argument("--mcmc-adapt-iters", type=int, default=1500, help="iteration cap of each adaptive phase")
-    ap.add_argument("--probe", choices=["bd_heavy", "promoter", "csr"], default=None,
+    ap.add_argument("--probe", choices=["bd_heavy", "promoter", "csr", "batch"], default=None,
                     help="time one small case for a profiler capture instead of the bench line: bd_heavy = eight "
                          "birth-death instances of the uneven batch's largest size (N = 18,863, K = 26,884 jumps) "
                          "on clusters of --probe-cluster CTAs; promoter = the two-state promoter log-likelihood of "
                          "256 jittered thetas on its 50 x 100 snapshots (one exact launch of the samplers); csr = "
                          "the general CSR configuration (N = 2^20, 8 nonzeros per row, K = 309), --probe-chain 0 "
-                         "(one launch per jump) or 2 (one cooperative launch)")
+                         "(one launch per jump) or 2 (one cooperative launch); batch = the uneven batch of 4,096 "
+                         "birth-death instances, autotuned, replayed as a CUDA graph")
     ap.add_argument("--probe-chain", type=int, default=0)
+    ap.add_argument("--probe-threads", type=int, default=0, help="promoter probe: threads per CTA (0 = automatic)")
     ap.add_argument("--probe-cluster", type=int, default=4)
     ap.add_argument("--probe-precision", type=int, default=1, help="1 = FP32, 2 = FP64")
     ap.add_argument("--configs", action="store_true",
@@ -302,7 +304,26 @@ def probe_bd_heavy(cluster: int, precision: int):
             "ms": ms, "ns_per_jump": ms * 1e6 / K}
 
 
-def probe_promoter():
+def probe_batch(precision: int):
+    """The uneven batch of 4,096 birth-death instances: autotuned, one warm
+    CUDA-graph replay, then replays timed with CUDA events."""
+    import numpy as np
+    import synth
+    import paper_2312_05647_gb300 as mjp
+    bc = synth.bd_batch()
+    K = _bd_K(bc["N"], bc["theta"][:, 0], bc["theta"][:, 1], bc["t"])
+    bt = mjp.Batch(bc["N"], bc["theta"], bc["t"], precision=precision)
+    o = bt.empty_out()
+    tuned = bt.tune(o)
+    bt.run(o, use_graph=True)
+    ms = _events_ms(lambda: bt.run(o, use_graph=True), reps=3)
+    bt.check()
+    updates = float(np.sum(K * bc["N"]))
+    return {"probe": "batch", "precision": precision, "ms": ms, "state_updates_per_s": updates / (ms / 1e3),
+            "tuned": tuned}
+
+
+def probe_promoter(threads: int = 0):
     """The two-state promoter log-likelihood of 256 jittered thetas (FP32, the
     samplers' exact evaluation): one warm call, then one call timed."""
     import torch
@@ -312,12 +333,20 @@ def probe_promoter():
     snaps = synth.gillespie_snapshots(cfg["kind"], cfg["dims"], cfg["theta"], cfg["times"], 100, synth.rng(5, 0))
     ob = mjp.Obs(600, cfg["times"], synth.snapshot_obs(cfg["kind"], cfg["dims"], snaps), cfg["rho0"])
     m = mjp.Model(cfg["kind"], cfg["dims"], cfg["theta"], mjp.FP32)
+    if threads:
+        m.set_option(mjp.OPT_THREADS, threads)
     th = torch.tensor(synth.jitter(cfg["theta"], 256, 0.2, synth.rng(5, 11)), dtype=torch.float64, device="cuda")
     lo = torch.empty(256, dtype=torch.float64, device="cuda")
     mjp.loglik(m, ob, th, out=lo)
     ms = _events_ms(lambda: mjp.loglik(m, ob, th, out=lo))
     m.check()
-    return {"probe": "promoter", "thetas": 256, "ms": ms}
+    m.set_option(mjp.OPT_PROFILE, 1)
+    mjp.loglik(m, ob, th, out=lo)
+    torch.cuda.synchronize()
+    plan_ms, chain_ms = m.last_timing()
+    m.set_option(mjp.OPT_PROFILE, 0)
+    return {"probe": "promoter", "thetas": 256, "threads": threads, "ms": ms, "plan_ms": plan_ms,
+            "chain_ms": chain_ms}
 
 
 def probe_csr(chain: int, precision: int):
@@ -577,9 +606,11 @@ def main():
             if args.probe == "bd_heavy":
                 res = probe_bd_heavy(args.probe_cluster, args.probe_precision)
             elif args.probe == "promoter":
-                res = probe_promoter()
+                res = probe_promoter(args.probe_threads)
             elif args.probe == "csr":
                 res = probe_csr(args.probe_chain, args.probe_precision)
+            elif args.probe == "batch":
+                res = probe_batch(args.probe_precision)
             else:
                 res = other_configs()
             print(json.dumps(res), flush=True)

@@ -92,7 +92,11 @@ extern "C" {
 #define MJP_PTR_DEVICE 1
 
 /* ---- model options (rate_model_set_option) ----------------------------- */
-#define MJP_OPT_RENORM_PERIOD 1 /* FP32 chains: rescale rho to its initial mass every r jumps (0 = off, default) */
+#define MJP_OPT_RENORM_PERIOD 1 /* FP32 chains: every r jumps, add back to each state the defect of its FP32 exit
+                                   coefficient (1 minus the rounded outflow coefficients of its column of B), which
+                                   keeps the unit column sums of B (Eq. B_def) that rounding breaks.  Default 32;
+                                   0 = off; else a multiple of 8 in [8, 2^20].  Identical across kernels.  FP64
+                                   chains ignore it.  Also a batch option. */
 #define MJP_OPT_K_CAP 2         /* largest K accepted (default 2^26) */
 #define MJP_OPT_THREADS 3       /* threads per CTA for stencil chains, one warp of which forms the weights (0 = automatic; else a multiple of 32 in [64, 1024]) */
 #define MJP_OPT_CLUSTER 4       /* CTAs per instance for stencil chains (0 = automatic; 1, 2, 4, 8, 16) */
@@ -102,9 +106,11 @@ extern "C" {
 #define MJP_OPT_CHAIN 7         /* general CSR models: 0 or 1 = one launch per jump (default), 2 = the whole chain in
                                    one cooperative launch with a bounded grid barrier per jump (identical results;
                                    see MJP_OPT_WAIT_LIMIT).  Stencil models: 0 = automatic (the register-resident kernels for
-                                   the log-likelihood of FP32 mRNA/protein boxes and for expv_series of birth-death
-                                   models, both without renormalisation or forced thread counts (and for the
-                                   former forced cluster sizes), else the shared-memory kernel), 1 = shared-memory
+                                   the log-likelihood of FP32 mRNA/protein boxes (automatic thread count or 256),
+                                   of FP32 two-state models whose observation groups have at most two members (one
+                                   CTA of MJP_OPT_THREADS / 32 <= 8 warps per theta; automatic when 0) and for
+                                   expv_series of birth-death models (automatic thread count), none with a forced
+                                   cluster size, else the shared-memory kernel), 1 = shared-memory
                                    kernel, 2 = register-resident kernel (MJP_ERR_UNSUPPORTED where it does not
                                    apply; other models' expv_series always runs the shared-memory kernel).  Also a batch option
                                    (expv_batch_set_option): 0 = the register-resident birth-death kernel wherever every
@@ -292,7 +298,8 @@ int expv_batch_check(mjp_batch* b, void* stream);
  * register-resident kernel; see beside MJP_OPT_CHAIN), MJP_OPT_CLUSTER (CTAs
  * per heavy instance, 0 = automatic, else 1 .. 8; instances that need more
  * CTAs to fit still get them), MJP_OPT_HALO (halo width of the
- * register-resident kernel's clusters).  Takes effect at the next run or tune
+ * register-resident kernel's clusters), MJP_OPT_RENORM_PERIOD (FP32 exit-defect
+ * correction period, as for models).  Takes effect at the next run or tune
  * (a captured graph is rebuilt).  Every setting gives the same results up to
  * the bit (the kernels share their arithmetic).  Errors: MJP_ERR_ARG. */
 int expv_batch_set_option(mjp_batch* b, int option, int64_t value);

@@ -95,6 +95,7 @@ struct mjp_obs {
   int nmem = 0;
   int maxmem = 0;  // most members in one group
   std::vector<double> times;  // ascending (host copy)
+  std::vector<int32_t> members;  // host copy (groups in ascending time order)
   DevBuf d_times, d_gptr, d_counts, d_mptr, d_members, d_rho64, d_rho32;
   ~mjp_obs() {
     d_times.release(); d_gptr.release(); d_counts.release(); d_mptr.release();
@@ -956,6 +957,7 @@ int mjp_obs_create(mjp_obs** out, int64_t n, int ntimes, const double* times,
   o->nmem = (int)(mp.back());
   for (size_t g = 0; g + 1 < mp.size(); ++g) o->maxmem = std::max<int>(o->maxmem, (int)(mp[g + 1] - mp[g]));
   o->times = st;
+  o->members = mem;
   int rc = 0;
   if ((rc = o->d_times.ensure(sizeof(double) * ntimes)) || (rc = o->d_gptr.ensure(sizeof(int64_t) * gp.size())) ||
       (rc = o->d_counts.ensure(sizeof(double) * cnt.size())) || (rc = o->d_mptr.ensure(sizeof(int64_t) * mp.size())) ||
@@ -1031,11 +1033,26 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   if (m->chain != 1 && m->kind == MJP_MRNA_PROT2D && m->precision == MJP_FP32 &&
       (m->chain == 2 || (m->cluster == 0 && m->threads == 0)))
     use_reg = chain_reg2d_plan(m->M, m->P, nt, obs->nmem, 8, m->threads, &rp);
-  if (m->chain == 2 && !use_reg)
-    return fail(MJP_ERR_UNSUPPORTED, "the register-resident chain needs an FP32 mRNA/protein box without "
-                                     "a forced thread count that fits 8 CTAs");
+  // Register-resident two-state chain: FP32, groups of at most two members,
+  // no forced cluster size (a thread count picks its warps).
+  RegTsPlan tp = {};
+  bool use_ts = false;
+  if (m->chain != 1 && m->kind == MJP_TWOSTATE && m->precision == MJP_FP32 && m->cluster == 0) {
+    int col_lo = -1, col_hi = -1;  // columns (n_R) of the observed states
+    if (obs->G > 0)
+      for (int32_t sidx : obs->members) {
+        const int c = (int)(sidx % m->M);
+        col_lo = col_lo < 0 ? c : std::min(col_lo, c);
+        col_hi = std::max(col_hi, c);
+      }
+    use_ts = chain_regts_plan(m->M, nt, obs->G, obs->maxmem, col_lo, col_hi, m->threads, &tp);
+  }
+  if (m->chain == 2 && !use_reg && !use_ts)
+    return fail(MJP_ERR_UNSUPPORTED, "the register-resident chain needs an FP32 mRNA/protein box that fits 8 "
+                                     "CTAs, at the automatic thread count or 256, or an FP32 two-state model whose "
+                                     "groups have at most two members and that fits one CTA");
   int rc = 0;
-  if (!use_reg && (rc = stencil_config(m, 1, nt, obs->G, nmem_list, &C, &T, &slab))) return rc;
+  if (!use_reg && !use_ts && (rc = stencil_config(m, 1, nt, obs->G, nmem_list, &C, &T, &slab))) return rc;
   if ((rc = ensure_status(m))) return rc;
   if ((rc = m->d_win.ensure(sizeof(Win) * (size_t)nt * B))) return rc;
   if ((rc = m->d_info.ensure(sizeof(JobInfo) * (size_t)B))) return rc;
@@ -1080,6 +1097,7 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   cp.slab = slab; cp.status = pp.status;
   cp.job_map = ordered ? m->d_jmap.as<int32_t>() : nullptr;
   if (use_reg) MJP_CUDA(launch_chain_reg2d(cp, rp, s));
+  else if (use_ts) MJP_CUDA(launch_chain_regts(cp, tp, s));
   else MJP_CUDA(launch_chain_stencil(m->kind, m->precision, 1, cp, C, T, s));
   if ((rc = mark(m, 2, s))) return rc;
   if (where == MJP_PTR_HOST) {

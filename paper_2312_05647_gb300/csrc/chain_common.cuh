@@ -216,6 +216,22 @@ __device__ __forceinline__ float bd_defect(const Coef<T>& co, int n, int N) {
   const float e = __fadd_rn(bn, ain);
   return (float)(((double)e - (double)bn) - (double)ain);
 }
+// Two-state state (column m, row sigma): the active row (sigma = 0) exits by
+// birth beta' (absent at m = N_R - 1), death fl(gamma m) and deactivation
+// lambda_ina, summed as fl(fl(fl(gamma m) + beta') + lambda_ina); the inactive
+// row by activation and death, fl(lambda_act + fl(gamma m)).  The defect is
+// that exit minus its outflows, formed in FP64 and rounded.
+template <typename T>
+__device__ __forceinline__ float ts_defect(const Coef<T>& co, int row, int m, int M) {
+  const float bm = __fmul_rn((float)co.b, (float)m);
+  const float ain = m + 1 < M ? (float)co.a : 0.0f;
+  if (row == 0) {
+    const float e = __fadd_rn(__fadd_rn(bm, ain), (float)co.d);
+    return (float)((((double)e - (double)bm) - (double)ain) - (double)co.d);
+  }
+  const float e = __fadd_rn((float)co.c, bm);
+  return (float)(((double)e - (double)co.c) - (double)bm);
+}
 // mRNA/protein column m: e0 = fl(fl(fl(gamma_m m) + k_m') + fl(k_p m)) (k_m'
 // = k_m below the last column), the exit without the protein decay, and its
 // column defect e0 - (its three outflows), formed in FP64 and rounded.

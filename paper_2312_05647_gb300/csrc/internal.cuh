@@ -203,6 +203,18 @@ bool chain_reg1d_plan(int precision, int64_t Nmax, int ntimes, int cluster, int 
                       bool small = false);
 int64_t chain_reg1d_max_states(int precision);
 cudaError_t launch_chain_reg1d(int precision, const ChainParams& p, const Reg1dPlan& rp, cudaStream_t s);
+// Register-resident two-state chain (stencil_regts.cu): FP32 loglik, one CTA
+// per theta, groups of at most two members.
+struct RegTsPlan {
+  int threads;   // per CTA (32 W)
+  int qp;        // state pairs per thread and row (1, 3 or 7)
+  int tlo;       // first thread holding an observed column
+  int nslot;     // history slots (qp per thread from tlo on)
+  size_t smem;   // dynamic shared memory per CTA
+};
+bool chain_regts_plan(int64_t M, int ntimes, int G, int maxmem, int col_lo, int col_hi, int threads,
+                      RegTsPlan* out);
+cudaError_t launch_chain_regts(const ChainParams& p, const RegTsPlan& rp, cudaStream_t s);
 int64_t rk4_max_states();
 // Krylov subspace steps for one birth-death distribution (krylov.cu).
 struct KrylovParams {

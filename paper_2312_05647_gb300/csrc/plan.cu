@@ -93,8 +93,23 @@ __device__ void set_status(int* st, int code) {
   if (st) atomicCAS(st, 0, code);
 }
 
-// Plan one time on one warp.
-__device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst, int lane) {
+// Window [L, K] of x = Omega t under the paper's rule: Algorithm 2's last k
+// and the first k whose left Poisson tail is not negligible; false when
+// there is no chain (x = 0) or K exceeds the cap.
+__device__ bool window_bounds(const PlanParams& p, double x, int64_t& L, int64_t& K) {
+  if (x == 0.0) return false;
+  const double s = __dsqrt_rn(x);
+  const double kstar = __dadd_rn(x, __dmul_rn(6.0, s));  // Omega t + 6 sqrt(Omega t)
+  if (!(kstar + 1.0 <= (double)p.kcap)) return false;
+  K = (int64_t)floor(kstar) + 1;
+  const double lo = __dsub_rn(x, __dmul_rn(10.0, s));  // Poisson left tail below x - 10 sqrt x is < e^-50
+  L = lo > 0.0 ? (int64_t)floor(lo) : 0;
+  return true;
+}
+
+// Plan one time on one warp.  doff: the arena offset reserved for this
+// window's weights (paper's rule), or -1.
+__device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst, int lane, long long doff_in) {
   Win r;
   double x = __dmul_rn(omega, t);
   r.x = x;
@@ -119,11 +134,24 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
     }
     return;
   }
-  int64_t K = (int64_t)floor(kstar) + 1;  // Algorithm 2's last k
+  int64_t K = 0, L = 0;
+  window_bounds(p, x, L, K);
   int64_t m = (int64_t)floor(x);
-  double lo = x - 10.0 * s;  // Poisson left tail below x - 10 sqrt x is < e^-50
-  int64_t L = lo > 0.0 ? (int64_t)floor(lo) : 0;
   int64_t R = (int64_t)floor(x + 10.0 * s) + 10;
+
+  // Under the paper's rule K is known before the scans: the window [L, K]
+  // of the weight arena was reserved by the CTA and receives the
+  // unnormalised weights as the scans form them (scaled by 1 / W below), so
+  // no second pair of scans is needed.
+  const bool direct = p.arena && p.trunc_mode == MJP_TRUNC_PAPER;
+  const int64_t dsize = K - L + 1;
+  const unsigned long long doff = doff_in >= 0 ? (unsigned long long)doff_in : 0ull;
+  const bool dstore = direct && doff_in >= 0;
+  auto put_raw = [&](int64_t k, double w) {
+    if (p.arena_fp64) reinterpret_cast<double*>(p.arena)[doff + (k - L)] = w;
+    else reinterpret_cast<float*>(p.arena)[doff + (k - L)] = (float)w;
+  };
+  if (dstore && lane == 0) put_raw(m, 1.0);
 
   // Upward from the mode: w_k = w_{k-1} x / k, w_m = 1.
   Kahan sum, tailsum;
@@ -137,6 +165,7 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
     if (k <= R) {
       sum.add(w);
       if (p.trunc_mode == MJP_TRUNC_PAPER && k > K) tailsum.add(w);
+      if (dstore && k <= K) put_raw(k, w);
     }
   }
   double wR = carry;
@@ -148,7 +177,10 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
     double term = (k >= L) ? __ddiv_rn((double)(k + 1), x) : 1.0;
     double w = __dmul_rn(warp_incl_prod(term, lane), carry);
     carry = __shfl_sync(kFull, w, 31);
-    if (k >= L) sum.add(w);
+    if (k >= L) {
+      sum.add(w);
+      if (dstore) put_raw(k, w);
+    }
     if (k == L) wL = w;
   }
   double W = warp_sum(sum.s) - warp_sum(sum.c);
@@ -204,10 +236,25 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
   r.PL = wL / W;
   r.tail = tail;
   r.woff = -1;
-  // Store P_L..P_K (the tail folded into P_K) in the arena, recomputing the
-  // same product scans, so the chain reads the weights instead of running
-  // the recurrence.
-  if (p.arena) {
+  // P_L..P_K (the tail folded into P_K) in the arena, so the chain reads the
+  // weights instead of running the recurrence: the stored unnormalised
+  // weights scaled by 1 / W (paper's rule), or (tolerance rule, K known only
+  // now) the same product scans run again.
+  if (direct) {
+    if (dstore) {
+      r.woff = (int64_t)doff;
+      __syncwarp();  // every lane's raw weights are visible to the lane that scales them
+      const double invW = __ddiv_rn(1.0, W);
+      for (int64_t j = lane; j < dsize; j += 32) {
+        double v = p.arena_fp64 ? reinterpret_cast<double*>(p.arena)[doff + j]
+                                : (double)reinterpret_cast<float*>(p.arena)[doff + j];
+        v = __dmul_rn(v, invW);
+        if (L + j == K) v = v + tail;
+        if (p.arena_fp64) reinterpret_cast<double*>(p.arena)[doff + j] = v;
+        else reinterpret_cast<float*>(p.arena)[doff + j] = (float)v;
+      }
+    }
+  } else if (p.arena) {
     const int64_t size = K - L + 1;
     unsigned long long off = 0;
     if (lane == 0) off = atomicAdd(p.arena_used, (unsigned long long)size);
@@ -278,7 +325,33 @@ __global__ void __launch_bounds__(256) plan_kernel(PlanParams p) {
   }
   Win* wj = p.win + (int64_t)job * p.ntimes;
   const double* tj = p.times + (p.times_per_job ? (int64_t)job * p.ntimes : 0);
-  for (int i = warp; i < p.ntimes; i += blockDim.x >> 5) plan_time(p, omega, tj[i], wj + i, lane);
+  // Paper's rule: the weight windows of all this instance's times are
+  // reserved in one piece, in time order (the same layout every call, and an
+  // instance's windows either all fit or all run the chain's recurrence).
+  __shared__ long long s_off[kMaxTimes];
+  const bool direct = p.arena && p.trunc_mode == MJP_TRUNC_PAPER;
+  if (direct) {
+    for (int i = tid; i < p.ntimes; i += blockDim.x) {
+      int64_t L = 0, K = 0;
+      s_off[i] = window_bounds(p, __dmul_rn(omega, tj[i]), L, K) ? (long long)(K - L + 1) : 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      long long tot = 0;
+      for (int i = 0; i < p.ntimes; ++i) {
+        const long long sz = s_off[i];
+        s_off[i] = sz > 0 ? tot : -1;
+        tot += sz;
+      }
+      const unsigned long long base = tot > 0 ? atomicAdd(p.arena_used, (unsigned long long)tot) : 0ull;
+      const bool fit = (long long)base + tot <= (long long)p.arena_cap;
+      for (int i = 0; i < p.ntimes; ++i) s_off[i] = (fit && s_off[i] >= 0) ? (long long)base + s_off[i] : -1;
+      if (!fit && p.arena_over) atomicOr(p.arena_over, 1);
+    }
+    __syncthreads();
+  }
+  for (int i = warp; i < p.ntimes; i += blockDim.x >> 5)
+    plan_time(p, omega, tj[i], wj + i, lane, direct ? s_off[i] : -1);
   __syncthreads();
   if (tid == 0) {
     int64_t kmax = 0;

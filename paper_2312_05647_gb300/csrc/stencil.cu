@@ -148,17 +148,8 @@ template <int KIND, typename T>
 __device__ float exit_defect(const Coef<T>& co, int row, int col, int M, int P) {
   if (KIND == MJP_BD1D) return bd_defect(co, col, M);
   if (KIND == MJP_MRNA_PROT2D) return mrna_defect(mrna_col(co, col, M), (float)co.d, row);
+  if (KIND == MJP_TWOSTATE) return ts_defect(co, row, col, M);
   const float fm = (float)col;
-  if (KIND == MJP_TWOSTATE) {
-    const float bm = __fmul_rn((float)co.b, fm);
-    const float ain = col + 1 < M ? (float)co.a : 0.0f;
-    if (row == 0) {  // active: birth, death, deactivation
-      const float e = __fadd_rn(__fadd_rn(bm, ain), (float)co.d);
-      return (float)((((double)e - (double)bm) - (double)ain) - (double)co.d);
-    }
-    const float e = __fadd_rn((float)co.c, bm);  // inactive: activation, death
-    return (float)(((double)e - (double)co.c) - (double)bm);
-  }
   // Autoregulatory network, tile row 2 q + sigma (Pm = P / 2 protein counts).
   const int q = row >> 1, Pm = P / 2;
   const float fq = (float)q;

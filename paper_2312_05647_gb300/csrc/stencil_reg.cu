@@ -637,6 +637,8 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
 
   // ---- the jump chain -------------------------------------------------------
   int k = 1;
+  // Jumps left until the next defect correction (never reached when off: K < 2^30).
+  int dleft = p.renorm > 0 ? p.renorm : 0x7fffffff;
   auto step = [&](auto DIRC) {
     constexpr int DIR = decltype(DIRC)::value;
     constexpr int ROT = 1 - DIR;  // rotation of rho_k
@@ -657,7 +659,10 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     // Work that touches no edge overlaps the barrier: the exit-defect
     // correction and the observations of rho_k, the next chunk of weights,
     // the recurrence one jump ahead.
-    if (p.renorm > 0 && k % p.renorm == 0) defect_fix(std::integral_constant<int, ROT>{});
+    if (--dleft == 0) {
+      dleft = p.renorm;
+      defect_fix(std::integral_constant<int, ROT>{});
+    }
     advance(k, lo, hi);
     accumulate(k, lo, hi, std::integral_constant<int, ROT>{});
     if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
