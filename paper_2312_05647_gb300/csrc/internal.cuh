@@ -206,9 +206,10 @@ cudaError_t launch_chain_reg1d(int precision, const ChainParams& p, const Reg1dP
 // Register-resident two-state chain (stencil_regts.cu): FP32 loglik, one CTA
 // per theta, groups of at most two members.
 struct RegTsPlan {
-  int threads;   // per CTA (32 W)
+  int threads;   // per CTA: chain warps and reducer warps
+  int chain_warps;
   int qp;        // state pairs per thread and row (1, 3 or 7)
-  int tlo;       // first thread holding an observed column
+  int tlo;       // first chain thread holding an observed column
   int nslot;     // history slots (qp per thread from tlo on)
   size_t smem;   // dynamic shared memory per CTA
 };
