@@ -1092,7 +1092,7 @@ int loglik(mjp_model* m, const mjp_obs* obs, const double* theta, int B, double*
   cp.rho0 = (m->precision == MJP_FP64) ? obs->d_rho64.p : obs->d_rho32.p;
   cp.gptr = obs->d_gptr.as<int64_t>(); cp.counts = obs->d_counts.as<double>();
   cp.mptr = obs->d_mptr.as<int64_t>(); cp.members = obs->d_members.as<int32_t>();
-  cp.G = obs->G; cp.nmem = nmem_list; cp.ll = d_out;
+  cp.G = obs->G; cp.nmem = nmem_list; cp.ll = d_out; cp.wait_limit = m->wait_limit;
   cp.renorm = (m->precision == MJP_FP32) ? m->renorm : 0;
   cp.slab = slab; cp.status = pp.status;
   cp.job_map = ordered ? m->d_jmap.as<int32_t>() : nullptr;

@@ -112,6 +112,9 @@ struct ChainParams {
   const int64_t* job_s0;   // rho0 = delta at s0 for each job (instead of rho0)
   int tile_max;            // padded tile size of the largest job in the launch
   const void* arena;       // planner's weight arena (T), indexed by Win::woff
+  // Polls of a bounded wait between a kernel's warp groups before it gives up
+  // (status kStatusTimeout); MJP_OPT_WAIT_LIMIT.
+  long long wait_limit = 1LL << 24;
 };
 
 // One jump of the general-CSR chain (csr.cu).

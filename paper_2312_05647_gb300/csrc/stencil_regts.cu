@@ -36,8 +36,8 @@
 // most 8 terms), added to the group's accumulator with a Kahan step, while
 // the chain warps fill the other half.  Two mbarriers per half hand it over
 // (full: the chain threads have written it; empty: the reducers have read
-// it); every wait on them is bounded and reports kStatusTimeout when it runs
-// out.  The reducers also stage the weights of Algorithm 2 (FP64 in the
+// it); every wait on them is bounded (p.wait_limit polls, MJP_OPT_WAIT_LIMIT)
+// and reports kStatusTimeout when it runs out.  The reducers also stage the weights of Algorithm 2 (FP64 in the
 // planner, rounded to FP32) from the planner's arena 32 jumps at a time, one
 // chunk ahead; a window without a stored copy runs the recurrence P_k =
 // P_{k-1} x / k from P_L (FP64) while its chunk is staged.
@@ -63,7 +63,6 @@ constexpr int kWStride = kWRing + 4;
 constexpr int kHS = 2 * kHist + 4;
 constexpr int kMaxChainWarps = 8;
 constexpr int kReduceWarps = 2;
-constexpr long long kWaitPolls = 1LL << 22;  // polls of a handover wait (~0.3 s) before it gives up
 
 struct TsLayout {
   size_t edge, tx, tPL, ttail, twb, pw, tL, tK, trec, gptr, ring, gloc, gtime, acc_s, acc_c, hist, total;
@@ -498,7 +497,7 @@ __global__ void __launch_bounds__(32 * (kMaxChainWarps + kReduceWarps))
     // (chunk q - 2), then hands it over; at the end, wait until the reducers
     // have read the last two chunks.
     for (int q = 0; q < nq && ok; ++q) {
-      if (q >= 2) ok = chain_all(mbar_wait(&empty_bar[q & 1], ((q >> 1) - 1) & 1, kWaitPolls));
+      if (q >= 2) ok = chain_all(mbar_wait(&empty_bar[q & 1], ((q >> 1) - 1) & 1, p.wait_limit));
       if (!ok) break;
       hc = kHist * (q & 1);
       if (kHist * q + kHist <= Kmax) TsSeq<0, kHist>::run(jump, std::false_type{});
@@ -506,12 +505,12 @@ __global__ void __launch_bounds__(32 * (kMaxChainWarps + kReduceWarps))
       mbar_arrive(&full_bar[q & 1]);
     }
     for (int q = nq; q < nq + 2 && ok; ++q)
-      if (q >= 2) ok = chain_all(mbar_wait(&empty_bar[q & 1], ((q >> 1) - 1) & 1, kWaitPolls));
+      if (q >= 2) ok = chain_all(mbar_wait(&empty_bar[q & 1], ((q >> 1) - 1) & 1, p.wait_limit));
     if (!ok && tid == 0) set_status(p.status, kStatusTimeout);
   } else {
     auto red_sync = [&]() { named_sync(2, nred); };
     for (int q = 0; q < nq && ok; ++q) {
-      ok = named_and(2, nred, mbar_wait(&full_bar[q & 1], (q >> 1) & 1, kWaitPolls));
+      ok = named_and(2, nred, mbar_wait(&full_bar[q & 1], (q >> 1) & 1, p.wait_limit));
       if (!ok) break;
       cp_async_wait<0>();
       red_sync();  // the weights every reducer staged for this chunk have landed

@@ -144,3 +144,26 @@ def test_two_state_register_chain_edge_cases():
     ref0 = oracle.loglik(oracle.build_model(synth.TWOSTATE, [N_R], thetas[0]), rho0, times, obs)
     assert abs(ll[0] - ref0) <= LL_PER_OBS * _nobs(obs)
     assert ll[1] == -np.inf  # no births: n_R > 0 has probability zero
+
+
+def test_two_state_register_chain_handover_wait_that_runs_out_is_reported():
+    # A wait limit of zero polls: the first hand-over that is not ready at
+    # once gives up; both warp groups stop, the status word says so, and the
+    # model (and the context) stay usable.
+    import paper_2312_05647_gb300 as mjp
+    from paper_2312_05647_gb300.capi import MJPError
+    times = np.linspace(0.5, 8.0, 6)
+    cfg, obs = _promoter(120, times, 30, seed=41)
+    thetas = synth.jitter(cfg["theta"], 4, 0.2, synth.rng(9, 42))
+    m = mjp.Model(synth.TWOSTATE, [120], thetas[0], mjp.FP32)
+    m.set_option(mjp.OPT_CHAIN, 2)
+    m.set_option(mjp.OPT_WAIT_LIMIT, 0)
+    o = mjp.Obs(240, times, obs, cfg["rho0"])
+    with pytest.raises(MJPError) as ei:
+        mjp.loglik(m, o, thetas)  # host call: synchronises and checks the status word
+    assert ei.value.code == -5  # MJP_ERR_DEVICE_TIMEOUT
+    m.set_option(mjp.OPT_WAIT_LIMIT, 1 << 24)
+    ll = mjp.loglik(m, o, thetas)
+    m.check()
+    ref = _ll(120, thetas, times, obs, cfg["rho0"], chain=2)
+    np.testing.assert_array_equal(ll, ref)
