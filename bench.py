@@ -41,10 +41,12 @@ LL_PER_OBS = 5e-6
 # On-chip bytes per state update of the register-resident chain (4-column x
 # 10-row blocks): per thread and jump it writes its block's edges (left and
 # right columns, first and last rows: 112 B) to shared memory and reads its
-# neighbours' (112 B), and reads and writes the 40 residuals in tensor memory
-# (320 B); per state 5.6 B of shared memory and 8 B of tensor memory.
+# neighbours' (112 B); per row of 4 states it reads 10 words from tensor
+# memory (4 residuals, 4 exit coefficients, the inflow-from-above coefficient
+# twice) and writes the 4 residuals back (56 B); per state 5.6 B of shared
+# memory and 14 B of tensor memory.
 SMEM_BYTES_PER_UPDATE = 224.0 / 40
-TMEM_BYTES_PER_UPDATE = 320.0 / 40
+TMEM_BYTES_PER_UPDATE = 56.0 / 4
 
 
 def parse():

@@ -22,14 +22,19 @@
 // edges that cross a CTA boundary are written into the neighbour CTA's halo
 // slots through distributed shared memory.
 //
-// The residuals live in tensor memory (TMEM, 256 KB per SM, otherwise idle in
-// this kernel): the registers of a 512-thread CTA hold the 40 values of a
-// block and the coefficients, not 40 residuals as well.  Each warp owns its
-// 32 TMEM lanes (the quadrant warp % 4 may address) and 4 columns per row of
-// its blocks; a row's four residuals are read with one tcgen05.ld (issued
-// while the previous row is computed) and written back with one tcgen05.st.
-// The CTA holds one allocation from start to end, sized so that all CTAs the
-// register file admits on one SM fit its TMEM (no allocation ever waits).
+// The residuals and the row coefficients live in tensor memory (TMEM, 256 KB
+// per SM, otherwise idle in this kernel): the registers of a 512-thread CTA
+// hold the 40 values of a block and the column coefficients, not 40 residuals
+// as well, and the coefficients that depend on the row (the exit of each
+// column pair and the inflow from the row above), formed once in the
+// prologue exactly as the update formed them every jump before, are loaded
+// instead of recomputed.  Each warp owns its 32 TMEM lanes (the quadrant
+// warp % 4 may address) and 12 columns per row of its blocks; a row's
+// residuals and coefficients are read with three tcgen05.ld (issued while the
+// previous row is computed) and its residuals written back with one
+// tcgen05.st.  The CTA holds one allocation from start to end, sized so that
+// all CTAs the register file admits on one SM fit its TMEM (no allocation
+// ever waits).
 //
 // Every neighbour read and edge write uses a per-thread base plus a
 // compile-time offset (the edge arrays have fixed strides), and the jump
@@ -55,14 +60,17 @@ constexpr int kQC = 4;            // columns per thread block of states
 // its barrier); <= 128 registers per thread either way, so the register file
 // itself admits one (T = 512) or two (T = 256) CTAs per SM.
 constexpr int kMaxNQ = 512;       // column quads (M <= 2048)
-// TMEM columns per CTA: T / 128 warps share each lane quadrant, 4 columns per
-// row of their blocks (<= 10 rows): 160 -> 256 columns at T = 512, 80 -> 128
-// at T = 256, so the CTAs an SM can hold never exceed its 512 columns and an
-// allocation never waits.
+// TMEM columns per CTA: T / 128 warps share each lane quadrant, kRowCols
+// columns per row of their blocks (<= 10 rows): 480 -> 512 columns at T = 512,
+// 240 -> 256 at T = 256, so the CTAs an SM can hold never exceed its 512
+// columns and an allocation never waits.
 template <int T>
 constexpr unsigned tmem_cols() {
-  return T == 512 ? 256u : 128u;
+  return T == 512 ? 512u : 256u;
 }
+// Tensor-memory columns per block row: 4 residuals, the exit coefficients of
+// the two column pairs, the inflow coefficient from above (twice) and 2 spare.
+constexpr unsigned kRowCols = 12;
 // Fixed strides of the edge arrays (per parity):
 //  - columns [2 sides][QR][T + 1] float2: the left (side 0) and right (side 1)
 //    column of block t, row pair r; entry T (kZero) is a zero slot;
@@ -181,6 +189,32 @@ __device__ __forceinline__ void tmem_ld4_wait(Tmem4& v, float2& a, float2& b) {
   a = make_float2(__uint_as_float(v.r0), __uint_as_float(v.r1));
   b = make_float2(__uint_as_float(v.r2), __uint_as_float(v.r3));
 }
+// Row r's residuals, exit coefficients and inflow-from-above coefficient
+// (three 4-column loads, waited for together).
+struct Tmem2 {
+  unsigned r0, r1;
+};
+struct Tmem12 {
+  Tmem4 r, d;
+  Tmem2 c;
+};
+__device__ __forceinline__ void tmem_ld12_issue(unsigned taddr, Tmem12& v) {
+  tmem_ld4_issue(taddr, v.r);
+  tmem_ld4_issue(taddr + 4u, v.d);
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+               : "=r"(v.c.r0), "=r"(v.c.r1) : "r"(taddr + 8u) : "memory");
+}
+__device__ __forceinline__ void tmem_ld12_wait(Tmem12& v, float2& rA, float2& rB, float2& dA, float2& dB,
+                                               float2& cup) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v.r.r0), "+r"(v.r.r1), "+r"(v.r.r2), "+r"(v.r.r3), "+r"(v.d.r0), "+r"(v.d.r1),
+                 "+r"(v.d.r2), "+r"(v.d.r3), "+r"(v.c.r0), "+r"(v.c.r1)::"memory");
+  rA = make_float2(__uint_as_float(v.r.r0), __uint_as_float(v.r.r1));
+  rB = make_float2(__uint_as_float(v.r.r2), __uint_as_float(v.r.r3));
+  dA = make_float2(__uint_as_float(v.d.r0), __uint_as_float(v.d.r1));
+  dB = make_float2(__uint_as_float(v.d.r2), __uint_as_float(v.d.r3));
+  cup = make_float2(__uint_as_float(v.c.r0), __uint_as_float(v.c.r1));
+}
 __device__ __forceinline__ void tmem_st4(unsigned taddr, float2 a, float2 b) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
                "r"(__float_as_uint(a.x)), "r"(__float_as_uint(a.y)), "r"(__float_as_uint(b.x)),
@@ -274,7 +308,7 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   tmem_fence_after();
   // This thread's residuals: lane 32 (warp % 4) + lane, columns
   // (warp / 4) 4 NR + 4 r .. + 3 for row r of its block.
-  const unsigned tres = tmem_base + ((32u * (unsigned)(warp & 3)) << 16) + (unsigned)(warp >> 2) * 8u * kQR;
+  const unsigned tres = tmem_base + ((32u * (unsigned)(warp & 3)) << 16) + (unsigned)(warp >> 2) * kRowCols * 2u * kQR;
 
   // Observation entries: (member q, register slot, time) of the states this
   // thread holds, in member order (= time order).  Two passes: count, then
@@ -374,7 +408,15 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   S[NR][0] = S[NR][1] = v_make(0.0f, 0.0f);
   // Residuals start at zero.
 #pragma unroll
-  for (int r = 0; r < NR; ++r) tmem_st4(tres + 4u * r, v_make(0.0f, 0.0f), v_make(0.0f, 0.0f));
+  for (int r = 0; r < NR; ++r) {
+    // Row r's coefficients, as the update formed them every jump before.
+    const float fr = (float)(pb + r);
+    const float2 fp2 = v_make(fr, fr);
+    tmem_st4(tres + kRowCols * r, v_make(0.0f, 0.0f), v_make(0.0f, 0.0f));
+    tmem_st4(tres + kRowCols * r + 4u, v_fma(c_ngp, fp2, d0A), v_fma(c_ngp, fp2, d0B));  // -e_{m,p}
+    const float2 cu = v_fma(c_gp, fp2, c_gp);  // gamma_p (p+1) from p+1
+    tmem_st4(tres + kRowCols * r + 8u, cu, v_make(0.0f, 0.0f));
+  }
   // The row arrays of the neighbouring CTAs: our first row is the row above
   // CTA rank-1 (its array 0), our last row the row below CTA rank+1 (array 1).
   unsigned char* nb_dn = nullptr;
@@ -511,15 +553,8 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     tmem_wait_st();  // the last jump's residual stores are complete
     // The residuals of the next row in this jump's order are loaded while the
     // current row is computed.
-    Tmem4 pre;
-    tmem_ld4_issue(tres + 4u * (DIR == 0 ? 0 : NR - 1), pre);
-    // Row index as a float pair, stepped exactly (integers below 2^24).
-    float2 fp;
-    {
-      const float f0 = (float)opaque(pb + (DIR == 0 ? 0 : NR - 1));
-      fp = v_make(f0, f0);
-    }
-    const float2 fstep = DIR == 0 ? v_make(1.0f, 1.0f) : v_make(-1.0f, -1.0f);
+    Tmem12 pre;
+    tmem_ld12_issue(tres + kRowCols * (DIR == 0 ? 0 : NR - 1), pre);
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
       const int r = DIR == 0 ? i : NR - 1 - i;
@@ -553,10 +588,9 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
       const float lin = (r & 1) ? lp.y : lp.x;
       const float rin = (r & 1) ? rp.y : rp.x;
       float2 rA, rB;  // residuals of row r
-      tmem_ld4_wait(pre, rA, rB);
-      if (i + 1 < NR) tmem_ld4_issue(tres + 4u * (DIR == 0 ? r + 1 : r - 1), pre);
-      const float2 dA = v_fma(c_ngp, fp, d0A), dB = v_fma(c_ngp, fp, d0B);  // -e_{m,p}
-      const float2 cup = v_fma(c_gp, fp, c_gp);  // gamma_p (p+1) from p+1
+      float2 dA, dB, cup;  // -e_{m,p} of the two column pairs; gamma_p (p+1) from p+1
+      tmem_ld12_wait(pre, rA, rB, dA, dB, cup);
+      if (i + 1 < NR) tmem_ld12_issue(tres + kRowCols * (DIR == 0 ? r + 1 : r - 1), pre);
       // t = residual + inflows from the left, right, below and above + exit,
       // and in row P-1 the protein birth k_p m that does not leave it.
       float2 tA = rA;
@@ -599,10 +633,9 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
         yB.y = p3c ? 0.0f : yB.y;
         rB.y = p3c ? 0.0f : rB.y;
       }
-      tmem_st4(tres + 4u * r, rA, rB);
+      tmem_st4(tres + kRowCols * r, rA, rB);
       S[sn][0] = yA;
       S[sn][1] = yB;
-      fp = v_add(fp, fstep);
     }
   };
 
@@ -617,7 +650,7 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     for (int r = 0; r < NR; ++r) {
       const int pr = pb + r;
       float2 rA, rB;
-      tmem_ld4(tres + 4u * r, rA, rB);
+      tmem_ld4(tres + kRowCols * r, rA, rB);
       float b[kQC];
 #pragma unroll
       for (int c = 0; c < kQC; ++c) b[c] = own * __fmul_rn(period, mrna_defect(mrna_col(co, m0 + c, M), co.d, pr));
@@ -631,7 +664,7 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
         }
       rA = v_fma(v_make(b[0], b[2]), ya, rA);
       rB = v_fma(v_make(b[1], b[3]), yb, rB);
-      tmem_st4(tres + 4u * r, rA, rB);
+      tmem_st4(tres + kRowCols * r, rA, rB);
     }
   };
 

@@ -488,11 +488,15 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
       }
     }
   };
-  // Defect correction of the compensated chain after jump k_e (pairs at home);
-  // the period is a multiple of the round length P1.
-  auto defect = [&](int k_e) {
+  // Defect correction of the compensated chain after every p.renorm jumps,
+  // i.e. at the end of every (p.renorm / P1)-th round (pairs at home; the
+  // period is a multiple of the round length).  rleft counts the rounds left
+  // (never reaching zero when the correction is off: K < 2^30).
+  int rleft = (kComp && p.renorm > 0) ? p.renorm / P1 : 0x7fffffff;
+  auto defect = [&]() {
     if constexpr (kComp) {
-      if (p.renorm > 0 && k_e % p.renorm == 0) {
+      if (--rleft == 0) {
+        rleft = p.renorm / P1;
 #pragma unroll
         for (int j = 0; j < QP; ++j) res[j] = __ffma2_rn(cb[j], r[j], res[j]);
       }
@@ -541,7 +545,7 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
   for (int g = 0; g < ngroups; ++g) {
     if (wact) RotSeq<P1, 0, P1>::run(jump_plain);
     else k += P1;
-    defect(k - 1);
+    defect();
     scrub();
     round_end(k - 1);
   }
@@ -562,7 +566,7 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
     RotSeq<P1, 0, P1>::run(jump_acc);
     const int k_e = k - 1;
     if (k_e >= Kmax) break;
-    defect(k_e);
+    defect();
     scrub();
     if ((k_e + P1) % kChunk1 == 0) cp_async_wait<0>();
     rec_round(k_e + 1, min(Kmax, k_e + P1));

@@ -17,9 +17,9 @@
 // pairs) and the two gene states of a column sit in the same slot of the two
 // rows.  Only a thread's first and last column need another thread's value:
 // shuffles inside a warp, a double-buffered shared-memory slot and a named
-// barrier of the chain warps between warps.  The pairs rotate through QP + 1 register slots
-// (pair j of rho_k is written over pair j - 1 of rho_{k-1}, its last reader),
-// so an in-place jump copies no register.
+// barrier of the chain warps between warps.  The pairs rotate through QP + 1
+// register slots (pair j of rho_k is written over pair j - 1 of rho_{k-1},
+// its last reader), so an in-place jump copies no register.
 //
 // Arithmetic per state is the shared-memory kernel's compensated jump
 // (stencil.cu; chain_common.cuh) in the same order -- residual, inflow from
@@ -37,10 +37,11 @@
 // the chain warps fill the other half.  Two mbarriers per half hand it over
 // (full: the chain threads have written it; empty: the reducers have read
 // it); every wait on them is bounded (p.wait_limit polls, MJP_OPT_WAIT_LIMIT)
-// and reports kStatusTimeout when it runs out.  The reducers also stage the weights of Algorithm 2 (FP64 in the
-// planner, rounded to FP32) from the planner's arena 32 jumps at a time, one
-// chunk ahead; a window without a stored copy runs the recurrence P_k =
-// P_{k-1} x / k from P_L (FP64) while its chunk is staged.
+// and reports kStatusTimeout when it runs out.  The reducers also stage the
+// weights of Algorithm 2 (FP64 in the planner, rounded to FP32) from the
+// planner's arena 32 jumps at a time, one chunk ahead; a window without a
+// stored copy runs the recurrence P_k = P_{k-1} x / k from P_L (FP64) while
+// its chunk is staged.
 #include <algorithm>
 #include <type_traits>
 
