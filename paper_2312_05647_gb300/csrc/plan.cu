@@ -107,6 +107,81 @@ __device__ bool window_bounds(const PlanParams& p, double x, int64_t& L, int64_t
   return true;
 }
 
+// Weights of the paper's rule, ratios to w_m = 1 at the mode m = floor(x):
+// upward w_k = w_{k-1} x / k over (m, R], downward w_k = w_{k+1} (k+1) / x
+// over [L, m).  Each lane forms the running product of a run of kRun
+// consecutive terms, one warp-wide product scan joins the runs, so a weight
+// costs two multiplications besides its term (x times the reciprocal of k, or
+// k + 1 times the reciprocal of x).  Returns the window sum W over [L, R]
+// (plain FP64 sum: ~1e3 positive terms, relative error ~1e-13), the tail
+// sum over (K, R] and w_L; the unnormalised weights of [L, K] go to `put`
+// when `store`.
+constexpr int kRun = 8;
+template <class Put>
+__device__ void paper_weights(double x, int64_t L, int64_t K, int64_t m, int64_t R, int lane, bool store,
+                              Put& put, double& W, double& tailsum, double& wL) {
+  double sw = lane == 0 ? 1.0 : 0.0, st = 0.0, wl = 0.0;
+  if (store && lane == 0) put(m, 1.0);
+  double carry = 1.0;
+  for (int64_t base = m + 1; base <= R; base += 32 * kRun) {
+    const int64_t k0 = base + (int64_t)lane * kRun;
+    double loc[kRun], pr = 1.0;
+#pragma unroll
+    for (int b = 0; b < kRun; ++b) {
+      const int64_t k = k0 + b;
+      const double term = k <= R ? __dmul_rn(x, __drcp_rn((double)k)) : 1.0;
+      pr = __dmul_rn(pr, term);
+      loc[b] = pr;
+    }
+    const double incl = warp_incl_prod(pr, lane);
+    double excl = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) excl = 1.0;
+    const double pre = __dmul_rn(carry, excl);
+#pragma unroll
+    for (int b = 0; b < kRun; ++b) {
+      const int64_t k = k0 + b;
+      if (k <= R) {
+        const double w = __dmul_rn(pre, loc[b]);
+        sw += w;
+        if (k > K) st += w;
+        else if (store) put(k, w);
+      }
+    }
+    carry = __shfl_sync(kFull, __dmul_rn(pre, pr), 31);
+  }
+  const double invx = __drcp_rn(x);
+  carry = 1.0;
+  for (int64_t base = m - 1; base >= L; base -= 32 * kRun) {
+    const int64_t k0 = base - (int64_t)lane * kRun;
+    double loc[kRun], pr = 1.0;
+#pragma unroll
+    for (int b = 0; b < kRun; ++b) {
+      const int64_t k = k0 - b;
+      const double term = k >= L ? __dmul_rn((double)(k + 1), invx) : 1.0;
+      pr = __dmul_rn(pr, term);
+      loc[b] = pr;
+    }
+    const double incl = warp_incl_prod(pr, lane);
+    double excl = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) excl = 1.0;
+    const double pre = __dmul_rn(carry, excl);
+#pragma unroll
+    for (int b = 0; b < kRun; ++b) {
+      const int64_t k = k0 - b;
+      if (k >= L) {
+        const double w = __dmul_rn(pre, loc[b]);
+        sw += w;
+        if (store) put(k, w);
+        if (k == L) wl = w;
+      }
+    }
+    carry = __shfl_sync(kFull, __dmul_rn(pre, pr), 31);
+  }
+  W = warp_sum(sw);
+  tailsum = warp_sum(st);
+  wL = (L == m) ? 1.0 : warp_sum(wl);  // w_L sits in exactly one lane
+}
+
 // Plan one time on one warp.  doff: the arena offset reserved for this
 // window's weights (paper's rule), or -1.
 __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst, int lane, long long doff_in) {
@@ -151,10 +226,33 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
     if (p.arena_fp64) reinterpret_cast<double*>(p.arena)[doff + (k - L)] = w;
     else reinterpret_cast<float*>(p.arena)[doff + (k - L)] = (float)w;
   };
-  if (dstore && lane == 0) put_raw(m, 1.0);
+  if (p.trunc_mode == MJP_TRUNC_PAPER) {
+    double W, ts, wL;
+    paper_weights(x, L, K, m, R, lane, dstore, put_raw, W, ts, wL);
+    r.L = L;
+    r.K = K;
+    r.PL = wL / W;
+    r.tail = ts / W;
+    r.woff = -1;
+    if (dstore) {
+      r.woff = (int64_t)doff;
+      __syncwarp();  // every lane's raw weights are visible to the lane that scales them
+      const double invW = __ddiv_rn(1.0, W);
+      for (int64_t j = lane; j < dsize; j += 32) {
+        double v = p.arena_fp64 ? reinterpret_cast<double*>(p.arena)[doff + j]
+                                : (double)reinterpret_cast<float*>(p.arena)[doff + j];
+        v = __dmul_rn(v, invW);
+        if (L + j == K) v = v + r.tail;
+        if (p.arena_fp64) reinterpret_cast<double*>(p.arena)[doff + j] = v;
+        else reinterpret_cast<float*>(p.arena)[doff + j] = (float)v;
+      }
+    }
+    if (lane == 0) *dst = r;
+    return;
+  }
 
-  // Upward from the mode: w_k = w_{k-1} x / k, w_m = 1.
-  Kahan sum, tailsum;
+  // Tolerance rule.  Upward from the mode: w_k = w_{k-1} x / k, w_m = 1.
+  Kahan sum;
   if (lane == 0) sum.add(1.0);
   double carry = 1.0;
   for (int64_t base = m + 1; base <= R; base += 32) {
@@ -162,11 +260,7 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
     double term = (k <= R) ? __ddiv_rn(x, (double)k) : 1.0;
     double w = __dmul_rn(warp_incl_prod(term, lane), carry);
     carry = __shfl_sync(kFull, w, 31);
-    if (k <= R) {
-      sum.add(w);
-      if (p.trunc_mode == MJP_TRUNC_PAPER && k > K) tailsum.add(w);
-      if (dstore && k <= K) put_raw(k, w);
-    }
+    if (k <= R) sum.add(w);
   }
   double wR = carry;
   // Downward from the mode: w_k = w_{k+1} (k+1) / x.
@@ -177,10 +271,7 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
     double term = (k >= L) ? __ddiv_rn((double)(k + 1), x) : 1.0;
     double w = __dmul_rn(warp_incl_prod(term, lane), carry);
     carry = __shfl_sync(kFull, w, 31);
-    if (k >= L) {
-      sum.add(w);
-      if (dstore) put_raw(k, w);
-    }
+    if (k >= L) sum.add(w);
     if (k == L) wL = w;
   }
   double W = warp_sum(sum.s) - warp_sum(sum.c);
@@ -188,9 +279,7 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
   wL = (L == m) ? 1.0 : warp_sum(wL);
 
   double tail;
-  if (p.trunc_mode == MJP_TRUNC_PAPER) {
-    tail = (warp_sum(tailsum.s) - warp_sum(tailsum.c)) / W;
-  } else {
+  {
     // Smallest K with sum_{j>K} w_j <= tol W: walk down from R with suffix sums.
     double thr = p.tol * W;
     double S = 0.0;   // sum_{j > base}
@@ -237,24 +326,9 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
   r.tail = tail;
   r.woff = -1;
   // P_L..P_K (the tail folded into P_K) in the arena, so the chain reads the
-  // weights instead of running the recurrence: the stored unnormalised
-  // weights scaled by 1 / W (paper's rule), or (tolerance rule, K known only
-  // now) the same product scans run again.
-  if (direct) {
-    if (dstore) {
-      r.woff = (int64_t)doff;
-      __syncwarp();  // every lane's raw weights are visible to the lane that scales them
-      const double invW = __ddiv_rn(1.0, W);
-      for (int64_t j = lane; j < dsize; j += 32) {
-        double v = p.arena_fp64 ? reinterpret_cast<double*>(p.arena)[doff + j]
-                                : (double)reinterpret_cast<float*>(p.arena)[doff + j];
-        v = __dmul_rn(v, invW);
-        if (L + j == K) v = v + tail;
-        if (p.arena_fp64) reinterpret_cast<double*>(p.arena)[doff + j] = v;
-        else reinterpret_cast<float*>(p.arena)[doff + j] = (float)v;
-      }
-    }
-  } else if (p.arena) {
+  // weights instead of running the recurrence (K is known only now: the same
+  // product scans run again).
+  if (p.arena) {
     const int64_t size = K - L + 1;
     unsigned long long off = 0;
     if (lane == 0) off = atomicAdd(p.arena_used, (unsigned long long)size);
