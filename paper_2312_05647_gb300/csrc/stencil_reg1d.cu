@@ -390,6 +390,15 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
   // rho*_i += w_{i,k} rho_k for the active times [l, hgh] of jump k (Kahan in
   // FP32), the result written out at k = K_i for the states this lane owns;
   // rho_k's pairs at rotation O.
+  // Bit 2 j (2 j + 1): state y0 + j (y0 + QP + j) of this lane is owned by
+  // it and lies in this CTA's segment, so its outputs are its to write.
+  unsigned omask = 0;
+#pragma unroll
+  for (int j = 0; j < QP; ++j) {
+    const int ya = y0 + j, yc = y0 + QP + j;
+    if (owned_y(ya) && xw + ya >= h && xw + ya < h + own) omask |= 1u << (2 * j);
+    if (owned_y(yc) && xw + yc >= h && xw + yc < h + own) omask |= 2u << (2 * j);
+  }
   auto accumulate = [&](int k, int l, int hgh, auto OC) {
     constexpr int O = decltype(OC)::value;
     for (int i = l; i <= hgh; ++i) {
@@ -401,22 +410,24 @@ __global__ void __launch_bounds__(kMaxT, 1) chain_reg1d_kernel(const ChainParams
         const int slot = (i * QP + j) * nthr + tid;
         const T2 v = r[(j + O) % P1];
         const int ya = y0 + j, yc = y0 + QP + j;
-        const bool oa = owned_y(ya) && xw + ya >= h && xw + ya < h + own;
-        const bool oc = owned_y(yc) && xw + yc >= h && xw + yc < h + own;
+        const bool oa = (omask >> (2 * j)) & 1u, oc = (omask >> (2 * j + 1)) & 1u;
         if (sizeof(T) == 4) {
+          // Kahan step of both states as FP32x2 operations, each lane rounded
+          // as the scalar step: y = w v - c, t = s + y, c = (t - s) - y.
+          const float2 w2 = make_float2((float)w, (float)w), m1 = make_float2(-1.0f, -1.0f);
+          const float2 vf = make_float2((float)v.x, (float)v.y);
           float2 s, cc;
           if (first) {
-            s = make_float2(__fmul_rn((float)w, (float)v.x), __fmul_rn((float)w, (float)v.y));
+            s = __fmul2_rn(w2, vf);
             cc = make_float2(0.0f, 0.0f);
           } else {
             const T2 s0v = acc_s[slot];
             s = make_float2((float)s0v.x, (float)s0v.y);
             cc = acc_c[slot];
-            const float yx = __fsub_rn(__fmul_rn((float)w, (float)v.x), cc.x);
-            const float yy = __fsub_rn(__fmul_rn((float)w, (float)v.y), cc.y);
-            const float tx = __fadd_rn(s.x, yx), ty = __fadd_rn(s.y, yy);
-            cc = make_float2(__fsub_rn(__fsub_rn(tx, s.x), yx), __fsub_rn(__fsub_rn(ty, s.y), yy));
-            s = make_float2(tx, ty);
+            const float2 y = __ffma2_rn(cc, m1, __fmul2_rn(w2, vf));
+            const float2 t = __fadd2_rn(s, y);
+            cc = __ffma2_rn(y, m1, __ffma2_rn(s, m1, t));
+            s = t;
           }
           if (last) {
             if (oa) o[ya] = (T)__fsub_rn(s.x, cc.x);
