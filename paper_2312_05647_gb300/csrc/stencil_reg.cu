@@ -135,14 +135,25 @@ template <int NR, int ROT>
 __device__ __forceinline__ float pick(const float2 (&S)[NR + 1][2], int slot) {
   const bool c1 = slot & 1, c2 = slot & 2;
   const int r = slot >> 2;
-  float v = 0.0f;
+  // Column of every row (independent selections), then a binary tree over
+  // the bits of the row index (depth log2 NR instead of NR).
+  float x[16];
 #pragma unroll
-  for (int q = 0; q < NR; ++q) {
-    const float2 a = S[rslot<NR>(q, ROT)][0], b = S[rslot<NR>(q, ROT)][1];
-    const float x = c2 ? (c1 ? b.y : a.y) : (c1 ? b.x : a.x);
-    v = (r == q) ? x : v;
+  for (int q = 0; q < 16; ++q) {
+    if (q < NR) {
+      const float2 a = S[rslot<NR>(q < NR ? q : 0, ROT)][0], b = S[rslot<NR>(q < NR ? q : 0, ROT)][1];
+      x[q] = c2 ? (c1 ? b.y : a.y) : (c1 ? b.x : a.x);
+    } else {
+      x[q] = 0.0f;
+    }
   }
-  return v;
+#pragma unroll
+  for (int bit = 0; bit < 4; ++bit) {
+    const bool hi = (r >> bit) & 1;
+#pragma unroll
+    for (int q = 0; q < (16 >> (bit + 1)); ++q) x[q] = hi ? x[2 * q + 1] : x[2 * q];
+  }
+  return x[0];
 }
 
 // The value of v, hidden from the optimiser: quantities derived from it inside
