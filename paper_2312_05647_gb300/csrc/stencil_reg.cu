@@ -485,6 +485,15 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     while (h + 1 < nt && t_L[h + 1] <= k) ++h;
   };
   advance(0, lo, hi);
+  // First jump at which the active range [lo, hi] changes (a window ends or
+  // the next one starts); the per-jump check is one comparison.
+  auto next_change = [&](int l, int h) -> int {
+    int kn = 0x7fffffff;
+    if (l < nt) kn = min(kn, t_K[l] + 1);
+    if (h + 1 < nt) kn = min(kn, t_L[h + 1]);
+    return kn;
+  };
+  int knext = next_change(lo, hi);
   // Stage the stored weights of jumps [k0, k0 + kChunk) of every window into
   // the ring (slot j % kStage), spread over all threads.
   auto stage_chunk = [&](int k0) {
@@ -707,7 +716,10 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
       dleft = p.renorm;
       defect_fix(std::integral_constant<int, ROT>{});
     }
-    advance(k, lo, hi);
+    if (k >= knext) {
+      advance(k, lo, hi);
+      knext = next_change(lo, hi);
+    }
     accumulate(k, lo, hi, std::integral_constant<int, ROT>{});
     if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
     if (wwarp && any_rec && k + 1 <= Kmax) rec_step(k + 1);
