@@ -223,6 +223,7 @@ int arena_prepare(mjp_model* m, const double* host_theta, int B, const double* t
   pp.arena_used = m->d_arena_ctl.as<unsigned long long>();
   pp.arena_over = reinterpret_cast<int*>(m->d_arena_ctl.as<char>() + 8);
   pp.arena_fp64 = m->precision == MJP_FP64 ? 1 : 0;
+  pp.fp64_weights = pp.arena_fp64;
   return MJP_OK;
 }
 
@@ -247,6 +248,7 @@ int csr_run(mjp_model* m, const void* rho0, const double* sorted_times, int nt, 
   pp.kind = MJP_CSR; pp.M = 1; pp.P = 1; pp.N = n; pp.ntheta = 0; pp.theta = nullptr; pp.B = 1;
   pp.ntimes = nt; pp.times = m->d_times.as<double>();
   pp.trunc_mode = trunc_mode; pp.tol = tol; pp.omega_factor = 1.1; pp.omega_fixed = m->csr_omega;
+  pp.fp64_weights = m->precision == MJP_FP64 ? 1 : 0;
   pp.kcap = m->kcap; pp.win = m->d_win.as<Win>(); pp.info = m->d_info.as<JobInfo>();
   pp.status = m->d_status.as<int>();
   if ((rc = mark(m, 0, s))) return rc;

@@ -267,6 +267,7 @@ int enqueue(mjp_batch* b, void* out, cudaStream_t s) {
   pp.arena_used = b->d_arena_ctl.as<unsigned long long>();
   pp.arena_over = reinterpret_cast<int*>(b->d_arena_ctl.as<char>() + 8);
   pp.arena_fp64 = b->precision == MJP_FP64 ? 1 : 0;
+  pp.fp64_weights = pp.arena_fp64;
   MJP_CUDA(cudaMemsetAsync(b->d_arena_ctl.p, 0, 16, s));
   MJP_CUDA(launch_plan(pp, s));
   MJP_CUDA(cudaEventRecord(b->ev_fork, s));

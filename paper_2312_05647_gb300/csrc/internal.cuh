@@ -75,6 +75,9 @@ struct PlanParams {
   unsigned long long* arena_used;   // element counter (zeroed before the planner)
   int* arena_over;
   int arena_fp64;                   // element type: 1 = double, 0 = float
+  // 1: the chain is FP64 (weights formed to FP64 precision); 0: FP32 chain
+  // (weights formed in float-float on the FP32 pipe).
+  int fp64_weights;
 };
 
 // Chain inputs (stencil models).

@@ -107,18 +107,145 @@ __device__ bool window_bounds(const PlanParams& p, double x, int64_t& L, int64_t
   return true;
 }
 
+// Float-float numbers (hi + lo, |lo| <= ulp(hi) / 2: ~48 significant bits)
+// on the FP32 pipe, which GB300 runs 64 times faster than its FP64 pipe.
+// Error-free transformations: TwoSum (Knuth), FastTwoSum (Dekker, |a| >= |b|)
+// and TwoProd with a fused multiply-add; every operation explicitly rounded.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_from(double d) {
+  const float hi = __double2float_rn(d);
+  return FF{hi, __double2float_rn(d - (double)hi)};
+}
+__device__ __forceinline__ double ff_to(FF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff_fast_two_sum(p, e);
+}
+// a times an integer-valued float c (exact in FP32).
+__device__ __forceinline__ FF ff_mul_int(FF a, float c) {
+  const float p = __fmul_rn(a.hi, c);
+  float e = __fmaf_rn(a.hi, c, -p);
+  e = __fmaf_rn(a.lo, c, e);
+  return ff_fast_two_sum(p, e);
+}
+// 1 / c for an integer-valued float c: r0 rounded, plus r0 times the exact
+// residual 1 - c r0.
+__device__ __forceinline__ FF ff_rcp_int(float c) {
+  const float r0 = __frcp_rn(c);
+  const float e = __fmaf_rn(-c, r0, 1.0f);
+  return ff_fast_two_sum(r0, __fmul_rn(r0, e));
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return ff_fast_two_sum(s, e);
+}
+__device__ __forceinline__ FF ff_shfl_up(FF a, int d) {
+  return FF{__shfl_up_sync(kFull, a.hi, d), __shfl_up_sync(kFull, a.lo, d)};
+}
+
 // Weights of the paper's rule, ratios to w_m = 1 at the mode m = floor(x):
 // upward w_k = w_{k-1} x / k over (m, R], downward w_k = w_{k+1} (k+1) / x
 // over [L, m).  Each lane forms the running product of a run of kRun
-// consecutive terms, one warp-wide product scan joins the runs, so a weight
-// costs two multiplications besides its term (x times the reciprocal of k, or
-// k + 1 times the reciprocal of x).  Returns the window sum W over [L, R]
-// (plain FP64 sum: ~1e3 positive terms, relative error ~1e-13), the tail
-// sum over (K, R] and w_L; the unnormalised weights of [L, K] go to `put`
-// when `store`.
+// consecutive terms, one warp-wide product scan joins the runs.  The
+// products run in float-float (relative error ~1e-14 over a window of ~10^4
+// terms: far below the FP32 weights the chains read and the 1e-12 of the FP64
+// chains are served by paper_weights64), and so do the per-lane sums.  Returns the window sum W over [L, R],
+// the tail sum over (K, R] and w_L; the unnormalised weights of [L, K] go to
+// `put` when `store`.
 constexpr int kRun = 8;
+__device__ __forceinline__ FF ff_warp_incl_prod(FF v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const FF t = ff_shfl_up(v, o);
+    if (lane >= o) v = ff_mul(v, t);
+  }
+  return v;
+}
 template <class Put>
 __device__ void paper_weights(double x, int64_t L, int64_t K, int64_t m, int64_t R, int lane, bool store,
+                              Put& put, double& W, double& tailsum, double& wL) {
+  FF sw{lane == 0 ? 1.0f : 0.0f, 0.0f}, st{0.0f, 0.0f}, wl{0.0f, 0.0f};
+  if (store && lane == 0) put(m, FF{1.0f, 0.0f});
+  const FF xf = ff_from(x), invx = ff_from(1.0 / x);
+  FF carry{1.0f, 0.0f};
+  for (int64_t base = m + 1; base <= R; base += 32 * kRun) {
+    const int64_t k0 = base + (int64_t)lane * kRun;
+    FF loc[kRun], pr{1.0f, 0.0f};
+#pragma unroll
+    for (int b = 0; b < kRun; ++b) {
+      const int64_t k = k0 + b;
+      const FF term = k <= R ? ff_mul(xf, ff_rcp_int((float)k)) : FF{1.0f, 0.0f};
+      pr = ff_mul(pr, term);
+      loc[b] = pr;
+    }
+    const FF incl = ff_warp_incl_prod(pr, lane);
+    FF excl = ff_shfl_up(incl, 1);
+    if (lane == 0) excl = FF{1.0f, 0.0f};
+    const FF pre = ff_mul(carry, excl);
+#pragma unroll
+    for (int b = 0; b < kRun; ++b) {
+      const int64_t k = k0 + b;
+      if (k <= R) {
+        const FF w = ff_mul(pre, loc[b]);
+        sw = ff_add(sw, w);
+        if (k > K) st = ff_add(st, w);
+        else if (store) put(k, w);
+      }
+    }
+    const FF last = ff_mul(pre, pr);
+    carry = FF{__shfl_sync(kFull, last.hi, 31), __shfl_sync(kFull, last.lo, 31)};
+  }
+  carry = FF{1.0f, 0.0f};
+  for (int64_t base = m - 1; base >= L; base -= 32 * kRun) {
+    const int64_t k0 = base - (int64_t)lane * kRun;
+    FF loc[kRun], pr{1.0f, 0.0f};
+#pragma unroll
+    for (int b = 0; b < kRun; ++b) {
+      const int64_t k = k0 - b;
+      const FF term = k >= L ? ff_mul_int(invx, (float)(k + 1)) : FF{1.0f, 0.0f};
+      pr = ff_mul(pr, term);
+      loc[b] = pr;
+    }
+    const FF incl = ff_warp_incl_prod(pr, lane);
+    FF excl = ff_shfl_up(incl, 1);
+    if (lane == 0) excl = FF{1.0f, 0.0f};
+    const FF pre = ff_mul(carry, excl);
+#pragma unroll
+    for (int b = 0; b < kRun; ++b) {
+      const int64_t k = k0 - b;
+      if (k >= L) {
+        const FF w = ff_mul(pre, loc[b]);
+        sw = ff_add(sw, w);
+        if (store) put(k, w);
+        if (k == L) wl = w;
+      }
+    }
+    const FF last = ff_mul(pre, pr);
+    carry = FF{__shfl_sync(kFull, last.hi, 31), __shfl_sync(kFull, last.lo, 31)};
+  }
+  W = warp_sum(ff_to(sw));
+  tailsum = warp_sum(ff_to(st));
+  wL = (L == m) ? 1.0 : warp_sum(ff_to(wl));  // w_L sits in exactly one lane
+}
+
+// The same in FP64 (x / k as x times the reciprocal of k), for the FP64
+// chains, whose 1e-12 agreement with the oracle needs weights (and P_L, the
+// start of the recurrence of a window without a stored copy) to FP64
+// precision.
+template <class Put>
+__device__ void paper_weights64(double x, int64_t L, int64_t K, int64_t m, int64_t R, int lane, bool store,
                               Put& put, double& W, double& tailsum, double& wL) {
   double sw = lane == 0 ? 1.0 : 0.0, st = 0.0, wl = 0.0;
   if (store && lane == 0) put(m, 1.0);
@@ -222,13 +349,17 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
   const int64_t dsize = K - L + 1;
   const unsigned long long doff = doff_in >= 0 ? (unsigned long long)doff_in : 0ull;
   const bool dstore = direct && doff_in >= 0;
-  auto put_raw = [&](int64_t k, double w) {
+  // Raw weights: float-float for FP32 chains, FP64 for FP64 chains (whose
+  // arena holds doubles).
+  auto put_raw = [&](int64_t k, FF w) { reinterpret_cast<float*>(p.arena)[doff + (k - L)] = w.hi; };
+  auto put_raw64 = [&](int64_t k, double w) {
     if (p.arena_fp64) reinterpret_cast<double*>(p.arena)[doff + (k - L)] = w;
     else reinterpret_cast<float*>(p.arena)[doff + (k - L)] = (float)w;
   };
   if (p.trunc_mode == MJP_TRUNC_PAPER) {
     double W, ts, wL;
-    paper_weights(x, L, K, m, R, lane, dstore, put_raw, W, ts, wL);
+    if (p.fp64_weights || p.arena_fp64) paper_weights64(x, L, K, m, R, lane, dstore, put_raw64, W, ts, wL);
+    else paper_weights(x, L, K, m, R, lane, dstore, put_raw, W, ts, wL);
     r.L = L;
     r.K = K;
     r.PL = wL / W;
@@ -238,13 +369,21 @@ __device__ void plan_time(const PlanParams& p, double omega, double t, Win* dst,
       r.woff = (int64_t)doff;
       __syncwarp();  // every lane's raw weights are visible to the lane that scales them
       const double invW = __ddiv_rn(1.0, W);
-      for (int64_t j = lane; j < dsize; j += 32) {
-        double v = p.arena_fp64 ? reinterpret_cast<double*>(p.arena)[doff + j]
-                                : (double)reinterpret_cast<float*>(p.arena)[doff + j];
-        v = __dmul_rn(v, invW);
-        if (L + j == K) v = v + r.tail;
-        if (p.arena_fp64) reinterpret_cast<double*>(p.arena)[doff + j] = v;
-        else reinterpret_cast<float*>(p.arena)[doff + j] = (float)v;
+      if (p.arena_fp64) {
+        double* a = reinterpret_cast<double*>(p.arena) + doff;
+        for (int64_t j = lane; j < dsize; j += 32) {
+          double v = __dmul_rn(a[j], invW);
+          if (L + j == K) v = v + r.tail;
+          a[j] = v;
+        }
+      } else {  // FP32 weights scaled in float-float on the FP32 pipe
+        float* a = reinterpret_cast<float*>(p.arena) + doff;
+        const FF invWf = ff_from(invW);
+        for (int64_t j = lane; j < dsize; j += 32) {
+          FF v = ff_mul(FF{a[j], 0.0f}, invWf);
+          if (L + j == K) v = ff_add(v, ff_from(r.tail));
+          a[j] = __fadd_rn(v.hi, v.lo);
+        }
       }
     }
     if (lane == 0) *dst = r;
