@@ -234,6 +234,50 @@ __device__ __forceinline__ void tmem_st4(unsigned taddr, float2 a, float2 b) {
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// Hand-over of the block rows that cross a CTA boundary.  A sending thread
+// writes its 16 bytes into the neighbour CTA's row array with st.async, which
+// counts them on that CTA's hand-over mbarrier (one per direction and jump
+// parity); the receiving threads wait for the phase of the jump they need,
+// and the first of them re-arms the barrier with the bytes it expects two
+// jumps later.  Addresses are 32-bit shared-memory addresses (mapa gives the
+// neighbour's copy of a variable).
+__device__ __forceinline__ unsigned cluster_addr(unsigned local, int rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void hbar_init(unsigned a) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void hbar_arm(unsigned a, unsigned bytes) {
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+// At most `polls` tests of the phase of parity ph (none when polls is 0):
+// false when the phase has not completed by then.
+__device__ __forceinline__ bool hbar_wait(unsigned a, unsigned ph, long long polls) {
+  for (long long i = 0; i < polls; ++i) {
+    unsigned ok;
+    asm volatile("{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok) : "r"(a), "r"(ph) : "memory");
+    if (ok) return true;
+    if (i >= 16) __nanosleep(32);
+  }
+  return false;
+}
+__device__ __forceinline__ void st_async16(unsigned raddr, float2 a, float2 b, unsigned rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                   raddr),
+               "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "r"(rbar)
+               : "memory");
+}
+// Plain store into a neighbour CTA (ordered by a later cluster barrier).
+__device__ __forceinline__ void st_cluster16(unsigned raddr, float2 a, float2 b) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(raddr), "f"(a.x), "f"(a.y), "f"(b.x),
+               "f"(b.y)
+               : "memory");
+}
+
 // Exclusive prefix sum of v over the block (blockDim <= 1024).
 __device__ int block_exclusive_scan(int v, int* wsum) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -259,6 +303,9 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int wsum[32];
   __shared__ unsigned tmem_base;
+  // Hand-over barriers [direction][jump parity]: 0 counts the row from the
+  // CTA below (rank - 1), 1 the row from the CTA above (rank + 1).
+  __shared__ __align__(8) unsigned long long hbar[2][2];
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
@@ -357,7 +404,28 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     float4* e = reinterpret_cast<float4*>(smem + L.edge);
     for (int q = tid; q < (int)(2 * G::par_bytes / 16); q += blockDim.x) e[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  // Every CTA's edge arrays are zeroed before any neighbour writes into them.
+  // The hand-over barriers of this CTA, armed for their first phase (jump 1
+  // for parity 1, jump 2 for parity 0; the rows of rho_0 cross by plain
+  // stores and a cluster barrier).  Every CTA holds at least one row block,
+  // so the neighbour's boundary row block sends one 16-byte row per column
+  // quad, NQ in all, every jump.
+  const unsigned hb = (unsigned)__cvta_generic_to_shared(&hbar[0][0]);
+  const unsigned hbytes = 16u * (unsigned)NQ;
+  if (C > 1 && tid == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) hbar_init(hb + 8u * i);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (rank > 0) {
+      hbar_arm(hb, hbytes);
+      hbar_arm(hb + 8u, hbytes);
+    }
+    if (rank + 1 < C) {
+      hbar_arm(hb + 16u, hbytes);
+      hbar_arm(hb + 24u, hbytes);
+    }
+  }
+  // Every CTA's edge arrays are zeroed and its barriers set up before any
+  // neighbour writes into them.
   if (C > 1) cluster.sync();
   else __syncthreads();
 
@@ -429,18 +497,35 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     tmem_st4(tres + kRowCols * r + 8u, cu, v_make(0.0f, 0.0f));
   }
   // The row arrays of the neighbouring CTAs: our first row is the row above
-  // CTA rank-1 (its array 0), our last row the row below CTA rank+1 (array 1).
-  unsigned char* nb_dn = nullptr;
-  unsigned char* nb_up = nullptr;
-  if (C > 1) {
-    if (rank > 0 && rb == 0) nb_dn = cluster.map_shared_rank(E0, rank - 1) + G::row(0) + 16u * (kZero + 1 + qx);
-    if (rank + 1 < C && rb == nrb - 1)
-      nb_up = cluster.map_shared_rank(E0, rank + 1) + G::row(1) + 16u * (kZero + 1 + qx);
+  // CTA rank-1 (its array 0, counted by its barrier from above), our last row
+  // the row below CTA rank+1 (array 1, its barrier from below).  The threads
+  // that send a row are the ones that receive the neighbour's.
+  const bool rx_dn = C > 1 && rank > 0 && rb == 0;
+  const bool rx_up = C > 1 && rank + 1 < C && rb == nrb - 1;
+  unsigned nb_dn = 0, nb_up = 0, nbar_dn = 0, nbar_up = 0;
+  {
+    const unsigned e0 = (unsigned)__cvta_generic_to_shared(E0);
+    if (rx_dn) {
+      nb_dn = cluster_addr(e0 + (unsigned)G::row(0) + 16u * (kZero + 1 + qx), rank - 1);
+      nbar_dn = cluster_addr(hb + 16u, rank - 1);
+    }
+    if (rx_up) {
+      nb_up = cluster_addr(e0 + (unsigned)G::row(1) + 16u * (kZero + 1 + qx), rank + 1);
+      nbar_up = cluster_addr(hb, rank + 1);
+    }
   }
+  // False once one of this thread's hand-over waits has run out: from then on
+  // it neither waits, re-arms nor sends rows to the neighbouring CTAs (so no
+  // barrier sees an arrival or bytes outside the phase it is armed for), and
+  // the chain runs on to its end with the status set.
+  bool hok = true;
   // Edges of the block: the left (c0) and right (c3) columns per row pair,
-  // the first and last rows as (c0, c2, c1, c3).
-  auto publish = [&](int par, auto ROTC) {
+  // the first and last rows as (c0, c2, c1, c3).  The rows for the
+  // neighbouring CTAs go by st.async (counted on their hand-over barrier of
+  // this parity), those of rho_0 (INIT) by plain stores.
+  auto publish = [&](int par, auto ROTC, auto INITC) {
     constexpr int ROT = decltype(ROTC)::value;
+    constexpr bool INIT = decltype(INITC)::value;
     unsigned char* Ep = E0 + (par ? G::par_bytes : 0);
 #pragma unroll
     for (int r = 0; r < kQR; ++r) {
@@ -459,19 +544,17 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     fr[1] = S[sf][1];
     lr[0] = S[sl][0];
     lr[1] = S[sl][1];
-    const size_t po = par ? G::par_bytes : 0;
-    if (nb_dn) {
-      float2* d = reinterpret_cast<float2*>(nb_dn + po);
-      d[0] = S[sf][0];
-      d[1] = S[sf][1];
+    const unsigned po = par ? (unsigned)G::par_bytes : 0u;
+    if (rx_dn) {
+      if (INIT) st_cluster16(nb_dn + po, S[sf][0], S[sf][1]);
+      else if (hok) st_async16(nb_dn + po, S[sf][0], S[sf][1], nbar_dn + 8u * (unsigned)par);
     }
-    if (nb_up) {
-      float2* d = reinterpret_cast<float2*>(nb_up + po);
-      d[0] = S[sl][0];
-      d[1] = S[sl][1];
+    if (rx_up) {
+      if (INIT) st_cluster16(nb_up + po, S[sl][0], S[sl][1]);
+      else if (hok) st_async16(nb_up + po, S[sl][0], S[sl][1], nbar_up + 8u * (unsigned)par);
     }
   };
-  publish(0, std::integral_constant<int, 0>{});
+  publish(0, std::integral_constant<int, 0>{}, std::true_type{});
   if (C > 1) cluster.sync();
   else __syncthreads();
 
@@ -692,26 +775,44 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   int k = 1;
   // Jumps left until the next defect correction (never reached when off: K < 2^30).
   int dleft = p.renorm > 0 ? p.renorm : 0x7fffffff;
+  // Hand-over waits: bit q of hph is the parity of the next phase of the
+  // parity-q barriers.  A completed phase is re-armed (by the column-quad-0
+  // thread) for the jump two ahead, before this thread's next row goes out,
+  // so the neighbour's bytes of that jump always find it armed.  After a wait
+  // that gave up (status kStatusTimeout) the thread stops waiting, arming and
+  // sending; a neighbour thread waiting for its rows then gives up too, after
+  // at most one more limit, and the chain runs on to its end.
+  unsigned hph = 0;
+  const bool arm_dn = rx_dn && qx == 0, arm_up = rx_up && qx == 0;
+  auto handover = [&](int q) {
+    const unsigned ph = (hph >> q) & 1u;
+    if (hok) {
+      bool ok = !rx_dn || hbar_wait(hb + 8u * (unsigned)q, ph, p.wait_limit);
+      if (ok && rx_up) ok = hbar_wait(hb + 16u + 8u * (unsigned)q, ph, p.wait_limit);
+      if (ok) {
+        if (arm_dn) hbar_arm(hb + 8u * (unsigned)q, hbytes);
+        if (arm_up) hbar_arm(hb + 16u + 8u * (unsigned)q, hbytes);
+      } else {
+        hok = false;
+        set_status(p.status, kStatusTimeout);
+      }
+    }
+    hph ^= 1u << q;
+  };
   auto step = [&](auto DIRC) {
     constexpr int DIR = decltype(DIRC)::value;
     constexpr int ROT = 1 - DIR;  // rotation of rho_k
     const int par = (k - 1) & 1;
     if (edge_w) update(par, DIRC, std::true_type{});
     else update(par, DIRC, std::false_type{});
-    publish(par ^ 1, std::integral_constant<int, ROT>{});
+    publish(par ^ 1, std::integral_constant<int, ROT>{}, std::false_type{});
     // Chunk c (jumps [c kChunk, (c+1) kChunk)) is staged at jump (c-1) kChunk + 1,
     // after the last read of the slots it reuses (chunk c-2's, read up to jump
     // (c-1) kChunk - 1), and waited for at jump c kChunk - 1, before the barrier
     // that precedes its first read.
     if ((k & (kChunk - 1)) == kChunk - 1) cp_async_wait<0>();
-    // Edges written into this CTA need CTA-scope ordering; only the threads
-    // that wrote into a neighbour CTA pay a cluster-scope fence.
-    if (nb_dn || nb_up) fence_cluster();
-    else fence_cta();
-    cluster_arrive_relaxed();
-    // Work that touches no edge overlaps the barrier: the exit-defect
-    // correction and the observations of rho_k, the next chunk of weights,
-    // the recurrence one jump ahead.
+    // The exit-defect correction and the observations of rho_k, the window
+    // range, the next chunk of weights, the recurrence one jump ahead.
     if (--dleft == 0) {
       dleft = p.renorm;
       defect_fix(std::integral_constant<int, ROT>{});
@@ -723,7 +824,12 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     accumulate(k, lo, hi, std::integral_constant<int, ROT>{});
     if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
     if (wwarp && any_rec && k + 1 <= Kmax) rec_step(k + 1);
-    cluster_wait();
+    // The edges of this CTA's blocks (and its weights) are ordered by the CTA
+    // barrier; only the threads next to a CTA boundary also wait for the
+    // neighbour's row of rho_k.
+    __syncthreads();
+    if (rx_dn || rx_up) handover(k & 1);
+    __syncwarp();
     ++k;
   };
   while (k + 1 <= Kmax) {

@@ -2,7 +2,8 @@
 bit-identical to the shared-memory chain kernel on single-member observation
 groups (same operation order per state), and within the FP32 tolerance of the
 oracle, over box shapes that exercise ragged column quads, odd row counts and
-clusters of 1, 2 and 3 CTAs."""
+clusters of 1, 2, 3, 4 and 8 CTAs; the hand-over of the rows that cross a
+CTA boundary reports a wait that runs out."""
 import numpy as np
 import pytest
 
@@ -123,3 +124,58 @@ def test_register_chain_option_rejects_other_models():
     o = mjp.Obs(400, [0.5], [([np.array([0])], np.array([1.0]))], synth.delta(400, 0))
     with pytest.raises(MJPError):
         mjp.loglik(m, o, np.array([[5.0, 1.0, 1.0, 0.2]]))
+
+
+def _spread_obs(dims, times, ngroups, seed):
+    # Single-state groups anywhere in the box (rho_0 below is uniform, so
+    # every state has mass).
+    n = dims[0] * dims[1]
+    gen = np.random.default_rng(seed)
+    obs = []
+    for _ in times:
+        mem = [np.array([s]) for s in gen.choice(n, size=ngroups, replace=False)]
+        obs.append((mem, gen.integers(1, 6, size=ngroups).astype(float)))
+    return obs
+
+
+def test_register_chain_clusters_of_many_ctas_carry_rows_across_every_seam():
+    # A 40 x 1800 box: 4 CTAs per cluster at 512 threads, 8 at 256 threads.
+    # With rho_0 uniform every CTA boundary carries
+    # nonzero rows at every jump; both layouts give the same chain, and the
+    # oracle's log-likelihood within the FP32 tolerance.
+    dims, theta = (40, 1800), (6.0, 1.0, 30.0, 0.5)
+    n = dims[0] * dims[1]
+    times = np.array([0.02, 0.1, 0.3])
+    obs = _spread_obs(dims, times, 40, seed=77)
+    rho0 = np.full(n, 1.0 / n)
+    thetas = synth.jitter(theta, 2, 0.2, synth.rng(2, 78))
+    a = _loglik(dims, theta, thetas, times, obs, rho0, 2)
+    b = _loglik(dims, theta, thetas, times, obs, rho0, 2, threads=256)
+    np.testing.assert_array_equal(a, b)
+    nobs = sum(c.sum() for _, c in obs)
+    for i in range(len(thetas)):
+        ref = oracle.loglik(oracle.build_model(synth.MRNA_PROT2D, list(dims), thetas[i]), rho0, times, obs)
+        assert abs(a[i] - ref) <= PER_OBS_FP32 * nobs
+
+
+def test_register_chain_handover_wait_that_runs_out_is_reported():
+    # A wait limit of zero polls: the first wait for a neighbour CTA's row
+    # gives up at once; the status word says so (MJP_ERR_DEVICE_TIMEOUT), and
+    # the model and the context stay usable.
+    import paper_2312_05647_gb300 as mjp
+    from paper_2312_05647_gb300.capi import MJPError
+    dims, theta = (200, 200), (20.0, 1.0, 5.0, 0.1)  # 2 CTAs per cluster
+    times = np.array([0.05, 0.2])
+    obs, rho0 = _case(dims, theta, times, 20, seed=91)
+    thetas = synth.jitter(theta, 2, 0.2, synth.rng(2, 92))
+    m = mjp.Model(synth.MRNA_PROT2D, dims, theta, mjp.FP32)
+    m.set_option(mjp.OPT_CHAIN, 2)
+    m.set_option(mjp.OPT_WAIT_LIMIT, 0)
+    o = mjp.Obs(dims[0] * dims[1], times, obs, rho0)
+    with pytest.raises(MJPError) as ei:
+        mjp.loglik(m, o, thetas)
+    assert ei.value.code == -5
+    m.set_option(mjp.OPT_WAIT_LIMIT, 1 << 24)
+    ll = mjp.loglik(m, o, thetas)
+    m.check()
+    np.testing.assert_array_equal(ll, _loglik(dims, theta, thetas, times, obs, rho0, 2))
