@@ -712,6 +712,7 @@ def main():
                           f"derived nominal {derived:.2f} TFLOP/s ({sms} SMs x 128 FMA/clk x 2 x {max_mhz:.0f} MHz)",
             "flops_per_launch": flops, "flops_basis": "10 per state update (5-point stencil), algorithmic",
             "chain_ms_avg": statistics.mean(chain_ms), "plan_ms_avg": statistics.mean(plan_ms),
+            "state_updates_per_launch": updates, "state_updates_per_s": updates / chain_avg_s,
             "smem": {"achieved_gbs": smem_gbs, "peak_gbs": peak_smem, "frac": smem_gbs / peak_smem,
                      "bytes_per_update": SMEM_BYTES_PER_UPDATE, "peak_basis": "of measured (mjp_measure_peak)"},
             "tmem_gbs": TMEM_BYTES_PER_UPDATE * updates / chain_avg_s / 1e9}

@@ -254,12 +254,14 @@ __device__ __forceinline__ void hbar_arm(unsigned a, unsigned bytes) {
                : "memory");
 }
 // At most `polls` tests of the phase of parity ph (none when polls is 0):
-// false when the phase has not completed by then.
+// false when the phase has not completed by then.  The test acquires at
+// cluster scope: the bytes it orders were written by another CTA.
 __device__ __forceinline__ bool hbar_wait(unsigned a, unsigned ph, long long polls) {
   for (long long i = 0; i < polls; ++i) {
     unsigned ok;
-    asm volatile("{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                 : "=r"(ok) : "r"(a), "r"(ph) : "memory");
+    asm volatile(
+        "{ .reg .pred p; mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok) : "r"(a), "r"(ph) : "memory");
     if (ok) return true;
     if (i >= 16) __nanosleep(32);
   }
@@ -485,7 +487,10 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     S[r][1] = v_make(v[1], v[3]);
   }
   S[NR][0] = S[NR][1] = v_make(0.0f, 0.0f);
-  // Residuals start at zero.
+  // Residuals start at zero.  (Tensor-memory instructions are warp-wide: the
+  // warp is converged before each group of them that follows lane-dependent
+  // code.)
+  __syncwarp();
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     // Row r's coefficients, as the update formed them every jump before.
@@ -553,6 +558,9 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
       if (INIT) st_cluster16(nb_up + po, S[sl][0], S[sl][1]);
       else if (hok) st_async16(nb_up + po, S[sl][0], S[sl][1], nbar_up + 8u * (unsigned)par);
     }
+    // Only some lanes send: the warp is converged again before its next
+    // warp-wide tensor-memory instruction (the defect correction).
+    __syncwarp();
   };
   publish(0, std::integral_constant<int, 0>{}, std::true_type{});
   if (C > 1) cluster.sync();
@@ -879,6 +887,7 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   }
   // Keep every CTA's accumulators alive until rank 0 is done, and every
   // residual store complete before the tensor memory is released.
+  __syncwarp();
   tmem_wait_st();
   tmem_fence_before();
   if (C > 1) cluster.sync();
