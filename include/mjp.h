@@ -342,9 +342,9 @@ int expv_series_static(int kind, const int64_t* dims, int ndims, const double* t
 /*
  * Measured on-chip peaks of the current device, for roofline denominators (the
  * paper has no counterpart; the benchmark reports the chain kernels against
- * them).  MJP_PEAK_FP32_FMA: packed FP32 fused multiply-adds from independent
- * chains on two 512-thread CTAs per SM, in TFLOP/s (2 flops per lane and
- * instruction); MJP_PEAK_SMEM: 16-byte shared-memory loads and stores of
+ * them).  MJP_PEAK_FP32_FMA: FP32 fused multiply-adds from independent
+ * chains on two 512-thread CTAs per SM, in TFLOP/s (2 flops per FMA), the
+ * better of packed FP32x2 and scalar instructions; MJP_PEAK_SMEM: 16-byte shared-memory loads and stores of
  * consecutive vectors (no bank conflicts) on the same grid, in GB/s counting
  * read plus written bytes.  `iters` loop iterations per thread (a few hundred
  * thousand give ~10 ms); best of three timed launches with CUDA events on

@@ -1,6 +1,7 @@
 // peaks.cu -- measured on-chip peaks for the roofline denominators of the
-// chain kernels: the packed FP32 fused-multiply-add rate and the shared-memory
-// bandwidth of all SMs.  Not part of the method; the benchmark reports the
+// chain kernels: the FP32 fused-multiply-add rate (the better of packed FP32x2
+// and scalar instructions), the shared-memory bandwidth of all SMs and the
+// L2's random-gather rate.  Not part of the method; the benchmark reports the
 // chain kernels against these measured numbers instead of nominal ones.
 #include <cuda_runtime.h>
 
@@ -26,6 +27,23 @@ __global__ void __launch_bounds__(512) peak_fma_kernel(float* sink, int iters) {
   float s = 0.0f;
 #pragma unroll
   for (int j = 0; j < kFmaChains; ++j) s += a[j].x + a[j].y;
+  if (s == -1.0f) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// The same work as scalar FP32 FMAs: 2 kFmaChains independent chains per
+// thread (the instruction is emitted as written, so the chains stay scalar).
+__global__ void __launch_bounds__(512) peak_fma1_kernel(float* sink, int iters) {
+  float a[2 * kFmaChains];
+#pragma unroll
+  for (int j = 0; j < 2 * kFmaChains; ++j) a[j] = 1e-3f * (threadIdx.x + 3 * j);
+  const float m = 0.999997f, c = 3e-7f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 2 * kFmaChains; ++j) asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(a[j]) : "f"(m), "f"(c));
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 2 * kFmaChains; ++j) s += a[j];
   if (s == -1.0f) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
@@ -102,25 +120,34 @@ extern "C" int mjp_measure_peak(int which, int iters, double* result, void* stre
     MJP_CUDA(cudaMemsetAsync(ar.b.p, 0, sizeof(float) * kGatherN, s));
   }
   const size_t smem = (which == MJP_PEAK_SMEM) ? 2 * threads * sizeof(float4) : 0;
-  auto launch = [&]() -> cudaError_t {
-    if (which == MJP_PEAK_FP32_FMA) peak_fma_kernel<<<blocks, threads, 0, s>>>(sink.as<float>(), iters);
-    else if (which == MJP_PEAK_SMEM) peak_smem_kernel<<<blocks, threads, smem, s>>>(sink.as<float>(), iters);
-    else peak_gather_kernel<<<blocks, threads, 0, s>>>(ar.b.as<float>(), kGatherN - 1, sink.as<float>(), iters);
+  // form 1: the scalar FP32 FMA kernel (the FP32 peak is the better form's).
+  auto launch = [&](int form) -> cudaError_t {
+    if (which == MJP_PEAK_FP32_FMA) {
+      if (form == 0) peak_fma_kernel<<<blocks, threads, 0, s>>>(sink.as<float>(), iters);
+      else peak_fma1_kernel<<<blocks, threads, 0, s>>>(sink.as<float>(), iters);
+    } else if (which == MJP_PEAK_SMEM) {
+      peak_smem_kernel<<<blocks, threads, smem, s>>>(sink.as<float>(), iters);
+    } else {
+      peak_gather_kernel<<<blocks, threads, 0, s>>>(ar.b.as<float>(), kGatherN - 1, sink.as<float>(), iters);
+    }
     return cudaGetLastError();
   };
-  MJP_CUDA(launch());  // warm-up (clocks, instruction cache)
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   MJP_CUDA(cudaEventCreate(&e0));
   MJP_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  for (int r = 0; r < 3; ++r) {
-    MJP_CUDA(cudaEventRecord(e0, s));
-    MJP_CUDA(launch());
-    MJP_CUDA(cudaEventRecord(e1, s));
-    MJP_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.0f;
-    MJP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) best = ms;
+  const int forms = (which == MJP_PEAK_FP32_FMA) ? 2 : 1;
+  for (int f = 0; f < forms; ++f) {
+    MJP_CUDA(launch(f));  // warm-up (clocks, instruction cache)
+    for (int r = 0; r < 3; ++r) {
+      MJP_CUDA(cudaEventRecord(e0, s));
+      MJP_CUDA(launch(f));
+      MJP_CUDA(cudaEventRecord(e1, s));
+      MJP_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      MJP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) best = ms;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
