@@ -127,10 +127,14 @@ extern "C" {
                                    K_i = cumulative steps to t_i, eps_i = 0 */
 #define MJP_OPT_KAPPA 10        /* Krylov subspace size kappa (default 20, the paper's; 1 .. 32) */
 #define MJP_OPT_WAIT_LIMIT 11   /* polls of a bounded wait before it gives up (default 2^24, about a second; 0 = give up
-                                   at once): general CSR models with MJP_OPT_CHAIN = 2 (a CTA at the grid barrier) and
+                                   at once): general CSR models with MJP_OPT_CHAIN = 2 (a CTA at the grid barrier),
                                    the register-resident two-state log-likelihood chain (the hand-over of observation
-                                   chunks between its chain and reducer warps).  A wait that runs out stops the
-                                   chain; rate_model_check then returns MJP_ERR_DEVICE_TIMEOUT */
+                                   chunks between its chain and reducer warps) and the register-resident
+                                   mRNA/protein log-likelihood chain (the hand-over of the block rows that cross
+                                   from one CTA of a cluster to the next, every jump).  A wait that runs out stops
+                                   the CSR and two-state chains; the mRNA/protein chain stops waiting and runs on to
+                                   its end with invalid values.  rate_model_check then returns
+                                   MJP_ERR_DEVICE_TIMEOUT */
 
 typedef struct mjp_model mjp_model;
 typedef struct mjp_obs mjp_obs;
