@@ -437,7 +437,9 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   // register pair.  Threads without a block run the same instructions (the
   // tensor-memory accesses are warp-wide) with every coefficient zero, so
   // their values stay zero.
-  float crc[kQC], cdc[kQC], d0c[kQC];
+  // The column defects eps (formed in FP64, the only FP64 arithmetic of the
+  // defect correction) are kept in tensor memory for it.
+  float crc[kQC], cdc[kQC], d0c[kQC], epc[kQC];
   int colmask = 0;  // bit c: column m0 + c lies in the box
   const float own = owner ? 1.0f : 0.0f;
 #pragma unroll
@@ -447,7 +449,9 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     const float fm = (float)m;
     crc[c] = owner ? f_mul(co.b, (float)(m + 1)) : 0.0f;
     cdc[c] = owner ? f_mul(co.c, fm) : 0.0f;
-    d0c[c] = owner ? -mrna_col(co, m, M).e0 : 0.0f;
+    const MrnaCol mc = mrna_col(co, m, M);
+    d0c[c] = owner ? -mc.e0 : 0.0f;
+    epc[c] = owner ? mc.eps : 0.0f;
   }
   const float2 d0A = v_make(d0c[0], d0c[2]), d0B = v_make(d0c[1], d0c[3]);
   const float2 crA = v_make(crc[0], crc[2]), crB = v_make(crc[1], crc[3]);
@@ -499,7 +503,9 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     tmem_st4(tres + kRowCols * r, v_make(0.0f, 0.0f), v_make(0.0f, 0.0f));
     tmem_st4(tres + kRowCols * r + 4u, v_fma(c_ngp, fp2, d0A), v_fma(c_ngp, fp2, d0B));  // -e_{m,p}
     const float2 cu = v_fma(c_gp, fp2, c_gp);  // gamma_p (p+1) from p+1
-    tmem_st4(tres + kRowCols * r + 8u, cu, v_make(0.0f, 0.0f));
+    // Spare columns: the column defects of (c0, c2) in row 0, of (c1, c3) in row 1.
+    const float2 sp = r == 0 ? v_make(epc[0], epc[2]) : r == 1 ? v_make(epc[1], epc[3]) : v_make(0.0f, 0.0f);
+    tmem_st4(tres + kRowCols * r + 8u, cu, sp);
   }
   // The row arrays of the neighbouring CTAs: our first row is the row above
   // CTA rank-1 (its array 0, counted by its barrier from above), our last row
@@ -757,6 +763,19 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
   auto defect_fix = [&](auto ROTC) {
     constexpr int ROT = decltype(ROTC)::value;
     tmem_wait_st();
+    // Column parts: e0 in FP32 as mrna_col forms it, eps from tensor memory.
+    MrnaCol mcol[kQC];
+    {
+      float2 eA, eB, dummy;
+      tmem_ld4(tres + 8u, dummy, eA);
+      tmem_ld4(tres + kRowCols + 8u, dummy, eB);
+      const float ep[kQC] = {eA.x, eB.x, eA.y, eB.y};
+#pragma unroll
+      for (int c = 0; c < kQC; ++c) {
+        mcol[c].e0 = mrna_col(co, m0 + c, M).e0;
+        mcol[c].eps = ep[c];
+      }
+    }
 #pragma unroll 1
     for (int r = 0; r < NR; ++r) {
       const int pr = pb + r;
@@ -764,7 +783,7 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
       tmem_ld4(tres + kRowCols * r, rA, rB);
       float b[kQC];
 #pragma unroll
-      for (int c = 0; c < kQC; ++c) b[c] = own * __fmul_rn(period, mrna_defect(mrna_col(co, m0 + c, M), co.d, pr));
+      for (int c = 0; c < kQC; ++c) b[c] = own * __fmul_rn(period, mrna_defect(mcol[c], co.d, pr));
       // Row r sits in register slot r (home) or r - 1 (shifted); pick it by rotation.
       float2 ya = v_make(0.0f, 0.0f), yb = ya;
 #pragma unroll
