@@ -800,8 +800,22 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
 
   // ---- the jump chain -------------------------------------------------------
   int k = 1;
-  // Jumps left until the next defect correction (never reached when off: K < 2^30).
-  int dleft = p.renorm > 0 ? p.renorm : 0x7fffffff;
+  // Next defect correction (never reached when off: K < 2^30).
+  int kdef = p.renorm > 0 ? p.renorm : 0x7fffffff;
+  // Jumps with work besides the update, the edges and the observations (a
+  // chunk of weights lands (jump = 31 mod kChunk) or is staged (1 mod
+  // kChunk), the defect correction, a change of the active window range) are
+  // "events"; every other jump tests one counter.  act: this thread has
+  // observations to accumulate in the active range.
+  auto next_event = [&](int kk) -> int {
+    int e = min(kdef, knext);
+    e = min(e, (kk + 1) | (kChunk - 1));
+    e = min(e, ((kk + kChunk - 1) & ~(kChunk - 1)) + 1);
+    return e;
+  };
+  bool act = owner && lo <= hi;
+  const bool do_rec = wwarp && any_rec;
+  int kev = min(min(kdef, max(knext, 1)), kChunk - 1);
   // Hand-over waits: bit q of hph is the parity of the next phase of the
   // parity-q barriers.  A completed phase is re-armed (by the column-quad-0
   // thread) for the jump two ahead, before this thread's next row goes out,
@@ -837,20 +851,25 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     // after the last read of the slots it reuses (chunk c-2's, read up to jump
     // (c-1) kChunk - 1), and waited for at jump c kChunk - 1, before the barrier
     // that precedes its first read.
-    if ((k & (kChunk - 1)) == kChunk - 1) cp_async_wait<0>();
-    // The exit-defect correction and the observations of rho_k, the window
-    // range, the next chunk of weights, the recurrence one jump ahead.
-    if (--dleft == 0) {
-      dleft = p.renorm;
-      defect_fix(std::integral_constant<int, ROT>{});
+    // The exit-defect correction, the window range and the next chunk of
+    // weights (whose slots are not the ones read at this jump) at events;
+    // the observations of rho_k; the recurrence one jump ahead.
+    if (k == kev) {
+      if ((k & (kChunk - 1)) == kChunk - 1) cp_async_wait<0>();
+      if (k == kdef) {
+        kdef += p.renorm;
+        defect_fix(std::integral_constant<int, ROT>{});
+      }
+      if (k >= knext) {
+        advance(k, lo, hi);
+        knext = next_change(lo, hi);
+        act = owner && lo <= hi;
+      }
+      if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
+      kev = next_event(k);
     }
-    if (k >= knext) {
-      advance(k, lo, hi);
-      knext = next_change(lo, hi);
-    }
-    accumulate(k, lo, hi, std::integral_constant<int, ROT>{});
-    if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
-    if (wwarp && any_rec && k + 1 <= Kmax) rec_step(k + 1);
+    if (act) accumulate(k, lo, hi, std::integral_constant<int, ROT>{});
+    if (do_rec && k + 1 <= Kmax) rec_step(k + 1);
     // The edges of this CTA's blocks (and its weights) are ordered by the CTA
     // barrier; only the threads next to a CTA boundary also wait for the
     // neighbour's row of rho_k.
