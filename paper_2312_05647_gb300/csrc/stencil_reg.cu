@@ -128,34 +128,6 @@ __host__ __device__ constexpr int rslot(int r, int rot) {
   return rot == 0 ? r : (r == 0 ? NR : r - 1);
 }
 
-// Register value of observation slot r * 4 + c (row r, column c; columns
-// c0, c2 in pair 0 and c1, c3 in pair 1 of the row) at rotation ROT, by a tree
-// of selections (no local-memory array).
-template <int NR, int ROT>
-__device__ __forceinline__ float pick(const float2 (&S)[NR + 1][2], int slot) {
-  const bool c1 = slot & 1, c2 = slot & 2;
-  const int r = slot >> 2;
-  // Column of every row (independent selections), then a binary tree over
-  // the bits of the row index (depth log2 NR instead of NR).
-  float x[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    if (q < NR) {
-      const float2 a = S[rslot<NR>(q < NR ? q : 0, ROT)][0], b = S[rslot<NR>(q < NR ? q : 0, ROT)][1];
-      x[q] = c2 ? (c1 ? b.y : a.y) : (c1 ? b.x : a.x);
-    } else {
-      x[q] = 0.0f;
-    }
-  }
-#pragma unroll
-  for (int bit = 0; bit < 4; ++bit) {
-    const bool hi = (r >> bit) & 1;
-#pragma unroll
-    for (int q = 0; q < (16 >> (bit + 1)); ++q) x[q] = hi ? x[2 * q + 1] : x[2 * q];
-  }
-  return x[0];
-}
-
 // The value of v, hidden from the optimiser: quantities derived from it inside
 // the jump loop are recomputed each jump instead of being hoisted out of the
 // loop and held in registers for all states.
@@ -613,11 +585,24 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
     if (!owner || l > h) return;
     const int sk = k & (kStage - 1);
     while (ecur < eend && (ent[ecur].y >> 6) < l) ++ecur;
+    if (ecur >= eend || (ent[ecur].y >> 6) > h) return;
+    // Some of this thread's states are observed at this jump: its values go
+    // to a per-thread local array once (slot 4 r + c: row r, column c), and
+    // each observed one is read back by its slot.
+    float loc[NR * kQC];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const float2 a = S[rslot<NR>(r, ROT)][0], b = S[rslot<NR>(r, ROT)][1];
+      loc[kQC * r + 0] = a.x;
+      loc[kQC * r + 1] = b.x;
+      loc[kQC * r + 2] = a.y;
+      loc[kQC * r + 3] = b.y;
+    }
     for (int e = ecur; e < eend; ++e) {
       const int2 en = ent[e];
       const int ti = en.y >> 6;
       if (ti > h) break;
-      const float v = pick<NR, ROT>(S, en.y & 63);
+      const float v = loc[en.y & 63];
       const float w = ring[ti * kStage + sk];
       const float y = __fsub_rn(__fmul_rn(w, v), acc_c[en.x]);
       const float s0 = acc_s[en.x];
