@@ -761,6 +761,14 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
         mcol[c].eps = ep[c];
       }
     }
+    // The rows of rho_k, by row index, in a per-thread local array (the row
+    // loop is not unrolled, and registers cannot be indexed at run time).
+    float4 rows[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const float2 a = S[rslot<NR>(r, ROT)][0], b = S[rslot<NR>(r, ROT)][1];
+      rows[r] = make_float4(a.x, a.y, b.x, b.y);
+    }
 #pragma unroll 1
     for (int r = 0; r < NR; ++r) {
       const int pr = pb + r;
@@ -769,14 +777,8 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
       float b[kQC];
 #pragma unroll
       for (int c = 0; c < kQC; ++c) b[c] = own * __fmul_rn(period, mrna_defect(mcol[c], co.d, pr));
-      // Row r sits in register slot r (home) or r - 1 (shifted); pick it by rotation.
-      float2 ya = v_make(0.0f, 0.0f), yb = ya;
-#pragma unroll
-      for (int q = 0; q < NR; ++q)
-        if (q == r) {
-          ya = S[rslot<NR>(q, ROT)][0];
-          yb = S[rslot<NR>(q, ROT)][1];
-        }
+      const float4 y4 = rows[r];
+      const float2 ya = make_float2(y4.x, y4.y), yb = make_float2(y4.z, y4.w);
       rA = v_fma(v_make(b[0], b[2]), ya, rA);
       rB = v_fma(v_make(b[1], b[3]), yb, rB);
       tmem_st4(tres + kRowCols * r, rA, rB);
