@@ -182,8 +182,12 @@ struct Tmem12 {
   Tmem2 c;
 };
 __device__ __forceinline__ void tmem_ld12_issue(unsigned taddr, Tmem12& v) {
-  tmem_ld4_issue(taddr, v.r);
-  tmem_ld4_issue(taddr + 4u, v.d);
+  // Columns 0-7 (residuals, exit coefficients) in one load, 8-9 in another.
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v.r.r0), "=r"(v.r.r1), "=r"(v.r.r2), "=r"(v.r.r3), "=r"(v.d.r0), "=r"(v.d.r1), "=r"(v.d.r2),
+                 "=r"(v.d.r3)
+               : "r"(taddr)
+               : "memory");
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
                : "=r"(v.c.r0), "=r"(v.c.r1) : "r"(taddr + 8u) : "memory");
 }
@@ -513,12 +517,9 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
 #pragma unroll
     for (int r = 0; r < kQR; ++r) {
       const int s0 = rslot<NR>(2 * r, ROT), s1 = rslot<NR>(2 * r + 1, ROT);
-      float* cl = reinterpret_cast<float*>(Ep + G::col(0, r) + oT8);
-      float* cr = reinterpret_cast<float*>(Ep + G::col(1, r) + oT8);
-      cl[0] = S[s0][0].x;
-      cl[1] = S[s1][0].x;
-      cr[0] = S[s0][1].y;
-      cr[1] = S[s1][1].y;
+      // One 8-byte store per column and row pair (the slots are 8-byte aligned).
+      *reinterpret_cast<float2*>(Ep + G::col(0, r) + oT8) = make_float2(S[s0][0].x, S[s1][0].x);
+      *reinterpret_cast<float2*>(Ep + G::col(1, r) + oT8) = make_float2(S[s0][1].y, S[s1][1].y);
     }
     const int sf = rslot<NR>(0, ROT), sl = rslot<NR>(NR - 1, ROT);
     float2* fr = reinterpret_cast<float2*>(Ep + G::row(0) + oT16);
