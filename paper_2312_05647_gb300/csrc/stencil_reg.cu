@@ -856,12 +856,15 @@ __global__ void __launch_bounds__(kT, 512 / kT) chain_reg2d_kernel(const ChainPa
       if ((k & (kChunk - 1)) == 1 && k > 1 && k - 1 + kChunk <= Kmax) stage_chunk(k - 1 + kChunk);
       kev = next_event(k);
     }
-    if (act) accumulate(k, lo, hi, std::integral_constant<int, ROT>{});
     if (do_rec && k + 1 <= Kmax) rec_step(k + 1);
     // The edges of this CTA's blocks (and its weights) are ordered by the CTA
     // barrier; only the threads next to a CTA boundary also wait for the
-    // neighbour's row of rho_k.
+    // neighbour's row of rho_k.  The observations of rho_k come after the
+    // barrier (they read this thread's registers and ring slots that no one
+    // rewrites before the next barrier), so the warps that hold observed
+    // states sum them while the others start the next jump.
     __syncthreads();
+    if (act) accumulate(k, lo, hi, std::integral_constant<int, ROT>{});
     if (rx_dn || rx_up) handover(k & 1);
     __syncwarp();
     ++k;
