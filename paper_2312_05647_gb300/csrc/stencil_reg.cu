@@ -159,21 +159,12 @@ __device__ __forceinline__ void tmem_ld4(unsigned taddr, float2& a, float2& b) {
   a = make_float2(__uint_as_float(r0), __uint_as_float(r1));
   b = make_float2(__uint_as_float(r2), __uint_as_float(r3));
 }
-// Split form: issue the load of a row, wait for it later (one load in flight).
+// Registers of a 4-column load in flight.
 struct Tmem4 {
   unsigned r0, r1, r2, r3;
 };
-__device__ __forceinline__ void tmem_ld4_issue(unsigned taddr, Tmem4& v) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(v.r0), "=r"(v.r1), "=r"(v.r2), "=r"(v.r3) : "r"(taddr) : "memory");
-}
-__device__ __forceinline__ void tmem_ld4_wait(Tmem4& v, float2& a, float2& b) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(v.r0), "+r"(v.r1), "+r"(v.r2), "+r"(v.r3) :: "memory");
-  a = make_float2(__uint_as_float(v.r0), __uint_as_float(v.r1));
-  b = make_float2(__uint_as_float(v.r2), __uint_as_float(v.r3));
-}
 // Row r's residuals, exit coefficients and inflow-from-above coefficient
-// (three 4-column loads, waited for together).
+// (an 8-column and a 2-column load, waited for together).
 struct Tmem2 {
   unsigned r0, r1;
 };
