@@ -7,7 +7,12 @@
 // double-buffered by jump parity, and the observation accumulators.  Per jump
 // a thread reads its four neighbours' edges, updates its states in place (row
 // pair by row pair, keeping the old values the next ones still need), writes
-// its own edges and meets the rest of the cluster at one split barrier.
+// its own edges and meets the rest of its CTA at one barrier; the rows that
+// cross to a neighbouring CTA of the cluster go there by st.async, counted on
+// that CTA's hand-over mbarriers (no cluster barrier per jump).  Work that
+// only some threads have (the observations of rho_k, read from a per-thread
+// local array by slot) follows the barrier, so it overlaps the others' next
+// jump instead of holding every warp at it.
 // Compared with a shared-memory ping-pong of the whole slab (every state read
 // three times and written once per jump), shared-memory traffic drops from
 // 16 B to ~1.5 B per state and the FP32 pipe becomes the limit.
@@ -29,10 +34,11 @@
 // column pair and the inflow from the row above), formed once in the
 // prologue exactly as the update formed them every jump before, are loaded
 // instead of recomputed.  Each warp owns its 32 TMEM lanes (the quadrant
-// warp % 4 may address) and 12 columns per row of its blocks; a row's
-// residuals and coefficients are read with three tcgen05.ld (issued while the
-// previous row is computed) and its residuals written back with one
-// tcgen05.st.  The CTA holds one allocation from start to end, sized so that
+// warp % 4 may address) and 12 columns per row of its blocks (two of them
+// spare; in rows 0 and 1 they hold the column defects of the exit-defect
+// correction, so no FP64 arithmetic runs in the jump loop); a row's residuals
+// and coefficients are read with two tcgen05.ld (issued while the previous
+// row is computed) and its residuals written back with one tcgen05.st.  The CTA holds one allocation from start to end, sized so that
 // all CTAs the register file admits on one SM fit its TMEM (no allocation
 // ever waits).
 //
