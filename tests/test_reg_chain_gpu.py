@@ -2,8 +2,9 @@
 bit-identical to the shared-memory chain kernel on single-member observation
 groups (same operation order per state), and within the FP32 tolerance of the
 oracle, over box shapes that exercise ragged column quads, odd row counts and
-clusters of 1, 2, 3, 4 and 8 CTAs; the hand-over of the rows that cross a
-CTA boundary reports a wait that runs out."""
+clusters of 1, 2, 3, 4 and 8 CTAs; every state of a band observed (each
+thread summing an observation per register slot); the hand-over of the rows
+that cross a CTA boundary reports a wait that runs out."""
 import numpy as np
 import pytest
 
@@ -179,3 +180,34 @@ def test_register_chain_handover_wait_that_runs_out_is_reported():
     ll = mjp.loglik(m, o, thetas)
     m.check()
     np.testing.assert_array_equal(ll, _loglik(dims, theta, thetas, times, obs, rho0, 2))
+
+
+def _dense_obs(dims, times, rows, cols, seed):
+    # Every state of the given rows and columns is a single-member group at
+    # every time, so each thread that holds them has one observation per state
+    # (up to all 40 register slots) in every window.
+    gen = np.random.default_rng(seed)
+    states = [p * dims[0] + m for p in rows for m in cols]
+    return [([np.array([s]) for s in states], gen.integers(1, 4, size=len(states)).astype(float)) for _ in times]
+
+
+@pytest.mark.parametrize("dims,rows,cols,times", [
+    ((30, 40), range(0, 40), range(0, 30), [0.05, 0.3, 1.0]),   # one CTA, every state observed
+    # Two CTAs, the rows on both sides of their seam, mRNA counts below 100
+    # (the higher ones fall below FP32's range by t = 0.3: their log is -inf
+    # in FP32 as it is not in FP64).
+    ((200, 200), range(93, 107), range(0, 100), [0.3]),
+])
+def test_register_chain_with_every_state_of_a_band_observed(dims, rows, cols, times):
+    theta = (20.0, 1.0, 5.0, 0.1)
+    n = dims[0] * dims[1]
+    times = np.array(times)
+    obs = _dense_obs(dims, times, rows, cols, seed=len(rows))
+    rho0 = np.full(n, 1.0 / n)
+    thetas = synth.jitter(theta, 2, 0.2, synth.rng(2, 93))
+    a = _loglik(dims, theta, thetas, times, obs, rho0, 1)
+    b = _loglik(dims, theta, thetas, times, obs, rho0, 2)
+    np.testing.assert_array_equal(a, b)
+    nobs = sum(c.sum() for _, c in obs)
+    ref = oracle.loglik(oracle.build_model(synth.MRNA_PROT2D, list(dims), thetas[0]), rho0, times, obs)
+    assert abs(b[0] - ref) <= PER_OBS_FP32 * nobs
