@@ -165,6 +165,27 @@ int mjp_sampler_trace(mjp_sampler* s, double* out, int where, void* stream);
  * pointers into the sampler (valid until the next call on it). */
 int mjp_sampler_evals(mjp_sampler* s, const double** psi, const double** loglik, int64_t* n);
 
+/* Checkpoint and resume (the paper has no counterpart: it runs its chains
+ * in one go).  A checkpoint holds everything a sampler carries from one run
+ * to the next: every chain's Psi, exact and surrogate log-likelihoods and
+ * iteration count (the Philox counter of its random numbers: with the seed,
+ * the whole random state), the counters, best points, kept samples,
+ * recorded evaluation pairs, Z and its Cholesky factor.  Restored into a
+ * sampler created with the same chains, capacities and seed (on the same
+ * model and observations, which the caller keeps), a run continues exactly
+ * as it would have without the interruption.  The surrogate network is
+ * saved separately (mjp_mlp_get_params / mjp_mlp_set_params).
+ * mjp_sampler_checkpoint_size: bytes of a checkpoint of `s`.
+ * mjp_sampler_save: writes it to host memory `buf` (`bytes` >= that size);
+ * synchronises `stream`.  Call it between runs.
+ * mjp_sampler_load: reads one written by mjp_sampler_save; MJP_ERR_ARG when
+ * `buf` is not a checkpoint of this library version, is truncated, or comes
+ * from a sampler with other chains, capacities or seed (then `s` is
+ * unchanged); synchronises `stream`.  The layout is the host's byte order. */
+int mjp_sampler_checkpoint_size(mjp_sampler* s, size_t* bytes);
+int mjp_sampler_save(mjp_sampler* s, void* buf, size_t bytes, void* stream);
+int mjp_sampler_load(mjp_sampler* s, const void* buf, size_t bytes, void* stream);
+
 typedef struct {
   int64_t every;        /* H: iterations between updates of Z (300) */
   int64_t window;       /* H': samples per update (100) */

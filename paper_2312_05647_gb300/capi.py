@@ -119,6 +119,9 @@ SIGNATURES = {
     "mjp_sampler_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(SamplerStats), _vp]),
     "mjp_sampler_trace": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
     "mjp_sampler_evals": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64p]),
+    "mjp_sampler_checkpoint_size": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "mjp_sampler_save": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "mjp_sampler_load": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
     "mjp_sampler_adapt": (ctypes.c_int, [_vp, ctypes.POINTER(AdaptCfg), ctypes.POINTER(AdaptReport), _vp]),
     "mjp_ess": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
                                ctypes.c_int, _vp]),

@@ -709,6 +709,47 @@ int64_t sum_count(const std::vector<int64_t>& cnt, int which) {
 
 }  // namespace
 
+namespace {
+
+// Checkpoint layout: a header, then the device buffers that carry a
+// sampler from one run to the next, in the order ckpt_parts lists them.
+// Buffers that live only inside a run (proposals, the compacted batch, its
+// theta and log-likelihoods, the control words) are not saved.
+constexpr uint64_t kCkptMagic = 0x3154504b434d4a4dULL;  // "MJMCKPT1" read as little-endian bytes
+constexpr int32_t kCkptVersion = 1;
+struct CkptHeader {
+  uint64_t magic;
+  int32_t version, chains;
+  int64_t cap, evcap;
+  uint64_t seed;
+  int64_t evn, rounds, kept_base;
+  int32_t np, ncnt, nbest, pad;
+};
+template <class F>
+void ckpt_parts(mjp_sampler* s, F&& f) {
+  const size_t C = (size_t)s->C;
+  const size_t ev = (size_t)std::max<int64_t>(s->evcap, 1);
+  f(s->psi, C * NP * 8);
+  f(s->ll, C * 8);
+  f(s->scur, C * 8);
+  f(s->it, C * 8);  // the chains' Philox counters
+  f(s->nrec, C * 8);
+  f(s->cnt, C * NCNT * 8);
+  f(s->best, C * NBEST * 8);
+  f(s->trace, C * (size_t)s->cap * NP * 8);
+  f(s->evpsi, ev * NP * 8);
+  f(s->evll, ev * 8);
+  f(s->Z, 16 * 8);
+  f(s->L, 16 * 8);
+}
+size_t ckpt_bytes(mjp_sampler* s) {
+  size_t n = sizeof(CkptHeader);
+  ckpt_parts(s, [&](DevBuf&, size_t b) { n += b; });
+  return n;
+}
+
+}  // namespace
+
 extern "C" {
 
 int mjp_sampler_create(mjp_sampler** out, mjp_model* m, const mjp_obs* obs, int chains, int64_t capacity,
@@ -995,6 +1036,76 @@ int mjp_sampler_evals(mjp_sampler* s, const double** psi, const double** ll, int
   *psi = s->evpsi.as<double>();
   *ll = s->evll.as<double>();
   *n = s->evn;
+  return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
+}
+
+int mjp_sampler_checkpoint_size(mjp_sampler* s, size_t* bytes) try {
+  if (!s || !bytes) return fail(MJP_ERR_ARG, "NULL argument");
+  *bytes = ckpt_bytes(s);
+  return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
+}
+
+int mjp_sampler_save(mjp_sampler* s, void* buf, size_t bytes, void* stream) try {
+  if (!s || !buf) return fail(MJP_ERR_ARG, "NULL argument");
+  if (bytes < ckpt_bytes(s)) return fail(MJP_ERR_ARG, "checkpoint buffer smaller than mjp_sampler_checkpoint_size");
+  cudaStream_t st = (cudaStream_t)stream;
+  CkptHeader h = {};
+  h.magic = kCkptMagic;
+  h.version = kCkptVersion;
+  h.chains = s->C;
+  h.cap = s->cap;
+  h.evcap = s->evcap;
+  h.seed = s->seed;
+  h.evn = s->evn;
+  h.rounds = s->rounds;
+  h.kept_base = s->kept_base;
+  h.np = NP;
+  h.ncnt = NCNT;
+  h.nbest = NBEST;
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  std::memcpy(out, &h, sizeof h);
+  size_t off = sizeof h;
+  cudaError_t e = cudaSuccess;
+  ckpt_parts(s, [&](DevBuf& b, size_t n) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out + off, b.p, n, cudaMemcpyDeviceToHost, st);
+    off += n;
+  });
+  MJP_CUDA(e);
+  MJP_CUDA(cudaStreamSynchronize(st));
+  return MJP_OK;
+} catch (...) {
+  return ::mjp::exception_status();
+}
+
+int mjp_sampler_load(mjp_sampler* s, const void* buf, size_t bytes, void* stream) try {
+  if (!s || !buf) return fail(MJP_ERR_ARG, "NULL argument");
+  if (bytes < sizeof(CkptHeader)) return fail(MJP_ERR_ARG, "checkpoint too short");
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof h);
+  if (h.magic != kCkptMagic || h.version != kCkptVersion || h.np != NP || h.ncnt != NCNT || h.nbest != NBEST)
+    return fail(MJP_ERR_ARG, "not a sampler checkpoint of this library version");
+  if (h.chains != s->C || h.cap != s->cap || h.evcap != s->evcap || h.seed != s->seed)
+    return fail(MJP_ERR_ARG, "checkpoint of a sampler with other chains, capacities or seed");
+  if (bytes < ckpt_bytes(s)) return fail(MJP_ERR_ARG, "checkpoint truncated");
+  if (h.evn < 0 || h.evn > s->evcap || h.rounds < 0 || h.kept_base < 0)
+    return fail(MJP_ERR_ARG, "checkpoint counters out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  size_t off = sizeof h;
+  cudaError_t e = cudaSuccess;
+  ckpt_parts(s, [&](DevBuf& b, size_t n) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.p, in + off, n, cudaMemcpyHostToDevice, st);
+    off += n;
+  });
+  MJP_CUDA(e);
+  MJP_CUDA(cudaStreamSynchronize(st));
+  s->evn = h.evn;
+  s->rounds = h.rounds;
+  s->kept_base = h.kept_base;
   return MJP_OK;
 } catch (...) {
   return ::mjp::exception_status();

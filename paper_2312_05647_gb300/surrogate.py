@@ -184,6 +184,33 @@ class Sampler:
         ll = torch.as_tensor(_DeviceView(l.value, (m,)), device="cuda").clone()
         return psi, ll
 
+    def checkpoint(self, path=None, net: MLP | None = None, stream=None) -> dict:
+        """The sampler's state between runs (mjp_sampler_save: chains, Philox
+        counters, counters, kept samples and evaluations, Z) as a byte array,
+        with the surrogate's parameters when `net` is given; written to `path`
+        (.npz) when one is given, and returned as a dict of arrays."""
+        n = ctypes.c_size_t()
+        capi.check(capi.lib().mjp_sampler_checkpoint_size(self._h, ctypes.byref(n)))
+        blob = np.zeros(int(n.value), dtype=np.uint8)
+        capi.check(capi.lib().mjp_sampler_save(self._h, _ptr(blob), blob.nbytes, _stream(stream)))
+        d = {"sampler": blob}
+        if net is not None:
+            d["mlp_params"], d["mlp_norm"] = net.get_params(stream)
+        if path is not None:
+            np.savez(path, **d)
+        return d
+
+    def resume(self, source, net: MLP | None = None, stream=None):
+        """Restore a checkpoint (a path written by checkpoint(), or its dict)
+        into this sampler, created with the same chains, capacities and seed
+        on the same model and observations; and the surrogate's parameters
+        into `net` when it is given and the checkpoint holds them."""
+        d = source if isinstance(source, dict) else np.load(source)
+        blob = np.ascontiguousarray(d["sampler"], dtype=np.uint8)
+        capi.check(capi.lib().mjp_sampler_load(self._h, _ptr(blob), blob.nbytes, _stream(stream)))
+        if net is not None and "mlp_params" in d:
+            net.set_params(d["mlp_params"], d["mlp_norm"], stream)
+
     def adapt(self, stream=None, **kw) -> dict:
         c = dict(SI_ADAPT)
         c.update(kw)
