@@ -3,8 +3,9 @@ bit-identical to the shared-memory chain kernel on single-member observation
 groups (same operation order per state), and within the FP32 tolerance of the
 oracle, over box shapes that exercise ragged column quads, odd row counts and
 clusters of 1, 2, 3, 4 and 8 CTAs; every state of a band observed (each
-thread summing an observation per register slot); the hand-over of the rows
-that cross a CTA boundary reports a wait that runs out."""
+thread summing an observation per register slot); ten runs of the same launch
+identical bit for bit; the hand-over of the rows that cross a CTA boundary
+reports a wait that runs out."""
 import numpy as np
 import pytest
 
@@ -211,3 +212,21 @@ def test_register_chain_with_every_state_of_a_band_observed(dims, rows, cols, ti
     nobs = sum(c.sum() for _, c in obs)
     ref = oracle.loglik(oracle.build_model(synth.MRNA_PROT2D, list(dims), thetas[0]), rho0, times, obs)
     assert abs(b[0] - ref) <= PER_OBS_FP32 * nobs
+
+
+@pytest.mark.parametrize("dims,threads", [((200, 200), 0), ((40, 1800), 256)])
+def test_register_chain_repeats_bit_for_bit(dims, threads):
+    # The same launch ten times (2- and 8-CTA clusters; rows handed over
+    # between CTAs by st.async, observations summed after the CTA barrier): a
+    # race in the hand-over, the edges or the observation sums would change
+    # some result between runs.
+    # Snapshots from the empty state reach past the first CTA boundary by
+    # t = 3 (p ~ 100 on the 200 x 200 box, ~300 on the 40 x 1800 one).
+    theta = (20.0, 1.0, 5.0, 0.1)
+    times = np.array([0.3, 1.0, 3.0])
+    obs, rho0 = _case(dims, theta, times, 30, seed=13)
+    thetas = synth.jitter(theta, 4, 0.2, synth.rng(2, 14))
+    runs = [_loglik(dims, theta, thetas, times, obs, rho0, 2, threads=threads) for _ in range(10)]
+    assert np.all(np.isfinite(runs[0]))
+    for r in runs[1:]:
+        np.testing.assert_array_equal(runs[0], r)
